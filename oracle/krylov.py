@@ -1,0 +1,412 @@
+"""Textbook Krylov least-squares solvers in FP64 numpy (test infrastructure).
+
+TEST INFRASTRUCTURE: used by the tests, the smoke check and the CPU baseline
+only; the GPU library never imports it.
+
+Every solver starts from x_0 = 0, runs a fixed number of iterations and takes an
+operator with ``matvec`` (A x) and ``rmatvec`` (A^T y) on flat vectors.  Each
+follows the recurrences of the method's original publication, step by step, in
+that publication's notation:
+
+* ``cgls``  -- conjugate gradients on the normal equations A^T A x = A^T b
+  (Sec. 2.1.1, Eq. 3; Hestenes-Stiefel), optionally on the damped system
+  [A; lam I] x ~ [b; 0] of Sec. 2.2, Eq. 7.
+* ``lsqr``  -- Golub-Kahan bidiagonalisation A V_k = U_{k+1} H_k with the
+  Paige-Saunders short recurrences (Sec. 2.1.2, Eq. 4), optional damping.
+* ``lsmr``  -- Golub-Kahan with the Fong-Saunders recurrences minimising
+  ||A^T r_k|| (Sec. 2.1.3, Eq. 5), optional damping lam (Sec. 2.2, Eq. 7).
+* ``hybrid_lsqr`` -- Tikhonov on the projected LSQR problem with lam_k per
+  iteration (Sec. 2.2.1, Eq. 8), lam_k fixed or chosen by GCV (Sec. 2.2.2).
+* ``krylov_reference`` -- the dense definition used to pin the recurrences:
+  an orthonormal basis of K_k(A^T A, A^T b) (Sec. 2, Eq. 2 of the Methods
+  introduction) and the small least-squares problem each method minimises.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = ["cgls", "lsqr", "lsmr", "hybrid_lsqr", "gcv_lambda", "gcv_function",
+           "projected_tikhonov", "krylov_basis", "krylov_reference"]
+
+
+def _norm(v):
+    return float(np.sqrt(np.dot(v, v)))
+
+
+def _rotation(a, b):
+    """Givens rotation (c, s, r) with [c s; -s c] [a; b] = [r; 0], r = hypot(a, b) >= 0."""
+    r = math.hypot(a, b)
+    if r == 0.0:
+        return 1.0, 0.0, 0.0
+    return a / r, b / r, r
+
+
+# --------------------------------------------------------------------------- CGLS
+def cgls(op, b, iters, damp=0.0, keep_iterates=False):
+    """CGLS (Sec. 2.1.1): x_k minimises ||A x - b|| over K_k(A^T A, A^T b).
+
+    With damp = lam the same recurrence runs on [A; lam I] x ~ [b; 0] (Eq. 7).
+    History: ``resid`` = ||b - A x_k|| (carried explicitly as r_k),
+    ``normal_resid`` = ||A^T r_k - lam^2 x_k||.
+    """
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    lam2 = float(damp) ** 2
+    x = np.zeros(op.shape[1])
+    r = b.copy()
+    s = op.rmatvec(r)                      # s_0 = A^T r_0 - lam^2 x_0
+    p = s.copy()
+    gamma = float(np.dot(s, s))
+    hist = {"resid": [], "normal_resid": [], "iterates": []}
+    for _ in range(iters):
+        q = op.matvec(p)
+        delta = float(np.dot(q, q)) + lam2 * float(np.dot(p, p))
+        if delta == 0.0 or gamma == 0.0:
+            break
+        alpha = gamma / delta
+        x = x + alpha * p
+        r = r - alpha * q
+        s = op.rmatvec(r) - lam2 * x
+        gamma_new = float(np.dot(s, s))
+        beta = gamma_new / gamma
+        p = s + beta * p
+        gamma = gamma_new
+        hist["resid"].append(_norm(r))
+        hist["normal_resid"].append(math.sqrt(gamma))
+        if keep_iterates:
+            hist["iterates"].append(x.copy())
+    return x, hist
+
+
+# --------------------------------------------------------------------------- LSQR
+def lsqr(op, b, iters, damp=0.0, keep_iterates=False):
+    """LSQR (Sec. 2.1.2): Golub-Kahan bidiagonalisation + Paige-Saunders recurrences.
+
+    Bidiagonalisation: beta_1 u_1 = b, alpha_1 v_1 = A^T u_1,
+    beta_{i+1} u_{i+1} = A v_i - alpha_i u_i,
+    alpha_{i+1} v_{i+1} = A^T u_{i+1} - beta_{i+1} v_i.
+    With damp = lam > 0 a first rotation eliminates lam from the augmented
+    bidiagonal (Eq. 7 projected).  History: ``resid`` = phibar estimate of
+    ||r_k|| (augmented residual when damped), ``normal_resid`` =
+    phibar alpha |c| estimate of ||A^T r_k||, ``alpha``/``beta`` = the
+    bidiagonal entries.
+    """
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    lam = float(damp)
+    x = np.zeros(op.shape[1])
+    beta = _norm(b)
+    hist = {"resid": [], "normal_resid": [], "alpha": [], "beta": [beta], "iterates": []}
+    if beta == 0.0:
+        return x, hist
+    u = b / beta
+    v = op.rmatvec(u)
+    alpha = _norm(v)
+    hist["alpha"].append(alpha)
+    if alpha == 0.0:
+        return x, hist
+    v = v / alpha
+    w = v.copy()
+    phibar = beta
+    rhobar = alpha
+    psi_sq = 0.0
+    for _ in range(iters):
+        u = op.matvec(v) - alpha * u
+        beta = _norm(u)
+        if beta > 0.0:
+            u = u / beta
+        v = op.rmatvec(u) - beta * v
+        alpha_next = _norm(v)
+        if alpha_next > 0.0:
+            v = v / alpha_next
+        hist["beta"].append(beta)
+        hist["alpha"].append(alpha_next)
+        # rotation that eliminates the damping term
+        c1, s1, rhobar1 = _rotation(rhobar, lam)
+        psi = s1 * phibar
+        phibar = c1 * phibar
+        psi_sq += psi * psi
+        # rotation that eliminates beta_{i+1}
+        c, s, rho = _rotation(rhobar1, beta)
+        theta = s * alpha_next
+        rhobar = -c * alpha_next
+        phi = c * phibar
+        phibar = s * phibar
+        x = x + (phi / rho) * w
+        w = v - (theta / rho) * w
+        alpha = alpha_next
+        hist["resid"].append(math.sqrt(phibar * phibar + psi_sq))
+        hist["normal_resid"].append(abs(phibar * alpha_next * c))
+        if keep_iterates:
+            hist["iterates"].append(x.copy())
+        if beta == 0.0 or alpha_next == 0.0:
+            break
+    return x, hist
+
+
+# --------------------------------------------------------------------------- LSMR
+def lsmr(op, b, iters, damp=0.0, keep_iterates=False):
+    """LSMR (Sec. 2.1.3): Golub-Kahan + Fong-Saunders recurrences.
+
+    x_k minimises ||A^T r_k|| (of the damped system when damp = lam) over
+    K_k(A^T A, A^T b).  Three rotations per step: P-hat eliminates the damping,
+    P turns the bidiagonal into upper-triangular R_k, P-bar turns R_k^T into
+    upper-bidiagonal R-bar_k.  History: ``normal_resid`` = |zeta-bar_{k+1}|
+    estimate of ||A^T r_k - lam^2 x_k||, ``resid`` = the ||r_k|| estimate from
+    the same publication's extra rotations (Q-hat, Q, Q-tilde).
+    """
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    lam = float(damp)
+    x = np.zeros(op.shape[1])
+    beta = _norm(b)
+    hist = {"resid": [], "normal_resid": [], "iterates": []}
+    if beta == 0.0:
+        return x, hist
+    u = b / beta
+    v = op.rmatvec(u)
+    alpha = _norm(v)
+    if alpha == 0.0:
+        return x, hist
+    v = v / alpha
+
+    alphabar = alpha
+    zetabar = alpha * beta
+    rho = 1.0
+    rhobar = 1.0
+    cbar, sbar = 1.0, 0.0
+    h = v.copy()
+    hbar = np.zeros_like(x)
+    # state of the ||r_k|| estimate
+    betadd = beta          # beta-double-dot
+    betad = 0.0            # beta-dot
+    rhod = 1.0             # rho-dot of the previous step
+    tautilde = 0.0
+    thetatilde = 0.0
+    zeta = 0.0
+    dsum = 0.0
+
+    for _ in range(iters):
+        u = op.matvec(v) - alpha * u
+        beta = _norm(u)
+        if beta > 0.0:
+            u = u / beta
+        v = op.rmatvec(u) - beta * v
+        alpha = _norm(v)
+        if alpha > 0.0:
+            v = v / alpha
+
+        chat, shat, alphahat = _rotation(alphabar, lam)          # P-hat_k
+        rho_prev = rho
+        c, s, rho = _rotation(alphahat, beta)                   # P_k
+        theta_next = s * alpha
+        alphabar = c * alpha
+
+        rhobar_prev = rhobar                                     # P-bar_k
+        zeta_prev = zeta
+        thetabar = sbar * rho
+        cbar, sbar, rhobar = _rotation(cbar * rho, theta_next)
+        zeta = cbar * zetabar
+        zetabar = -sbar * zetabar
+
+        hbar = h - (thetabar * rho / (rho_prev * rhobar_prev)) * hbar
+        x = x + (zeta / (rho * rhobar)) * hbar
+        h = v - (theta_next / rho) * h
+
+        # ||r_k||: apply Q-hat_k and Q_k to (beta-double-dot, 0), then Q-tilde_{k-1}
+        betaacute = chat * betadd
+        betacheck = -shat * betadd
+        betahat = c * betaacute
+        betadd = -s * betaacute
+        thetatilde_prev = thetatilde
+        ctilde, stilde, rhotilde_prev = _rotation(rhod, thetabar)
+        thetatilde = stilde * rhobar
+        rhod = ctilde * rhobar
+        betad = -stilde * betad + ctilde * betahat
+        tautilde = (zeta_prev - thetatilde_prev * tautilde) / rhotilde_prev
+        taud = (zeta - thetatilde * tautilde) / rhod
+        dsum += betacheck * betacheck
+        hist["resid"].append(math.sqrt(dsum + (betad - taud) ** 2 + betadd * betadd))
+        hist["normal_resid"].append(abs(zetabar))
+        if keep_iterates:
+            hist["iterates"].append(x.copy())
+        if beta == 0.0 or alpha == 0.0:
+            break
+    return x, hist
+
+
+# ------------------------------------------------------------------ hybrid LSQR + GCV
+def _bidiagonal(alphas, betas, k):
+    """H_k ((k+1) x k lower bidiagonal): H[i,i] = alpha_{i+1}, H[i+1,i] = beta_{i+2}."""
+    h = np.zeros((k + 1, k))
+    for i in range(k):
+        h[i, i] = alphas[i]
+        h[i + 1, i] = betas[i + 1]
+    return h
+
+
+def gcv_function(sigma, p1, beta1, lam):
+    """GCV of the projected problem (Sec. 2.2.2) at lam, from H_k = P Sigma Q^T.
+
+    G(lam) = ||(I - H H^+_lam) beta1 e1||^2 / (trace(I - H H^+_lam))^2 with
+    H^+_lam = (H^T H + lam^2 I)^{-1} H^T; p1 = first row of P (length k+1).
+    """
+    k = sigma.shape[0]
+    s2 = sigma * sigma
+    l2 = lam * lam
+    f = l2 / (s2 + l2)                               # 1 - filter factor
+    num = float(np.sum((f * beta1 * p1[:k]) ** 2) + (beta1 * p1[k]) ** 2)
+    den = float((k + 1) - np.sum(s2 / (s2 + l2)))
+    return num / (den * den)
+
+
+GCV_GRID_POINTS = 200
+GCV_GRID_DECADES = 8.0
+GCV_REL_TOL = 1e-10
+
+
+def gcv_lambda(sigma, p1, beta1):
+    """Minimiser of the GCV function.
+
+    The paper gives no minimisation procedure.  Reading used here: evaluate G on
+    200 log-spaced points over [sigma_max 1e-8, sigma_max]; take the smallest
+    value (ties to the larger lam); refine by golden-section search in log lam on
+    the neighbouring grid bracket until the bracket is narrower than 1e-10
+    relative.
+    """
+    smax = float(np.max(sigma))
+    if smax == 0.0:
+        return 0.0
+    lo_exp = math.log(smax) - GCV_GRID_DECADES * math.log(10.0)
+    hi_exp = math.log(smax)
+    n = GCV_GRID_POINTS
+    grid = [lo_exp + (hi_exp - lo_exp) * i / (n - 1) for i in range(n)]
+    vals = [gcv_function(sigma, p1, beta1, math.exp(t)) for t in grid]
+    best = 0
+    for i in range(1, n):
+        if vals[i] <= vals[best]:
+            best = i
+    a = grid[max(best - 1, 0)]
+    c = grid[min(best + 1, n - 1)]
+    invphi = (math.sqrt(5.0) - 1.0) / 2.0
+    x1 = c - invphi * (c - a)
+    x2 = a + invphi * (c - a)
+    f1 = gcv_function(sigma, p1, beta1, math.exp(x1))
+    f2 = gcv_function(sigma, p1, beta1, math.exp(x2))
+    while c - a > GCV_REL_TOL:
+        if f1 < f2:
+            c, x2, f2 = x2, x1, f1
+            x1 = c - invphi * (c - a)
+            f1 = gcv_function(sigma, p1, beta1, math.exp(x1))
+        else:
+            a, x1, f1 = x1, x2, f2
+            x2 = a + invphi * (c - a)
+            f2 = gcv_function(sigma, p1, beta1, math.exp(x2))
+    t = 0.5 * (a + c)
+    # keep the grid point if the refinement did not improve on it
+    if gcv_function(sigma, p1, beta1, math.exp(t)) > vals[best]:
+        t = grid[best]
+    return math.exp(t)
+
+
+def projected_tikhonov(h, beta1, lam, svd=None):
+    """y = argmin ||beta1 e1 - H y||^2 + lam^2 ||y||^2 (Eq. 8) via the SVD H = P Sigma Q^T."""
+    p, sigma, qt = np.linalg.svd(h, full_matrices=True) if svd is None else svd
+    k = h.shape[1]
+    denom = sigma * sigma + lam * lam
+    coef = np.where(denom > 0.0, sigma * beta1 * p[0, :k] / np.where(denom > 0.0, denom, 1.0), 0.0)
+    return qt.T @ coef
+
+
+def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False):
+    """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lam_k fixed or chosen by GCV (Sec. 2.2.2).
+
+    Stores the basis V_k; at every iteration k solves the projected Tikhonov
+    problem for y_k and forms x_k = V_k y_k.  History: ``resid`` = projected
+    residual ||beta1 e1 - H_k y_k|| (equal to ||b - A x_k|| in exact arithmetic),
+    ``lambda`` = lam_k, ``alpha``/``beta`` = bidiagonal entries.
+    """
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    x = np.zeros(op.shape[1])
+    beta1 = _norm(b)
+    hist = {"resid": [], "lambda": [], "alpha": [], "beta": [beta1], "iterates": []}
+    if beta1 == 0.0:
+        return x, hist
+    u = b / beta1
+    v = op.rmatvec(u)
+    alpha = _norm(v)
+    hist["alpha"].append(alpha)
+    if alpha == 0.0:
+        return x, hist
+    v = v / alpha
+    basis = [v]
+    for k in range(1, iters + 1):
+        u = op.matvec(v) - alpha * u
+        beta = _norm(u)
+        if beta > 0.0:
+            u = u / beta
+        v = op.rmatvec(u) - beta * v
+        alpha = _norm(v)
+        if alpha > 0.0:
+            v = v / alpha
+        hist["beta"].append(beta)
+        hist["alpha"].append(alpha)
+        h = _bidiagonal(hist["alpha"], hist["beta"], k)
+        svd = np.linalg.svd(h, full_matrices=True)
+        if rule == "gcv":
+            lam_k = gcv_lambda(svd[1], svd[0][0, :], beta1)
+        elif rule == "fixed":
+            lam_k = float(lam)
+        else:
+            raise ValueError(rule)
+        y = projected_tikhonov(h, beta1, lam_k, svd)
+        x = np.stack(basis, axis=1) @ y
+        rhs = np.zeros(k + 1)
+        rhs[0] = beta1
+        hist["resid"].append(_norm(rhs - h @ y))
+        hist["lambda"].append(lam_k)
+        if keep_iterates:
+            hist["iterates"].append(x.copy())
+        basis.append(v)
+        if beta == 0.0 or alpha == 0.0:
+            break
+    return x, hist
+
+
+# ------------------------------------------------------------ dense Krylov reference
+def krylov_basis(a, b, k):
+    """Orthonormal basis (columns) of K_k(A^T A, A^T b), Arnoldi with full
+    re-orthogonalisation (two passes of classical Gram-Schmidt), dense FP64."""
+    a = np.asarray(a, dtype=np.float64)
+    ata = a.T @ a
+    q = a.T @ np.asarray(b, dtype=np.float64).reshape(-1)
+    basis = [q / np.linalg.norm(q)]
+    for _ in range(1, k):
+        w = ata @ basis[-1]
+        for _pass in range(2):
+            for qj in basis:
+                w = w - np.dot(qj, w) * qj
+        basis.append(w / np.linalg.norm(w))
+    return np.stack(basis, axis=1)
+
+
+def krylov_reference(a, b, k, method, damp=0.0):
+    """x_k by its defining minimisation over K_k (dense, for pinning the recurrences).
+
+    method "lsqr"/"cgls": argmin ||[A; lam I] x - [b; 0]|| over K_k (Eqs. 3-4, 7);
+    method "lsmr": argmin ||A^T b - (A^T A + lam^2 I) x|| over K_k (Eq. 5, 7).
+    K_k(A^T A + lam^2 I, A^T b) = K_k(A^T A, A^T b) (shift invariance, Sec. 2.2.1).
+    """
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    v = krylov_basis(a, b, k)
+    lam2 = float(damp) ** 2
+    if method in ("lsqr", "cgls"):
+        aug = np.vstack([a @ v, math.sqrt(lam2) * v])
+        rhs = np.concatenate([b, np.zeros(v.shape[0])])
+        y = np.linalg.lstsq(aug, rhs, rcond=None)[0]
+    elif method == "lsmr":
+        n_op = a.T @ (a @ v) + lam2 * v
+        y = np.linalg.lstsq(n_op, a.T @ b, rcond=None)[0]
+    else:
+        raise ValueError(method)
+    return v @ y

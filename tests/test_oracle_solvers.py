@@ -1,0 +1,180 @@
+"""Pins of the oracle's Krylov solvers against definitions that do not use their recurrences.
+
+* Each iterate is the minimiser over K_k(A^T A, A^T b) of the method's own
+  criterion (Eqs. 3-5): compared with a dense Krylov basis + lstsq.
+* CGLS and LSQR are mathematically equivalent (Sec. 2.1.2).
+* LSQR/LSMR converge to the least-squares solution (Sec. 2.1.3); with damping
+  lam, to the solution of the augmented system (Eq. 7).
+* ||r_k|| is monotone for CGLS/LSQR and ||A^T r_k|| for LSMR.
+* Hybrid LSQR with a fixed lam equals projecting the augmented system (Sec. 2.2.1).
+* The GCV function equals its definition with an explicit H^+_lam (Sec. 2.2.2),
+  and its minimiser agrees with a brute-force grid.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import krylov
+
+
+@pytest.fixture(scope="module")
+def tiny_system():
+    g = synth.config("tiny")
+    a = oracle.dense_matrix(g)
+    x_true = synth.ellipsoid_phantom(g, 4, seed=3).astype(np.float64).ravel()
+    rng = np.random.default_rng(4)
+    b = a @ x_true + 0.05 * rng.standard_normal(a.shape[0])
+    return a, b
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("method", ["cgls", "lsqr", "lsmr"])
+@pytest.mark.parametrize("damp", [0.0, 1.5])
+def test_iterates_minimise_over_krylov_space(tiny_system, method, damp):
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    solver = getattr(krylov, method)
+    _, hist = solver(op, b, 8, damp=damp, keep_iterates=True)
+    for k, xk in enumerate(hist["iterates"], start=1):
+        ref = krylov.krylov_reference(a, b, k, method, damp)
+        assert rel(xk, ref) < 1e-8, (method, damp, k)
+
+
+def test_cgls_equals_lsqr(tiny_system):
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    _, hc = krylov.cgls(op, b, 12, keep_iterates=True)
+    _, hl = krylov.lsqr(op, b, 12, keep_iterates=True)
+    for xc, xl in zip(hc["iterates"], hl["iterates"]):
+        assert rel(xc, xl) < 1e-9
+
+
+def test_lsqr_lsmr_reach_least_squares_solution():
+    rng = np.random.default_rng(8)
+    a = rng.standard_normal((60, 20))
+    b = rng.standard_normal(60)
+    ref = np.linalg.lstsq(a, b, rcond=None)[0]
+    op = oracle.DenseOperator(a)
+    for solver in (krylov.lsqr, krylov.lsmr, krylov.cgls):
+        x, _ = solver(op, b, 60)
+        assert rel(x, ref) < 1e-10
+
+
+@pytest.mark.parametrize("solver", [krylov.lsmr, krylov.lsqr, krylov.cgls])
+def test_damped_limit_is_augmented_lstsq(tiny_system, solver):
+    a, b = tiny_system
+    lam = 2.0
+    aug = np.vstack([a, lam * np.eye(a.shape[1])])
+    rhs = np.concatenate([b, np.zeros(a.shape[1])])
+    ref = np.linalg.lstsq(aug, rhs, rcond=None)[0]
+    x, _ = solver(oracle.DenseOperator(a), b, 150, damp=lam)
+    assert rel(x, ref) < 1e-8
+
+
+def test_residual_histories_monotone_and_match_explicit(tiny_system):
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    for name in ("cgls", "lsqr"):
+        _, h = getattr(krylov, name)(op, b, 25, keep_iterates=True)
+        r = np.array(h["resid"])
+        assert np.all(np.diff(r) <= 1e-12 * r[0])
+        explicit = [np.linalg.norm(b - a @ x) for x in h["iterates"]]
+        np.testing.assert_allclose(r, explicit, rtol=1e-9)
+        explicit_n = [np.linalg.norm(a.T @ (b - a @ x)) for x in h["iterates"]]
+        np.testing.assert_allclose(h["normal_resid"], explicit_n, rtol=1e-6)
+    _, h = krylov.lsmr(op, b, 25, keep_iterates=True)
+    nr = np.array(h["normal_resid"])
+    assert np.all(np.diff(nr) <= 1e-12 * nr[0])
+    explicit_n = [np.linalg.norm(a.T @ (b - a @ x)) for x in h["iterates"]]
+    np.testing.assert_allclose(nr, explicit_n, rtol=1e-6)
+    explicit = [np.linalg.norm(b - a @ x) for x in h["iterates"]]
+    np.testing.assert_allclose(h["resid"], explicit, rtol=1e-9)
+
+
+def test_damped_residual_estimates(tiny_system):
+    a, b = tiny_system
+    lam = 1.5
+    op = oracle.DenseOperator(a)
+    _, h = krylov.lsqr(op, b, 15, damp=lam, keep_iterates=True)
+    aug = [math.sqrt(np.linalg.norm(b - a @ x) ** 2 + lam * lam * np.linalg.norm(x) ** 2) for x in h["iterates"]]
+    np.testing.assert_allclose(h["resid"], aug, rtol=1e-9)
+    _, h = krylov.lsmr(op, b, 15, damp=lam, keep_iterates=True)
+    normal = [np.linalg.norm(a.T @ (b - a @ x) - lam * lam * x) for x in h["iterates"]]
+    np.testing.assert_allclose(h["normal_resid"], normal, rtol=1e-6)
+
+
+def test_hybrid_fixed_lambda_equals_damped_lsqr(tiny_system):
+    a, b = tiny_system
+    lam = 3.0
+    op = oracle.DenseOperator(a)
+    _, hh = krylov.hybrid_lsqr(op, b, 10, rule="fixed", lam=lam, keep_iterates=True)
+    _, hl = krylov.lsqr(op, b, 10, damp=lam, keep_iterates=True)
+    for k, (xh, xl) in enumerate(zip(hh["iterates"], hl["iterates"]), start=1):
+        assert rel(xh, xl) < 1e-9
+        assert rel(xh, krylov.krylov_reference(a, b, k, "lsqr", lam)) < 1e-8
+
+
+def test_projected_tikhonov_matches_normal_equations():
+    rng = np.random.default_rng(21)
+    k = 7
+    h = np.zeros((k + 1, k))
+    for i in range(k):
+        h[i, i] = rng.uniform(0.5, 2)
+        h[i + 1, i] = rng.uniform(0.1, 1)
+    beta1, lam = 3.7, 0.4
+    y = krylov.projected_tikhonov(h, beta1, lam)
+    e1 = np.zeros(k + 1)
+    e1[0] = beta1
+    ref = np.linalg.solve(h.T @ h + lam * lam * np.eye(k), h.T @ e1)
+    np.testing.assert_allclose(y, ref, rtol=1e-12)
+
+
+def test_gcv_function_equals_definition():
+    rng = np.random.default_rng(22)
+    k = 9
+    h = np.zeros((k + 1, k))
+    for i in range(k):
+        h[i, i] = rng.uniform(0.01, 2)
+        h[i + 1, i] = rng.uniform(0.01, 1)
+    beta1 = 2.3
+    p, sigma, _ = np.linalg.svd(h, full_matrices=True)
+    e1 = np.zeros(k + 1)
+    e1[0] = beta1
+    for lam in (1e-3, 0.05, 0.7, 4.0):
+        hdag = np.linalg.solve(h.T @ h + lam * lam * np.eye(k), h.T)
+        m = np.eye(k + 1) - h @ hdag
+        direct = np.linalg.norm(m @ e1) ** 2 / np.trace(m) ** 2
+        assert abs(krylov.gcv_function(sigma, p[0], beta1, lam) - direct) <= 1e-12 * direct
+
+
+def test_gcv_minimiser_matches_brute_force_grid(tiny_system):
+    a, b = tiny_system
+    _, h = krylov.lsqr(oracle.DenseOperator(a), b, 12)
+    k = 12
+    hk = np.zeros((k + 1, k))
+    for i in range(k):
+        hk[i, i] = h["alpha"][i]
+        hk[i + 1, i] = h["beta"][i + 1]
+    beta1 = h["beta"][0]
+    p, sigma, _ = np.linalg.svd(hk, full_matrices=True)
+    lam = krylov.gcv_lambda(sigma, p[0], beta1)
+    grid = np.exp(np.linspace(math.log(sigma.max()) - 8 * math.log(10), math.log(sigma.max()), 10_000))
+    vals = np.array([krylov.gcv_function(sigma, p[0], beta1, t) for t in grid])
+    best = grid[np.argmin(vals)]
+    step = grid[1] / grid[0]
+    assert best / step <= lam <= best * step
+    assert krylov.gcv_function(sigma, p[0], beta1, lam) <= vals.min() * (1 + 1e-9)
+
+
+def test_hybrid_gcv_runs_and_lambda_positive(tiny_system):
+    a, b = tiny_system
+    x, h = krylov.hybrid_lsqr(oracle.DenseOperator(a), b, 10, rule="gcv")
+    assert all(l > 0 for l in h["lambda"])
+    # projected residual equals the explicit one (A V_k = U_{k+1} H_k)
+    assert abs(h["resid"][-1] - np.linalg.norm(b - a @ x)) <= 1e-8 * np.linalg.norm(b)
