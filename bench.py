@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the Krylov CBCT hot path on GB300.
+
+Workload (the 256^3 medical configuration): 256^3 x 1 mm volume, 512 x 512
+detector of 0.8 mm pixels, 360 angles over 360 deg, DSO 1000 / DSD 1536 mm,
+random-ellipsoid phantom x 0.02 mm^-1, Poisson noise with I0 = 1e5.  One step
+= LSQR 30 iterations + LSMR 30 iterations on that b (both through the C ABI,
+FP32 vectors, FP64 scalars).
+
+Printed JSON line (rank 0):
+  value      ray-voxel Gupdates/s of the whole step (nnz(A) x projector
+             launches / step time), inputs resident in HBM;
+  e2e        the same metric with b read from pinned host memory and x
+             written back to the host inside the timed region;
+  roofline   the dominant projector kernel: nnz x 4 B gathered per launch /
+             its CUDA-event launch time, against the measured HBM copy peak;
+  cpu_baseline  the FP64 oracle on the host cores, on an 8-angle sample.
+`--impl reference` times that oracle alone (the CPU reference arm).
+Multi-GPU (torchrun): independent replicas, one per rank, weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ray-voxel Gupdates/s and LSQR iters/s at 256^3; serving recon/s, p50/p99 latency"
+UNIT = "Gupdates/s"
+ITERS = 30
+I0 = 1e5
+BYTES_PER_UPDATE = 4          # one FP32 voxel (forward) or projection (backward) value per ray-voxel update
+CPU_SAMPLE_ANGLES = 8
+
+# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by the projector source it was measured on; None once the source changed.
+NCU_TRAFFIC = {
+    # "forward": (bytes_per_launch, sha256 of csrc/projector.cu),
+}
+
+
+def workload_config():
+    import synth
+    g = synth.config("c2")
+    return g, {
+        "workload": "256^3 medical CBCT: LSQR 30 + LSMR 30 iterations per step",
+        "volume": [g.nx, g.ny, g.nz], "voxel_mm": g.dx,
+        "detector": [g.nu, g.nv], "pixel_mm": g.du, "angles": g.nangles,
+        "dso_mm": g.dso, "dsd_mm": g.dsd, "phantom": "10 random ellipsoids (seed 1) x 0.02 mm^-1",
+        "noise": "Poisson I0=1e5, log-transformed",
+        "l2": "inputs larger than L2 (projection stack 360 MiB, Krylov vectors 64-360 MiB each)",
+    }
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def projector_hash():
+    with open(os.path.join(ROOT, "paper_2211_14212_gb300", "csrc", "projector.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                p = [c.strip() for c in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def oracle_sample_rate(g, nangles=CPU_SAMPLE_ANGLES, gpu_nnz=None):
+    """FP64 oracle A x and A^T y on `nangles` angles of the workload; Gupdates/s."""
+    import numpy as np
+    import oracle
+    import synth
+    sub = g.angle_subset(nangles)
+    x = synth.ellipsoid_phantom(g, 10, seed=1, scale=0.02).astype(np.float64)
+    y = synth.random_projections(sub, 3)
+    nnz = gpu_nnz(sub) if gpu_nnz else oracle.nnz(sub)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.project(sub, x, cores)
+    oracle.backproject(sub, y, cores)
+    dt = time.perf_counter() - t0
+    return 2 * nnz / dt / 1e9, cores, dt, nnz
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    g, config = workload_config()
+    for _ in range(args.warmup):
+        oracle_sample_rate(g, 2)
+    vals, times = [], []
+    cores = nnz = None
+    for _ in range(args.steps):
+        v, cores, dt, nnz = oracle_sample_rate(g, CPU_SAMPLE_ANGLES)
+        vals.append(v)
+        times.append(dt)
+    value = sum(2 * nnz for _ in times) / sum(times) / 1e9
+    sample = "FP64 oracle A x + A^T y on %d of %d angles (%d updates each)" % (CPU_SAMPLE_ANGLES, g.nangles, nnz)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2211_14212_gb300 import cbct
+
+    g, config = workload_config()
+    dev = torch.device("cuda", local)
+    geom = cbct.Geometry(g)
+    x_true = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=1, scale=0.02)).to(dev)
+    b_clean = cbct.project(geom, x_true).cpu().numpy()
+    b_host = torch.from_numpy(synth.poisson_log_noise(b_clean, I0, seed=2 + rank)).pin_memory()
+    b = b_host.to(dev)
+    del b_clean
+    nnz = cbct.count_nnz(geom)
+    s = torch.cuda.Stream(device=dev)
+    x1 = torch.empty(geom.vol_shape, device=dev)
+    x2 = torch.empty(geom.vol_shape, device=dev)
+
+    def step(bb, xa, xb, profile):
+        r1 = cbct.lsqr(geom, bb, ITERS, x=xa, stream=s, profile=profile)[1]
+        t_lsqr = time.perf_counter()
+        r2 = cbct.lsmr(geom, bb, ITERS, x=xb, stream=s, profile=profile)[1]
+        return r1, r2, t_lsqr
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            step(b, x1, x2, False)
+    barrier()
+
+    # ---- timed region: inputs resident in HBM
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis and all(p.strip().isdigit() for p in vis.split(",")):
+        gpu_index = int(vis.split(",")[local])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    products = launches = 0
+    fwd_ms = bwd_ms = 0.0
+    fwd_n = bwd_n = 0
+    lsqr_s = 0.0
+    with ClockSampler(gpu_index) as clk:
+        with torch.cuda.stream(s):
+            ev0.record(s)
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                r1, r2, t1 = step(b, x1, x2, True)
+                lsqr_s += t1 - t0          # the solver synchronises its stream before returning
+                for r in (r1, r2):
+                    products += r.forward_launches + r.backward_launches
+                    launches += r.kernel_launches
+                    fwd_ms += r.forward_ms
+                    bwd_ms += r.backward_ms
+                    fwd_n += r.forward_launches
+                    bwd_n += r.backward_launches
+            ev1.record(s)
+        barrier()
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    clocks = clk.summary()
+    value = world * nnz * products / (elapsed_ms * 1e-3) / 1e9
+    lsqr_ips = ITERS * args.steps / lsqr_s
+
+    # ---- end to end: b from pinned host memory, x back to host, inside the timed region
+    xh1 = torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory()
+    xh2 = torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory()
+    bh = b_host.numpy()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_products = 0
+    with torch.cuda.stream(s):
+        for _ in range(args.steps):
+            r1, r2, _ = step(bh, xh1.numpy(), xh2.numpy(), False)
+            e2e_products += r1.forward_launches + r1.backward_launches + r2.forward_launches + r2.backward_launches
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * nnz * e2e_products / e2e_s / 1e9
+
+    if rank != 0:
+        return 0
+    dominant = "forward" if fwd_ms >= bwd_ms else "backward"
+    avg_ms = fwd_ms / max(fwd_n, 1) if dominant == "forward" else bwd_ms / max(bwd_n, 1)
+    peak, peak_kind = measured_peak()
+    achieved = nnz * BYTES_PER_UPDATE / (avg_ms * 1e-3) / 1e9
+    tr = NCU_TRAFFIC.get(dominant)
+    traffic = tr[0] if tr and tr[1] == projector_hash() else None
+    cpu = None
+    if not args.no_cpu_baseline:
+        def gpu_nnz(sub):
+            return cbct.count_nnz(cbct.Geometry(sub))
+        v, cores, dt, snnz = oracle_sample_rate(g, CPU_SAMPLE_ANGLES, gpu_nnz)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle A x + A^T y on %d of %d angles (%d updates each, %.1f s)"
+                         % (CPU_SAMPLE_ANGLES, g.nangles, snnz, dt)}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "lsqr_iters_per_s": lsqr_ips,
+        "nnz": nnz,
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "avg_launch_ms": avg_ms,
+                     "forward_ms_per_launch": fwd_ms / max(fwd_n, 1),
+                     "backward_ms_per_launch": bwd_ms / max(bwd_n, 1)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * geom.num_rays,
+                "d2h_bytes_per_step": 2 * 4 * geom.num_voxels},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
+
+
+if __name__ == "__main__":
+    main()

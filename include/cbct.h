@@ -1,0 +1,171 @@
+/*
+ * cbct.h -- C ABI of the GB300 cone-beam CT reconstruction library (libcbct.so).
+ *
+ * The library computes the two matrix-vector products every Krylov method of
+ * Sabate Landman, Biguri et al., "On Krylov Methods for Large Scale CBCT
+ * Reconstruction", spends its time on (Sec. 2: "the computational cost ... is
+ * dominated by a matrix vector product by A and A^T per iteration"):
+ *
+ *   y = A x     forward projection, A in R^{N x M} (Sec. 1, Eq. 1),
+ *   x = A^T y   its exact transpose (backprojection),
+ *
+ * and the solvers of Sec. 2.1-2.2 built around them, with every vector kept on
+ * the GPU and every Krylov scalar in FP64.
+ *
+ * System matrix.  A[i][j] is the length (mm) of ray i inside voxel j.  Ray i
+ * is the segment from the X-ray source to the centre of detector pixel i;
+ * voxel j is a half-open box.  N = nangles * nv * nu rays, M = nx * ny * nz.
+ *
+ * Geometry conventions (the paper leaves them to its toolbox):
+ *   rotation axis = z, origin = rotation centre = volume centre;
+ *   source at (dso cos t, dso sin t, 0) for source angle t;
+ *   detector centre at -(dsd - dso) (cos t, sin t, 0);
+ *   detector axes e_u = (-sin t, cos t, 0), e_v = (0, 0, 1);
+ *   pixel (iu, iv) centre = detector centre + (iu - (nu-1)/2) du e_u
+ *                                          + (iv - (nv-1)/2) dv e_v;
+ *   voxel (i, j, k) = [x0 + i dx, x0 + (i+1) dx) x [...] x [...],
+ *                     x0 = -nx dx / 2 (likewise y, z).
+ * Layout: volumes are x[k][j][i] (x fastest), projection stacks are
+ * y[a][iv][iu] (u fastest), both dense and row-major.
+ *
+ * Threading and streams.  Every call that takes a stream enqueues its GPU work
+ * on that stream (NULL = the legacy default stream).  Solvers synchronise the
+ * stream once at the end to copy their report to the host.  A geometry may be
+ * shared by calls on different streams and host threads.
+ *
+ * Errors.  Every call returns a cbct_status; nothing is thrown across the ABI.
+ * cbct_last_error() returns a message for the calling thread's last failure.
+ */
+#ifndef CBCT_H
+#define CBCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (binary-compatible with cudaStream_t); NULL = default stream. */
+typedef struct CUstream_st *cbct_stream;
+
+typedef enum {
+    CBCT_OK = 0,
+    CBCT_EINVAL = 1,      /* bad argument: null pointer, size, non-physical geometry */
+    CBCT_ENOMEM = 2,      /* device or host allocation failed */
+    CBCT_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+    CBCT_EBREAKDOWN = 4,  /* a Krylov scalar became zero or non-finite; x holds the last finite iterate */
+    CBCT_ETIMEOUT = 5,    /* a bounded wait gave up (serving) */
+    CBCT_EBUDGET = 6,     /* request larger than the serving HBM budget */
+    CBCT_ENOTFOUND = 7    /* unknown request id (serving) */
+} cbct_status;
+
+/* Storage type of volumes / projections / Krylov vectors.  Arithmetic is FP32
+ * (projectors) and FP64 (Krylov scalars) whatever the storage type. */
+typedef enum { CBCT_F32 = 0, CBCT_F16 = 1, CBCT_BF16 = 2 } cbct_dtype;
+
+/* Circular cone-beam scan.  Lengths in mm, angles in radians.  Requirements:
+ * all counts >= 1, all sizes > 0, dsd > dso, and the source and detector must
+ * lie outside the cylinder that circumscribes the volume. */
+typedef struct {
+    int nx, ny, nz;               /* voxels */
+    double dx, dy, dz;            /* voxel size */
+    int nu, nv;                   /* detector pixels (u = in-plane, v = axial) */
+    double du, dv;                /* pixel pitch */
+    double dso, dsd;              /* source-origin and source-detector distances */
+    int nangles;                  /* projections */
+    const double *angles_rad;     /* host array of nangles source angles; copied */
+} cbct_geometry_desc;
+
+typedef struct cbct_geometry cbct_geometry;   /* opaque, library-owned */
+
+/* Builds the device-side ray tables of a scan (on the current CUDA device).
+ * On success *out owns device memory until cbct_geometry_destroy. */
+cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct_geometry **out);
+void cbct_geometry_destroy(cbct_geometry *geom);
+int64_t cbct_geometry_num_voxels(const cbct_geometry *geom);   /* M, or -1 for NULL */
+int64_t cbct_geometry_num_rays(const cbct_geometry *geom);     /* N, or -1 for NULL */
+
+/* y = A x (Sec. 1, Eq. 1).  x: M device elements, y: N device elements, both
+ * of `dtype`, caller-owned, non-overlapping.  Ray sums are FP32 (Kahan-
+ * compensated for F16/BF16 storage).  Asynchronous on `stream`. */
+cbct_status cbct_project(const cbct_geometry *geom, const void *x, void *y,
+                         cbct_dtype dtype, cbct_stream stream);
+
+/* x = A^T y, the exact transpose of cbct_project (same ray/voxel lengths, so
+ * <A x, y> = <x, A^T y> up to FP32 rounding of the sums; Sec. 2.1.4 explains
+ * why an unmatched backprojector breaks the Krylov methods).  y: N device
+ * elements, x: M device elements of `dtype`.  Asynchronous on `stream`. */
+cbct_status cbct_backproject(const cbct_geometry *geom, const void *y, void *x,
+                             cbct_dtype dtype, cbct_stream stream);
+
+/* Number of nonzeros of A (positive-length ray/voxel pairs in FP32), counted
+ * by the forward traversal.  Synchronises `stream`. */
+cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream stream);
+
+/* ------------------------------------------------------------------ solvers
+ * All solvers start from x_0 = 0 and run opts->iters iterations (fewer on
+ * breakdown).  b (N FP32 values) and x (M FP32 values, output only) may be
+ * device or host pointers; host buffers are staged through device memory.
+ * Each iteration applies A once and A^T once; the loop runs without host
+ * synchronisation (optionally replayed as a CUDA graph).  The library
+ * allocates its workspace per call with stream-ordered allocation and frees
+ * it before returning. */
+
+typedef enum { CBCT_LAMBDA_FIXED = 0, CBCT_LAMBDA_GCV = 1 } cbct_lambda_rule;
+
+typedef struct {
+    int iters;               /* iterations (>= 1) */
+    double lambda;           /* Tikhonov lambda (Sec. 2.2, Eq. 6): damping of CGLS/LSQR/LSMR,
+                                or the fixed lambda of hybrid LSQR with CBCT_LAMBDA_FIXED */
+    cbct_lambda_rule rule;   /* hybrid LSQR only: fixed lambda or GCV (Sec. 2.2.2) */
+    cbct_dtype storage;      /* storage type of the Krylov vectors (u, v, basis V_k) */
+    int use_graph;           /* nonzero: capture one iteration as a CUDA graph and replay it */
+    int profile;             /* nonzero: time every projector launch with CUDA events (disables
+                                the graph) and fill the report's *_ms fields */
+} cbct_solve_opts;
+
+/* Per-iteration histories, written to caller-allocated HOST arrays of length
+ * >= opts->iters (any pointer may be NULL).  resid_norm: the solver's estimate
+ * of ||b - A x_k|| (of the damped residual when lambda > 0); normal_resid_norm:
+ * its estimate of ||A^T (b - A x_k) - lambda^2 x_k||; lambda_k: hybrid LSQR's
+ * lambda per iteration. */
+typedef struct {
+    int iters_done;
+    double *resid_norm;
+    double *normal_resid_norm;
+    double *lambda_k;
+    int64_t kernel_launches;     /* out: kernels this call launched (graph replays count each node) */
+    int64_t forward_launches;    /* out: forward-projector launches */
+    int64_t backward_launches;   /* out: backprojector launches */
+    double forward_ms;           /* out, profile != 0: summed device time of the forward launches */
+    double backward_ms;          /* out, profile != 0: summed device time of the backprojector launches */
+} cbct_solve_report;
+
+/* CGLS (Sec. 2.1.1, Eq. 3). */
+cbct_status cbct_cgls_solve(const cbct_geometry *geom, const float *b, float *x,
+                            const cbct_solve_opts *opts, cbct_solve_report *report,
+                            cbct_stream stream);
+/* LSQR (Sec. 2.1.2, Eq. 4): Golub-Kahan bidiagonalisation + Paige-Saunders recurrences. */
+cbct_status cbct_lsqr_solve(const cbct_geometry *geom, const float *b, float *x,
+                            const cbct_solve_opts *opts, cbct_solve_report *report,
+                            cbct_stream stream);
+/* LSMR (Sec. 2.1.3, Eq. 5; damped form of Sec. 2.2, Eq. 7 when lambda > 0). */
+cbct_status cbct_lsmr_solve(const cbct_geometry *geom, const float *b, float *x,
+                            const cbct_solve_opts *opts, cbct_solve_report *report,
+                            cbct_stream stream);
+/* Hybrid LSQR (Sec. 2.2.1, Eq. 8): Tikhonov on the projected problem with
+ * lambda_k fixed or chosen by GCV (Sec. 2.2.2).  Keeps the basis V_k on the
+ * device (iters + 1 volumes of the storage type). */
+cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *geom, const float *b, float *x,
+                                   const cbct_solve_opts *opts, cbct_solve_report *report,
+                                   cbct_stream stream);
+
+/* Message describing the calling thread's most recent error ("" if none). */
+const char *cbct_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBCT_H */

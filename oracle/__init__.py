@@ -71,7 +71,7 @@ def _load():
     lib.oracle_project_rays.restype = None
     lib.oracle_project.argtypes = [G, dp, dp, ctypes.c_int]
     lib.oracle_project.restype = None
-    lib.oracle_backproject.argtypes = [G, dp, dp]
+    lib.oracle_backproject.argtypes = [G, dp, dp, ctypes.c_int]
     lib.oracle_backproject.restype = None
     lib.oracle_nnz.argtypes = [G, ctypes.c_int]
     lib.oracle_nnz.restype = ctypes.c_int64
@@ -126,14 +126,14 @@ def project_rays(g, x, rays, nthreads: int = 0) -> np.ndarray:
     return out
 
 
-def backproject(g, y) -> np.ndarray:
-    """x = A^T y (explicit sequential scatter), x of shape (nz, ny, nx)."""
+def backproject(g, y, nthreads: int = 1) -> np.ndarray:
+    """x = A^T y (explicit scatter; sequential, or over `nthreads` ray chunks), shape (nz, ny, nx)."""
     lib = _load()
     s, keep = _geom(g)
     y = _f64(y).reshape(-1)
     assert y.size == g.num_rays
     x = np.empty(g.vol_shape, dtype=np.float64)
-    lib.oracle_backproject(ctypes.byref(s), _dptr(y), _dptr(x))
+    lib.oracle_backproject(ctypes.byref(s), _dptr(y), _dptr(x), int(nthreads))
     return x
 
 
@@ -193,7 +193,7 @@ class Operator:
         return project(self.g, x, self.nthreads).reshape(-1)
 
     def rmatvec(self, y):
-        return backproject(self.g, y).reshape(-1)
+        return backproject(self.g, y, self.nthreads or (os.cpu_count() or 1)).reshape(-1)
 
 
 class DenseOperator:

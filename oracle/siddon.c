@@ -193,17 +193,14 @@ void oracle_project(const og_geom *g, const double *x, double *y, int nthreads)
     oracle_project_rays(g, x, NULL, oracle_num_rays(g), y, nthreads);
 }
 
-/* x = A^T y as an explicit sequential scatter x[j] += l_ij y[i] over the rays in order. */
-void oracle_backproject(const og_geom *g, const double *y, double *x)
+/* Scatter x[j] += l_ij y[i] for rays [r0, r1) in order. */
+static void scatter_rays(const og_geom *g, const double *y, int64_t r0, int64_t r1, double *x)
 {
     int64_t cap = alpha_capacity(g);
-    int64_t nvox = (int64_t)g->nx * g->ny * g->nz;
     int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * cap);
     double *len = (double *)malloc(sizeof(double) * cap);
     double *alpha = (double *)malloc(sizeof(double) * cap);
-    memset(x, 0, sizeof(double) * nvox);
-    int64_t nr = oracle_num_rays(g);
-    for (int64_t r = 0; r < nr; ++r) {
+    for (int64_t r = r0; r < r1; ++r) {
         if (y[r] == 0.0) continue;
         int c = ray_segments(g, r, idx, len, alpha);
         for (int m = 0; m < c; ++m) x[idx[m]] += len[m] * y[r];
@@ -211,6 +208,37 @@ void oracle_backproject(const og_geom *g, const double *y, double *x)
     free(idx);
     free(len);
     free(alpha);
+}
+
+/*
+ * x = A^T y as an explicit scatter x[j] += l_ij y[i].  nthreads <= 1: one
+ * sequential pass over the rays in order.  nthreads > 1: the rays are cut
+ * into nthreads contiguous chunks, each scattered into its own zeroed volume,
+ * and the volumes are added in chunk order (the same sum, regrouped).
+ */
+void oracle_backproject(const og_geom *g, const double *y, double *x, int nthreads)
+{
+    int64_t nvox = (int64_t)g->nx * g->ny * g->nz;
+    int64_t nr = oracle_num_rays(g);
+    memset(x, 0, sizeof(double) * nvox);
+    if (nthreads <= 1) {
+        scatter_rays(g, y, 0, nr, x);
+        return;
+    }
+    double *part = (double *)calloc((size_t)nthreads * nvox, sizeof(double));
+#ifdef _OPENMP
+    omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(static, 1)
+    for (int t = 0; t < nthreads; ++t) {
+        int64_t r0 = nr * t / nthreads, r1 = nr * (t + 1) / nthreads;
+        scatter_rays(g, y, r0, r1, part + (size_t)t * nvox);
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        const double *pt = part + (size_t)t * nvox;
+        for (int64_t j = 0; j < nvox; ++j) x[j] += pt[j];
+    }
+    free(part);
 }
 
 /* Number of nonzero entries of A (positive-length ray/voxel pairs). */

@@ -1,0 +1,281 @@
+"""Python binding of libcbct.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/cbct.h; all
+computation happens in the library's CUDA kernels.  PyTorch provides device
+memory and the current stream.  There is no CPU fallback: if libcbct.so cannot
+be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcbct.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "cbct.h")
+
+CBCT_OK, CBCT_EINVAL, CBCT_ENOMEM, CBCT_ECUDA, CBCT_EBREAKDOWN, CBCT_ETIMEOUT, CBCT_EBUDGET, CBCT_ENOTFOUND = range(8)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBREAKDOWN", 5: "ETIMEOUT",
+                6: "EBUDGET", 7: "ENOTFOUND"}
+F32, F16, BF16 = 0, 1, 2
+LAMBDA_FIXED, LAMBDA_GCV = 0, 1
+
+
+class CbctError(RuntimeError):
+    def __init__(self, func, status, message):
+        super().__init__("%s failed: %s (%s)" % (func, STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("nu", ctypes.c_int), ("nv", ctypes.c_int),
+        ("du", ctypes.c_double), ("dv", ctypes.c_double),
+        ("dso", ctypes.c_double), ("dsd", ctypes.c_double),
+        ("nangles", ctypes.c_int), ("angles_rad", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("lam", ctypes.c_double), ("rule", ctypes.c_int),
+                ("storage", ctypes.c_int), ("use_graph", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int),
+                ("resid_norm", ctypes.POINTER(ctypes.c_double)),
+                ("normal_resid_norm", ctypes.POINTER(ctypes.c_double)),
+                ("lambda_k", ctypes.POINTER(ctypes.c_double)),
+                ("kernel_launches", ctypes.c_int64),
+                ("forward_launches", ctypes.c_int64),
+                ("backward_launches", ctypes.c_int64),
+                ("forward_ms", ctypes.c_double),
+                ("backward_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def declared_functions() -> list:
+    """Names of the functions include/cbct.h declares."""
+    text = open(HEADER_PATH).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cbct_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libcbct.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libcbct.so is not built (%s); run paper_2211_14212_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    G = ctypes.c_void_p
+    lib.cbct_geometry_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_void_p)]
+    lib.cbct_geometry_destroy.argtypes = [G]
+    lib.cbct_geometry_destroy.restype = None
+    lib.cbct_geometry_num_voxels.argtypes = [G]
+    lib.cbct_geometry_num_voxels.restype = i64
+    lib.cbct_geometry_num_rays.argtypes = [G]
+    lib.cbct_geometry_num_rays.restype = i64
+    for fn in ("cbct_project", "cbct_backproject"):
+        getattr(lib, fn).argtypes = [G, vp, vp, ctypes.c_int, vp]
+    lib.cbct_count_nnz.argtypes = [G, ctypes.POINTER(i64), vp]
+    for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve"):
+        getattr(lib, fn).argtypes = [G, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Report), vp]
+    lib.cbct_last_error.restype = ctypes.c_char_p
+    lib.cbct_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(func, status):
+    if status != CBCT_OK:
+        raise CbctError(func, status, load().cbct_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    codes = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
+    if t not in codes:
+        raise TypeError("unsupported dtype %s" % t)
+    return codes[t]
+
+
+STORAGE = {"f32": F32, "f16": F16, "bf16": BF16, F32: F32, F16: F16, BF16: BF16}
+
+
+class Geometry:
+    """Device-side scan geometry (cbct_geometry_create / _destroy).
+
+    Accepts the scan parameters as keywords or any object carrying them as
+    attributes (nx, ny, nz, dx, dy, dz, nu, nv, du, dv, dso, dsd, angles).
+    """
+
+    FIELDS = ("nx", "ny", "nz", "dx", "dy", "dz", "nu", "nv", "du", "dv", "dso", "dsd")
+
+    def __init__(self, spec=None, **kw):
+        if spec is not None:
+            kw = {f: getattr(spec, f) for f in self.FIELDS + ("angles",)}
+        self.params = kw
+        self.angles = np.ascontiguousarray(np.asarray(kw["angles"], dtype=np.float64))
+        lib = load()
+        d = _Desc(int(kw["nx"]), int(kw["ny"]), int(kw["nz"]), float(kw["dx"]), float(kw["dy"]), float(kw["dz"]),
+                  int(kw["nu"]), int(kw["nv"]), float(kw["du"]), float(kw["dv"]), float(kw["dso"]), float(kw["dsd"]),
+                  int(self.angles.shape[0]), self.angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        h = ctypes.c_void_p()
+        _check("cbct_geometry_create", lib.cbct_geometry_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.num_voxels = int(lib.cbct_geometry_num_voxels(h))
+        self.num_rays = int(lib.cbct_geometry_num_rays(h))
+        self.vol_shape = (int(kw["nz"]), int(kw["ny"]), int(kw["nx"]))
+        self.proj_shape = (int(self.angles.shape[0]), int(kw["nv"]), int(kw["nu"]))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().cbct_geometry_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _require_cuda(t, name, numel):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+
+
+def project(geom: Geometry, x, out=None, stream=None):
+    """y = A x on the GPU (cbct_project); x and y share one dtype (f32/f16/bf16)."""
+    import torch
+    _require_cuda(x, "x", geom.num_voxels)
+    if out is None:
+        out = torch.empty(geom.proj_shape, dtype=x.dtype, device=x.device)
+    _require_cuda(out, "out", geom.num_rays)
+    if out.dtype != x.dtype:
+        raise TypeError("x and out must share a dtype")
+    _check("cbct_project", load().cbct_project(geom.handle, ctypes.c_void_p(x.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()), _dtype_code(x.dtype),
+                                               _stream_handle(stream)))
+    return out
+
+
+def backproject(geom: Geometry, y, out=None, stream=None):
+    """x = A^T y on the GPU (cbct_backproject), the exact transpose of project()."""
+    import torch
+    _require_cuda(y, "y", geom.num_rays)
+    if out is None:
+        out = torch.empty(geom.vol_shape, dtype=y.dtype, device=y.device)
+    _require_cuda(out, "out", geom.num_voxels)
+    if out.dtype != y.dtype:
+        raise TypeError("y and out must share a dtype")
+    _check("cbct_backproject", load().cbct_backproject(geom.handle, ctypes.c_void_p(y.data_ptr()),
+                                                       ctypes.c_void_p(out.data_ptr()), _dtype_code(y.dtype),
+                                                       _stream_handle(stream)))
+    return out
+
+
+def count_nnz(geom: Geometry, stream=None) -> int:
+    n = ctypes.c_int64()
+    _check("cbct_count_nnz", load().cbct_count_nnz(geom.handle, ctypes.byref(n), _stream_handle(stream)))
+    return int(n.value)
+
+
+@dataclass
+class SolveReport:
+    iters_done: int
+    resid: np.ndarray
+    normal_resid: np.ndarray
+    lam: np.ndarray = field(default=None)
+    kernel_launches: int = 0
+    forward_launches: int = 0
+    backward_launches: int = 0
+    forward_ms: float = 0.0
+    backward_ms: float = 0.0
+
+
+def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=True, x=None, stream=None,
+           profile=False):
+    """Run one of the C-ABI solvers.  b/x may be CUDA tensors or host (numpy or
+    CPU torch, FP32) buffers; host buffers are staged by the library."""
+    import torch
+    lib = load()
+    on_device = isinstance(b, torch.Tensor) and b.is_cuda
+    if on_device:
+        _require_cuda(b, "b", geom.num_rays)
+        if b.dtype != torch.float32:
+            raise TypeError("b must be float32")
+        if x is None:
+            x = torch.empty(geom.vol_shape, dtype=torch.float32, device=b.device)
+        _require_cuda(x, "x", geom.num_voxels)
+        bptr, xptr = b.data_ptr(), x.data_ptr()
+    else:
+        bh = b.numpy() if isinstance(b, torch.Tensor) else np.asarray(b)
+        if bh.dtype != np.float32 or not bh.flags.c_contiguous or bh.size != geom.num_rays:
+            raise TypeError("host b must be a contiguous float32 array of %d elements" % geom.num_rays)
+        if x is None:
+            x = np.empty(geom.vol_shape, dtype=np.float32)
+        xh = x.numpy() if isinstance(x, torch.Tensor) else x
+        if xh.dtype != np.float32 or not xh.flags.c_contiguous or xh.size != geom.num_voxels:
+            raise TypeError("host x must be a contiguous float32 array of %d elements" % geom.num_voxels)
+        bptr, xptr = bh.ctypes.data, xh.ctypes.data
+    rule_code = {"fixed": LAMBDA_FIXED, "gcv": LAMBDA_GCV}[rule] if isinstance(rule, str) else int(rule)
+    opts = _Opts(int(iters), float(lam), rule_code, STORAGE[storage], 1 if use_graph else 0, 1 if profile else 0)
+    hr = np.zeros(iters, dtype=np.float64)
+    hn = np.zeros(iters, dtype=np.float64)
+    hl = np.zeros(iters, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rep = _Report(0, hr.ctypes.data_as(dp), hn.ctypes.data_as(dp), hl.ctypes.data_as(dp))
+    st = getattr(lib, fn)(geom.handle, ctypes.c_void_p(bptr), ctypes.c_void_p(xptr), ctypes.byref(opts),
+                          ctypes.byref(rep), _stream_handle(stream))
+    _check(fn, st)
+    k = rep.iters_done
+    return x, SolveReport(k, hr[:k].copy(), hn[:k].copy(), hl[:k].copy(), int(rep.kernel_launches),
+                          int(rep.forward_launches), int(rep.backward_launches), float(rep.forward_ms),
+                          float(rep.backward_ms))
+
+
+def cgls(geom, b, iters, lam=0.0, **kw):
+    """CGLS (Sec. 2.1.1), optionally damped (Eq. 7)."""
+    return _solve("cbct_cgls_solve", geom, b, iters, lam=lam, **kw)
+
+
+def lsqr(geom, b, iters, lam=0.0, **kw):
+    """LSQR (Sec. 2.1.2), optionally damped (Eq. 7)."""
+    return _solve("cbct_lsqr_solve", geom, b, iters, lam=lam, **kw)
+
+
+def lsmr(geom, b, iters, lam=0.0, **kw):
+    """LSMR (Sec. 2.1.3), optionally damped (Eq. 7)."""
+    return _solve("cbct_lsmr_solve", geom, b, iters, lam=lam, **kw)
+
+
+def hybrid_lsqr(geom, b, iters, rule="gcv", lam=0.0, **kw):
+    """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lambda_k fixed or by GCV (Sec. 2.2.2)."""
+    return _solve("cbct_hybrid_lsqr_solve", geom, b, iters, lam=lam, rule=rule, **kw)

@@ -1,0 +1,135 @@
+// Shared device-side definitions of the cone-beam library: the geometry as the
+// kernels see it, storage-type conversions and error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/cbct.h"
+
+namespace cbct {
+
+// ---------------------------------------------------------------- geometry
+//
+// Every ray is parametrised by alpha along d' = (pixel - source), with alpha = 0
+// where the ray crosses the plane through the rotation axis parallel to the
+// detector (so alpha stays small, |alpha| < ~0.2, inside the volume; the source
+// is at alpha = -dso/dsd, the pixel at 1 - dso/dsd).  The alpha at which ray
+// (a, iv, iu) crosses plane p of an axis is an affine function of p:
+//     alpha_x(p) = fma(p, Ax, Bx)   with (Ax, Bx, Ay, By) = ray_xy[a][iu]
+//     alpha_z(p) = fma(p, Az, Bz)   with (Az, Bz)         = ray_z[iv]
+// (x and y depend only on (angle, u); z only on v).  A == 0 marks a ray exactly
+// parallel to that axis' planes; B then holds the (fixed) voxel index on that
+// axis as a float.  The length of ray/voxel segment [alpha0, alpha1] is
+// (alpha1 - alpha0) * ray_len[iv][iu].
+//
+// Forward and transposed kernels derive every alpha from these tables with
+// the same single fma, so the segment lengths they use are bit-identical and
+// A^T is the exact transpose of A up to the order of the FP32 sums.
+struct DevGeom {
+    int nx, ny, nz;
+    int nu, nv, nangles;
+    float dso, dsd;          // mm
+    float du, dv;            // mm
+    float bx0, by0, bz0;     // lower corner of the volume, mm
+    float dx, dy, dz;        // voxel size, mm
+    const float4 *ray_xy;    // [nangles][nu]
+    const float2 *ray_z;     // [nv]
+    const float *ray_len;    // [nv][nu]
+    const float2 *trig;      // [nangles] (cos t, sin t), for footprint windows only
+};
+
+}  // namespace cbct
+
+struct cbct_geometry {
+    cbct::DevGeom dev;
+    cbct_geometry_desc desc;     // angles_rad points at `angles`
+    double *angles;              // host copy
+    int device;                  // CUDA device the tables live on
+    void *table_mem;             // one device allocation holding all tables
+};
+
+namespace cbct {
+
+// ------------------------------------------------------------- storage types
+template <typename T> struct Storage;
+template <> struct Storage<float> {
+    __device__ __forceinline__ static float load(const float *p) { return __ldg(p); }
+    __device__ __forceinline__ static float ld_plain(const float *p) { return *p; }
+    __device__ __forceinline__ static float round(float v) { return v; }
+    __device__ __forceinline__ static void store(float *p, float v) { *p = v; }
+};
+template <> struct Storage<__half> {
+    __device__ __forceinline__ static float load(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ __forceinline__ static float ld_plain(const __half *p) { return __half2float(*p); }
+    __device__ __forceinline__ static float round(float v) { return __half2float(__float2half_rn(v)); }
+    __device__ __forceinline__ static void store(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Storage<__nv_bfloat16> {
+    __device__ __forceinline__ static float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ __forceinline__ static float ld_plain(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    __device__ __forceinline__ static float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    __device__ __forceinline__ static void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+inline size_t dtype_size(cbct_dtype t) { return t == CBCT_F32 ? 4 : 2; }
+
+// ------------------------------------------------- projector epilogue scalars
+//
+// The fused epilogues compute out = a * (A x) + b * out_old (or the A^T
+// analogue).  a and b are FP64 values read from device memory (written by the
+// previous solver kernel) or given directly; a null pointer means the
+// immediate value.  out_old is read from `old` when set (an input buffer
+// distinct from the output), else from the output buffer itself.  `partial`, when non-null, receives one FP64 sum of
+// squares of the stored outputs per thread block, reduced later in a fixed
+// order (deterministic norms).
+struct Epilogue {
+    const double *a_ptr;
+    const double *b_ptr;
+    double a_val, b_val;
+    double *partial;
+    const int *stop;         // when non-null and *stop != 0, the launch does nothing
+    const void *old;         // where out_old is read (same storage type); null = the output itself
+};
+
+__device__ __forceinline__ double epi_a(const Epilogue &e) { return e.a_ptr ? *e.a_ptr : e.a_val; }
+__device__ __forceinline__ double epi_b(const Epilogue &e) { return e.b_ptr ? *e.b_ptr : e.b_val; }
+
+// Deterministic block reduction of one double per thread into thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *scratch /* NT/32 doubles */) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < NT / 32; ++w) s += scratch[w];
+    }
+    __syncthreads();
+    return s;
+}
+
+// ---------------------------------------------------------------- host side
+void set_error(const std::string &msg);
+cbct_status cuda_fail(cudaError_t err, const char *what);
+
+#define CBCT_CUDA_TRY(expr)                                     \
+    do {                                                        \
+        cudaError_t err__ = (expr);                             \
+        if (err__ != cudaSuccess) return ::cbct::cuda_fail(err__, #expr); \
+    } while (0)
+
+// Kernel launchers (projector.cu).  All return CBCT_OK or a CUDA failure.
+cbct_status launch_forward(const DevGeom &g, const void *x, void *y, cbct_dtype t,
+                           const Epilogue &epi, cudaStream_t s);
+cbct_status launch_backward(const DevGeom &g, const void *y, void *x, cbct_dtype t,
+                            const Epilogue &epi, cudaStream_t s);
+cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaStream_t s);
+int forward_num_blocks(const DevGeom &g);
+int backward_num_blocks(const DevGeom &g);
+
+}  // namespace cbct

@@ -1,0 +1,160 @@
+// Geometry handle: validation, FP64 construction of the per-ray alpha tables,
+// and the error plumbing shared by every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cbct {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+cbct_status cuda_fail(cudaError_t err, const char *what) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s", (int)err, cudaGetErrorString(err), what);
+    set_error(buf);
+    (void)cudaGetLastError();   // clear a sticky launch error so the next call is not blamed
+    return err == cudaErrorMemoryAllocation ? CBCT_ENOMEM : CBCT_ECUDA;
+}
+
+static cbct_status invalid(const char *msg) {
+    set_error(msg);
+    return CBCT_EINVAL;
+}
+
+// Affine map plane index -> alpha for one axis of one ray: alpha(p) = p*A + B,
+// from the ray origin q (alpha = 0) and direction component d along the axis.
+static void axis_map(double q, double d, double b0, double delta, int n, float *A, float *B) {
+    // exactly parallel rays keep a fixed voxel index (half-open voxels: floor)
+    if (d == 0.0) {
+        *A = 0.0f;
+        double idx = std::floor((q - b0) / delta);
+        if (idx < -1.0) idx = -1.0;
+        if (idx > (double)n) idx = (double)n;
+        *B = (float)idx;
+        return;
+    }
+    *A = (float)(delta / d);
+    *B = (float)((b0 - q) / d);
+}
+
+}  // namespace cbct
+
+using namespace cbct;
+
+extern "C" const char *cbct_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_geometry **out) {
+    if (!d || !out) return invalid("cbct_geometry_create: null argument");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nu < 1 || d->nv < 1 || d->nangles < 1)
+        return invalid("cbct_geometry_create: every count must be >= 1");
+    if (!(d->dx > 0 && d->dy > 0 && d->dz > 0 && d->du > 0 && d->dv > 0))
+        return invalid("cbct_geometry_create: voxel and pixel sizes must be > 0");
+    if (!(d->dso > 0 && d->dsd > d->dso))
+        return invalid("cbct_geometry_create: need 0 < dso < dsd");
+    if (!d->angles_rad) return invalid("cbct_geometry_create: angles_rad is null");
+    const double hx = 0.5 * d->nx * d->dx, hy = 0.5 * d->ny * d->dy;
+    const double rcyl = std::sqrt(hx * hx + hy * hy);
+    if (!(d->dso > rcyl) || !(d->dsd - d->dso > rcyl))
+        return invalid("cbct_geometry_create: source and detector must lie outside the volume's circumscribed cylinder");
+    // index ranges: voxels addressed with int32, rays with int64
+    if ((int64_t)d->nx * d->ny * d->nz >= (int64_t)1 << 31)
+        return invalid("cbct_geometry_create: more than 2^31-1 voxels");
+    if ((int64_t)d->nu * d->nv >= (int64_t)1 << 31)
+        return invalid("cbct_geometry_create: more than 2^31-1 pixels per projection");
+    if (d->nangles > 65535 || d->nv > 65535 * 4)
+        return invalid("cbct_geometry_create: more than 65535 angles");
+    for (int a = 0; a < d->nangles; ++a)
+        if (!std::isfinite(d->angles_rad[a])) return invalid("cbct_geometry_create: non-finite angle");
+
+    const int nx = d->nx, ny = d->ny, nz = d->nz, nu = d->nu, nv = d->nv, na = d->nangles;
+    const double dsd = d->dsd, m = d->dso / d->dsd;
+    const double bx0 = -0.5 * nx * d->dx, by0 = -0.5 * ny * d->dy, bz0 = -0.5 * nz * d->dz;
+
+    std::vector<float4> xy((size_t)na * nu);
+    std::vector<float2> zt(nv);
+    std::vector<float> len((size_t)nv * nu);
+    std::vector<float2> trig(na);
+    for (int a = 0; a < na; ++a) {
+        const double ct = std::cos(d->angles_rad[a]), st = std::sin(d->angles_rad[a]);
+        trig[a] = make_float2((float)ct, (float)st);
+        for (int iu = 0; iu < nu; ++iu) {
+            const double u = (iu - 0.5 * (nu - 1)) * d->du;
+            // rotated frame: source (dso, 0), pixel (dso - dsd, u); world = R(t) * frame
+            const double dxw = -dsd * ct - u * st, dyw = -dsd * st + u * ct;
+            const double qx = -u * m * st, qy = u * m * ct;
+            float4 e;
+            axis_map(qx, dxw, bx0, d->dx, nx, &e.x, &e.y);
+            axis_map(qy, dyw, by0, d->dy, ny, &e.z, &e.w);
+            xy[(size_t)a * nu + iu] = e;
+        }
+    }
+    for (int iv = 0; iv < nv; ++iv) {
+        const double v = (iv - 0.5 * (nv - 1)) * d->dv;
+        float2 e;
+        axis_map(v * m, v, bz0, d->dz, nz, &e.x, &e.y);
+        zt[iv] = e;
+        for (int iu = 0; iu < nu; ++iu) {
+            const double u = (iu - 0.5 * (nu - 1)) * d->du;
+            len[(size_t)iv * nu + iu] = (float)std::sqrt(dsd * dsd + u * u + v * v);
+        }
+    }
+
+    cbct_geometry *g = new (std::nothrow) cbct_geometry();
+    if (!g) { set_error("cbct_geometry_create: out of host memory"); return CBCT_ENOMEM; }
+    g->angles = new (std::nothrow) double[na];
+    if (!g->angles) { delete g; set_error("cbct_geometry_create: out of host memory"); return CBCT_ENOMEM; }
+    std::memcpy(g->angles, d->angles_rad, sizeof(double) * na);
+    g->desc = *d;
+    g->desc.angles_rad = g->angles;
+
+    auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t s_xy = align(xy.size() * sizeof(float4)), s_z = align(zt.size() * sizeof(float2));
+    const size_t s_len = align(len.size() * sizeof(float)), s_tr = align(trig.size() * sizeof(float2));
+    cudaError_t err = cudaGetDevice(&g->device);
+    char *mem = nullptr;
+    if (err == cudaSuccess) err = cudaMalloc(&mem, s_xy + s_z + s_len + s_tr);
+    if (err == cudaSuccess) err = cudaMemcpy(mem, xy.data(), xy.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(mem + s_xy, zt.data(), zt.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(mem + s_xy + s_z, len.data(), len.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(mem + s_xy + s_z + s_len, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        if (mem) cudaFree(mem);
+        delete[] g->angles;
+        delete g;
+        return cuda_fail(err, "cbct_geometry_create");
+    }
+    g->table_mem = mem;
+    DevGeom &dg = g->dev;
+    dg.nx = nx; dg.ny = ny; dg.nz = nz; dg.nu = nu; dg.nv = nv; dg.nangles = na;
+    dg.dso = (float)d->dso; dg.dsd = (float)d->dsd; dg.du = (float)d->du; dg.dv = (float)d->dv;
+    dg.bx0 = (float)bx0; dg.by0 = (float)by0; dg.bz0 = (float)bz0;
+    dg.dx = (float)d->dx; dg.dy = (float)d->dy; dg.dz = (float)d->dz;
+    dg.ray_xy = reinterpret_cast<const float4 *>(mem);
+    dg.ray_z = reinterpret_cast<const float2 *>(mem + s_xy);
+    dg.ray_len = reinterpret_cast<const float *>(mem + s_xy + s_z);
+    dg.trig = reinterpret_cast<const float2 *>(mem + s_xy + s_z + s_len);
+    *out = g;
+    return CBCT_OK;
+}
+
+extern "C" void cbct_geometry_destroy(cbct_geometry *g) {
+    if (!g) return;
+    if (g->table_mem) cudaFree(g->table_mem);
+    delete[] g->angles;
+    delete g;
+}
+
+extern "C" int64_t cbct_geometry_num_voxels(const cbct_geometry *g) {
+    return g ? (int64_t)g->dev.nx * g->dev.ny * g->dev.nz : -1;
+}
+
+extern "C" int64_t cbct_geometry_num_rays(const cbct_geometry *g) {
+    return g ? (int64_t)g->dev.nangles * g->dev.nv * g->dev.nu : -1;
+}

@@ -1,0 +1,199 @@
+// Building blocks shared by the Krylov solver drivers: deterministic FP64
+// reductions, Givens rotations, storage scaling, workspace and iteration
+// replay (optionally as a CUDA graph).
+#pragma once
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cbct {
+
+constexpr int VEC_THREADS = 256;
+constexpr int VEC_BLOCKS = 152 * 4;     // fixed grid: fixed partial layout, deterministic sums
+constexpr int RED_THREADS = 256;
+
+// Sum of n partials in a fixed order (thread t takes t, t+256, ...; then the
+// block tree), result valid in thread 0.  Launch with RED_THREADS threads.
+__device__ __forceinline__ double reduce_partials(const double *p, int n, double *scratch) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += RED_THREADS) s += p[i];
+    return block_sum<RED_THREADS>(s, scratch);
+}
+
+// Givens rotation (c, s, r): [c s; -s c] [a; b] = [r; 0], r = hypot(a, b) >= 0.
+struct Rot { double c, s, r; };
+__device__ __forceinline__ Rot givens(double a, double b) {
+    const double r = hypot(a, b);
+    if (r == 0.0) return Rot{1.0, 0.0, 0.0};
+    return Rot{a / r, b / r, r};
+}
+
+// Storage scale for a vector about to be written: FP16 storage keeps the
+// entries near unit RMS (stored = scale x true vector, scale a power of two
+// predicted from the previous norm) so that they stay clear of FP16
+// subnormals and overflow; FP32/BF16 keep scale 1.
+__device__ __forceinline__ double storage_scale(int scaled, double sqrt_len, double norm_pred) {
+    if (!scaled || !(norm_pred > 0.0) || !isfinite(norm_pred)) return 1.0;
+    double e = rint(log2(sqrt_len / norm_pred));
+    e = fmax(-60.0, fmin(60.0, e));
+    return exp2(e);
+}
+
+__device__ __forceinline__ bool good(double v) { return v > 0.0 && isfinite(v); }
+
+// -------------------------------------------------------------- vector kernels
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_sumsq(const T *__restrict__ x, int64_t n, double *partial) {
+    __shared__ double red[VEC_THREADS / 32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        const double v = (double)Storage<T>::ld_plain(x + i);
+        s += v * v;
+    }
+    s = block_sum<VEC_THREADS>(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// dst = coef * src, converting FP32 -> storage type.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_scale_to(const float *__restrict__ src, T *__restrict__ dst, int64_t n, const double *coef, const int *stop) {
+    if (stop && *stop) return;
+    const float c = (float)*coef;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS)
+        Storage<T>::store(dst + i, c * src[i]);
+}
+
+// Combine a basis: x[m] = sum_j coef[j] * basis_j[m], basis_j = basis + j * n.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_combine(const T *__restrict__ basis, const double *__restrict__ coef, int k, int64_t n, float *__restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        double acc = 0.0;
+        for (int j = 0; j < k; ++j) acc += coef[j] * (double)Storage<T>::ld_plain(basis + (size_t)j * n + i);
+        x[i] = (float)acc;
+    }
+}
+
+// --------------------------------------------------------------- host helpers
+
+// Stream-ordered workspace: every allocation is freed on the stream at scope exit.
+struct Workspace {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Workspace(cudaStream_t st) : s(st) {}
+    ~Workspace() {
+        for (void *p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    cudaError_t alloc(T **p, size_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 16, s);
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *p = (T *)q;
+        return e;
+    }
+};
+
+inline bool is_device_pointer(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// Launch accounting of one solver call: kernel counts and, in profiling
+// mode, a CUDA event pair around every projector launch.
+struct Tracker {
+    bool profile = false;
+    cudaStream_t s = nullptr;
+    int64_t launches = 0, fwd = 0, bwd = 0;
+    std::vector<cudaEvent_t> ev[2];         // [0] forward, [1] backward: start, end, start, end, ...
+    ~Tracker() {
+        for (auto &v : ev)
+            for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+    cbct_status mark(int kind) {
+        if (!profile) return CBCT_OK;
+        cudaEvent_t e;
+        CBCT_CUDA_TRY(cudaEventCreate(&e));
+        ev[kind].push_back(e);
+        CBCT_CUDA_TRY(cudaEventRecord(e, s));
+        return CBCT_OK;
+    }
+    // counts only (events are owned by this tracker)
+    Tracker snapshot() const {
+        Tracker t;
+        t.launches = launches;
+        t.fwd = fwd;
+        t.bwd = bwd;
+        return t;
+    }
+    // a graph captured the launches made since `before` once and replayed them `replays` times
+    void scale_since(const Tracker &before, int replays) {
+        if (replays <= 1) return;
+        launches = before.launches + (launches - before.launches) * replays;
+        fwd = before.fwd + (fwd - before.fwd) * replays;
+        bwd = before.bwd + (bwd - before.bwd) * replays;
+    }
+    // after the stream has been synchronised
+    void fill(cbct_solve_report *rep) {
+        if (!rep) return;
+        rep->kernel_launches = launches;
+        rep->forward_launches = fwd;
+        rep->backward_launches = bwd;
+        double ms[2] = {0.0, 0.0};
+        for (int k = 0; k < 2; ++k)
+            for (size_t i = 0; i + 1 < ev[k].size(); i += 2) {
+                float t = 0.0f;
+                if (cudaEventElapsedTime(&t, ev[k][i], ev[k][i + 1]) == cudaSuccess) ms[k] += t;
+            }
+        rep->forward_ms = ms[0];
+        rep->backward_ms = ms[1];
+    }
+};
+
+// Enqueue one iteration `iters` times; with use_graph (and a capturable
+// stream), capture it once as a CUDA graph and replay the graph.  *replays
+// is set to the number of graph launches (0 without a graph).
+template <typename F>
+cbct_status run_iterations(int iters, bool use_graph, cudaStream_t s, F &&enqueue_one, int *replays) {
+    *replays = 0;
+    if (iters <= 0) return CBCT_OK;
+    if (!use_graph || s == nullptr || iters < 2) {
+        for (int i = 0; i < iters; ++i) {
+            cbct_status st = enqueue_one();
+            if (st != CBCT_OK) return st;
+        }
+        return CBCT_OK;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CBCT_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cbct_status st = enqueue_one();
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != CBCT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    for (int i = 0; i < iters && e == cudaSuccess; ++i) {
+        e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) ++*replays;
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize");
+    return CBCT_OK;
+}
+
+}  // namespace cbct

@@ -1,0 +1,758 @@
+// Krylov least-squares solvers on the GPU: CGLS (Sec. 2.1.1), LSQR (Sec. 2.1.2),
+// LSMR (Sec. 2.1.3), all optionally damped by a Tikhonov lambda (Sec. 2.2,
+// Eqs. 6-7), and hybrid LSQR with a per-iteration lambda_k (Sec. 2.2.1-2.2.2).
+//
+// Vectors live on the device in FP32 (x and the search directions) or in the
+// chosen storage type (the Golub-Kahan vectors u, v and the basis V_k).  All
+// scalars (norms, rotations, coefficients) are FP64 and are produced by
+// single-block "finalize" kernels that reduce per-block partial sums in a fixed
+// order.  Nothing returns to the host inside the iteration loop, so one
+// iteration can be captured as a CUDA graph and replayed.
+//
+// Golub-Kahan vectors are stored unnormalised and, for FP16, multiplied by a
+// power-of-two scale: U = su * beta_i u_i and V = sv * alpha_i v_i.  The scale
+// factors and norms enter the coefficients of the next fused epilogue, so no
+// separate normalisation pass over the vectors is needed.
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "solver_common.cuh"
+
+namespace cbct {
+
+cbct_status launch_projected_solve(const double *alphas, const double *betas, const double *scales,
+                                   const int *iter, const int *stop, int rule, double lambda_fixed,
+                                   double *work, int kmax, double *coef, double *hist_lambda,
+                                   double *hist_resid, cudaStream_t s);
+
+// ===================================================================== LSQR / LSMR
+//
+// Golub-Kahan bidiagonalisation (Sec. 2.1.2):
+//   beta_1 u_1 = b,  alpha_1 v_1 = A^T u_1,
+//   beta_{i+1} u_{i+1} = A v_i - alpha_i u_i,
+//   alpha_{i+1} v_{i+1} = A^T u_{i+1} - beta_{i+1} v_i.
+
+struct GkState {
+    // bidiagonalisation
+    double alpha, beta;          // current alpha_i, beta_i (true values)
+    double su, sv;               // storage scales of U and V
+    double su_next, sv_next;     // scales chosen for the next U / V
+    double fa, fb;               // forward epilogue:  U <- fa * A V + fb * U
+    double ba, bb;               // backward epilogue: V <- ba * A^T U + bb * V
+    double c0;                   // U = c0 * b at the start; later the first update coefficient
+    double damp;                 // Tikhonov lambda
+    double sqrt_n, sqrt_m;
+    // LSQR
+    double rhobar, phibar, psisq;
+    // LSMR
+    double alphabar, zetabar, rho, rhobar_m, cbar, sbar;
+    double betadd, betad, rhod, tautilde, thetatilde, zeta, dsum;
+    // vector update coefficients
+    double k1, k2, k3, k4;
+    int iter, stop, status, scaled;
+};
+
+enum Method { M_LSQR = 0, M_LSMR = 1, M_HYBRID = 2 };
+
+// After ||b||^2: beta_1, the scale of U and the first backprojection's coefficients.
+__global__ void __launch_bounds__(RED_THREADS) gk_begin(GkState *st, const double *part, int np) {
+    __shared__ double red[RED_THREADS / 32];
+    const double ss = reduce_partials(part, np, red);
+    if (threadIdx.x) return;
+    const double beta = sqrt(ss);
+    st->iter = 0;
+    st->status = CBCT_OK;
+    st->stop = 0;
+    if (!good(beta)) {                          // b = 0: x = 0 is the solution
+        st->stop = 1;
+        st->status = beta == 0.0 ? CBCT_OK : CBCT_EBREAKDOWN;
+        return;
+    }
+    st->beta = beta;
+    st->su = storage_scale(st->scaled, st->sqrt_n, beta);
+    st->c0 = st->su;
+    st->sv_next = 1.0;
+    st->ba = st->sv_next / (st->su * beta);
+    st->bb = 0.0;
+}
+
+// After A^T u_1: alpha_1, start values of the method's recurrences.
+__global__ void __launch_bounds__(RED_THREADS) gk_begin2(GkState *st, const double *part, int np, int method) {
+    __shared__ double red[RED_THREADS / 32];
+    if (st->stop) return;
+    const double ss = reduce_partials(part, np, red);
+    if (threadIdx.x) return;
+    const double alpha = sqrt(ss) / st->sv_next;
+    if (!good(alpha)) {                         // A^T b = 0: x = 0 is the least-squares solution
+        st->stop = 1;
+        st->status = alpha == 0.0 ? CBCT_OK : CBCT_EBREAKDOWN;
+        return;
+    }
+    st->sv = st->sv_next;
+    st->alpha = alpha;
+    st->c0 = 1.0 / (st->sv * alpha);            // w_1 = v_1 (LSQR), h_1 = v_1 (LSMR)
+    if (method == M_LSQR) {
+        st->rhobar = alpha;
+        st->phibar = st->beta;
+        st->psisq = 0.0;
+    } else if (method == M_LSMR) {
+        st->alphabar = alpha;
+        st->zetabar = alpha * st->beta;
+        st->rho = 1.0;
+        st->rhobar_m = 1.0;
+        st->cbar = 1.0;
+        st->sbar = 0.0;
+        st->betadd = st->beta;
+        st->betad = 0.0;
+        st->rhod = 1.0;
+        st->tautilde = 0.0;
+        st->thetatilde = 0.0;
+        st->zeta = 0.0;
+        st->dsum = 0.0;
+    }
+    st->su_next = storage_scale(st->scaled, st->sqrt_n, st->beta);
+    st->fa = st->su_next / (st->sv * st->alpha);
+    st->fb = -st->su_next * st->alpha / (st->su * st->beta);
+}
+
+// After U <- A v_i - alpha_i u_i: beta_{i+1} and the backprojection's coefficients.
+__global__ void __launch_bounds__(RED_THREADS) gk_after_forward(GkState *st, const double *part, int np,
+                                                                double *beta_arr) {
+    __shared__ double red[RED_THREADS / 32];
+    if (st->stop) return;
+    const double ss = reduce_partials(part, np, red);
+    if (threadIdx.x) return;
+    const double beta = sqrt(ss) / st->su_next;
+    if (!good(beta)) {
+        st->stop = 1;
+        st->status = CBCT_EBREAKDOWN;
+        return;
+    }
+    st->su = st->su_next;
+    st->beta = beta;
+    if (beta_arr) beta_arr[st->iter + 1] = beta;
+    st->sv_next = storage_scale(st->scaled, st->sqrt_m, st->alpha);
+    st->ba = st->sv_next / (st->su * beta);
+    st->bb = -st->sv_next * beta / (st->sv * st->alpha);
+}
+
+// After V <- A^T u_{i+1} - beta_{i+1} v_i: alpha_{i+1}, the method's rotations,
+// the vector-update coefficients and the next forward's coefficients.
+__global__ void __launch_bounds__(RED_THREADS) gk_after_backward(GkState *st, const double *part, int np,
+                                                                 int method, double *hist_r, double *hist_n,
+                                                                 double *alpha_arr, double *scale_arr, int cap) {
+    __shared__ double red[RED_THREADS / 32];
+    if (st->stop) return;
+    const double ss = reduce_partials(part, np, red);
+    if (threadIdx.x) return;
+    const double alpha = sqrt(ss) / st->sv_next;
+    if (!good(alpha)) {
+        st->stop = 1;
+        st->status = CBCT_EBREAKDOWN;
+        return;
+    }
+    const double beta = st->beta;
+    const int it = st->iter;
+    if (method == M_LSQR) {
+        // rotation eliminating the damping, then the one eliminating beta_{i+1}
+        const Rot r1 = givens(st->rhobar, st->damp);
+        const double psi = r1.s * st->phibar;
+        const double phibar1 = r1.c * st->phibar;
+        st->psisq += psi * psi;
+        const Rot r2 = givens(r1.r, beta);
+        const double theta = r2.s * alpha;
+        st->rhobar = -r2.c * alpha;
+        const double phi = r2.c * phibar1;
+        st->phibar = r2.s * phibar1;
+        st->k1 = phi / r2.r;                        // x += k1 w
+        st->k2 = 1.0 / (st->sv_next * alpha);       // w = k2 V + k3 w
+        st->k3 = -theta / r2.r;
+        if (it < cap) {
+            hist_r[it] = sqrt(st->phibar * st->phibar + st->psisq);
+            hist_n[it] = fabs(st->phibar * alpha * r2.c);
+        }
+    } else if (method == M_LSMR) {
+        const Rot rh = givens(st->alphabar, st->damp);        // P-hat_k
+        const double rho_prev = st->rho;
+        const Rot rk = givens(rh.r, beta);                     // P_k
+        const double theta_next = rk.s * alpha;
+        st->alphabar = rk.c * alpha;
+        st->rho = rk.r;
+        const double rhobar_prev = st->rhobar_m;               // P-bar_k
+        const double zeta_prev = st->zeta;
+        const double thetabar = st->sbar * rk.r;
+        const Rot rb = givens(st->cbar * rk.r, theta_next);
+        st->cbar = rb.c;
+        st->sbar = rb.s;
+        st->rhobar_m = rb.r;
+        st->zeta = rb.c * st->zetabar;
+        st->zetabar = -rb.s * st->zetabar;
+        st->k1 = thetabar * rk.r / (rho_prev * rhobar_prev);  // hbar = h - k1 hbar
+        st->k2 = st->zeta / (rk.r * rb.r);                    // x += k2 hbar
+        st->k3 = 1.0 / (st->sv_next * alpha);                 // h = k3 V + k4 h
+        st->k4 = -theta_next / rk.r;
+        // ||r_k|| estimate: rotations Q-hat_k, Q_k applied to (beta-double-dot, 0), then Q-tilde_{k-1}
+        const double betaacute = rh.c * st->betadd;
+        const double betacheck = -rh.s * st->betadd;
+        const double betahat = rk.c * betaacute;
+        st->betadd = -rk.s * betaacute;
+        const double thetatilde_prev = st->thetatilde;
+        const Rot rt = givens(st->rhod, thetabar);
+        st->thetatilde = rt.s * rb.r;
+        st->rhod = rt.c * rb.r;
+        st->betad = -rt.s * st->betad + rt.c * betahat;
+        st->tautilde = (zeta_prev - thetatilde_prev * st->tautilde) / rt.r;
+        const double taud = (st->zeta - st->thetatilde * st->tautilde) / st->rhod;
+        st->dsum += betacheck * betacheck;
+        if (it < cap) {
+            hist_r[it] = sqrt(st->dsum + (st->betad - taud) * (st->betad - taud) + st->betadd * st->betadd);
+            hist_n[it] = fabs(st->zetabar);
+        }
+    }
+    if (alpha_arr) alpha_arr[it + 1] = alpha;
+    if (scale_arr) scale_arr[it + 1] = st->sv_next;
+    st->sv = st->sv_next;
+    st->alpha = alpha;
+    st->iter = it + 1;
+    st->su_next = storage_scale(st->scaled, st->sqrt_n, beta);
+    st->fa = st->su_next / (st->sv * alpha);
+    st->fb = -st->su_next * alpha / (st->su * beta);
+}
+
+// out = c * V (storage -> FP32); optionally zero a second vector.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_start_dirs(const T *__restrict__ V, float *__restrict__ w, float *__restrict__ zero1,
+             float *__restrict__ zero2, int64_t n, const GkState *st) {
+    if (st->stop) return;
+    const float c = (float)st->c0;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        w[i] = c * Storage<T>::ld_plain(V + i);
+        if (zero1) zero1[i] = 0.0f;
+        if (zero2) zero2[i] = 0.0f;
+    }
+}
+
+// LSQR: x += (phi/rho) w; w = v_{i+1} - (theta/rho) w.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_lsqr_update(const T *__restrict__ V, float *__restrict__ x, float *__restrict__ w, int64_t n, const GkState *st) {
+    if (st->stop) return;
+    const float k1 = (float)st->k1, k2 = (float)st->k2, k3 = (float)st->k3;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        const float wi = w[i];
+        x[i] = fmaf(k1, wi, x[i]);
+        w[i] = fmaf(k2, Storage<T>::ld_plain(V + i), k3 * wi);
+    }
+}
+
+// LSMR: hbar = h - k1 hbar; x += k2 hbar; h = v_{k+1} - (theta/rho) h.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_lsmr_update(const T *__restrict__ V, float *__restrict__ x, float *__restrict__ h, float *__restrict__ hbar,
+              int64_t n, const GkState *st) {
+    if (st->stop) return;
+    const float k1 = (float)st->k1, k2 = (float)st->k2, k3 = (float)st->k3, k4 = (float)st->k4;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        const float hi = h[i];
+        const float hb = fmaf(-k1, hbar[i], hi);
+        hbar[i] = hb;
+        x[i] = fmaf(k2, hb, x[i]);
+        h[i] = fmaf(k3, Storage<T>::ld_plain(V + i), k4 * hi);
+    }
+}
+
+// ===================================================================== CGLS
+//
+// Conjugate gradients on the normal equations (Sec. 2.1.1), damped form on
+// [A; lam I] x ~ [b; 0] (Eq. 7):
+//   q = A p;  delta = ||q||^2 + lam^2 ||p||^2;  a = gamma / delta;
+//   x += a p;  r -= a q;  s = A^T r - lam^2 x;  gamma' = ||s||^2;
+//   p = s + (gamma'/gamma) p.
+
+struct CgState {
+    double gamma, alpha, beta, lam2;
+    int iter, stop, status, pad;
+};
+
+__global__ void __launch_bounds__(RED_THREADS) cg_begin(CgState *st, const double *part, int np) {
+    __shared__ double red[RED_THREADS / 32];
+    const double ss = reduce_partials(part, np, red);
+    if (threadIdx.x) return;
+    st->iter = 0;
+    st->status = CBCT_OK;
+    st->stop = 0;
+    st->gamma = ss;
+    if (!good(ss)) {                                  // A^T b = 0: x = 0
+        st->stop = 1;
+        st->status = ss == 0.0 ? CBCT_OK : CBCT_EBREAKDOWN;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+cg_after_forward(CgState *st, const double *part_q, int nq, const double *part_p, int np) {
+    __shared__ double red[RED_THREADS / 32];
+    if (st->stop) return;
+    const double qq = reduce_partials(part_q, nq, red);
+    const double pp = reduce_partials(part_p, np, red);
+    if (threadIdx.x) return;
+    const double delta = qq + st->lam2 * pp;
+    if (!good(delta)) {
+        st->stop = 1;
+        st->status = CBCT_EBREAKDOWN;
+        return;
+    }
+    st->alpha = st->gamma / delta;
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+cg_after_backward(CgState *st, const double *part_s, int ns, const double *part_r, int nr,
+                  double *hist_r, double *hist_n, int cap) {
+    __shared__ double red[RED_THREADS / 32];
+    if (st->stop) return;
+    const double ss = reduce_partials(part_s, ns, red);
+    const double rr = reduce_partials(part_r, nr, red);
+    if (threadIdx.x) return;
+    const int it = st->iter;
+    if (it < cap) {
+        hist_r[it] = sqrt(rr);
+        hist_n[it] = sqrt(ss);
+    }
+    st->iter = it + 1;
+    if (!(ss > 0.0) || !isfinite(ss)) {               // converged exactly (or broke down)
+        st->stop = 1;
+        st->status = ss == 0.0 ? CBCT_OK : CBCT_EBREAKDOWN;
+        return;
+    }
+    st->beta = ss / st->gamma;
+    st->gamma = ss;
+}
+
+__global__ void __launch_bounds__(VEC_THREADS)
+k_copy_sumsq(const float *__restrict__ src, float *__restrict__ dst, float *__restrict__ dst2, int64_t n,
+             double *partial, const CgState *st) {
+    __shared__ double red[VEC_THREADS / 32];
+    if (st && st->stop) return;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        const float v = src[i];
+        dst[i] = v;
+        if (dst2) dst2[i] = 0.0f;
+        s += (double)v * v;
+    }
+    s = block_sum<VEC_THREADS>(s, red);
+    if (threadIdx.x == 0 && partial) partial[blockIdx.x] = s;
+}
+
+// r -= alpha q, partial ||r||^2
+__global__ void __launch_bounds__(VEC_THREADS)
+k_cg_r(float *__restrict__ r, const float *__restrict__ q, int64_t n, double *partial, const CgState *st) {
+    __shared__ double red[VEC_THREADS / 32];
+    if (st->stop) return;
+    const float a = (float)st->alpha;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        const float v = fmaf(-a, q[i], r[i]);
+        r[i] = v;
+        s += (double)v * v;
+    }
+    s = block_sum<VEC_THREADS>(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// x += alpha p; s -= lam^2 x; partial ||s||^2
+__global__ void __launch_bounds__(VEC_THREADS)
+k_cg_xs(float *__restrict__ x, float *__restrict__ s, const float *__restrict__ p, int64_t n, double *partial,
+        const CgState *st) {
+    __shared__ double red[VEC_THREADS / 32];
+    if (st->stop) return;
+    const float a = (float)st->alpha, l2 = (float)st->lam2;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        const float xi = fmaf(a, p[i], x[i]);
+        x[i] = xi;
+        const float si = fmaf(-l2, xi, s[i]);
+        s[i] = si;
+        acc += (double)si * si;
+    }
+    acc = block_sum<VEC_THREADS>(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// p = s + beta p; partial ||p||^2
+__global__ void __launch_bounds__(VEC_THREADS)
+k_cg_p(float *__restrict__ p, const float *__restrict__ s, int64_t n, double *partial, const CgState *st) {
+    __shared__ double red[VEC_THREADS / 32];
+    if (st->stop) return;
+    const float b = (float)st->beta;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        const float v = fmaf(b, p[i], s[i]);
+        p[i] = v;
+        acc += (double)v * v;
+    }
+    acc = block_sum<VEC_THREADS>(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// ====================================================================== drivers
+
+struct SolveIO {
+    const float *b_dev;
+    float *x_dev;
+    bool x_is_host;
+    float *x_host;
+};
+
+static cbct_status check_solve_args(const cbct_geometry *g, const float *b, float *x, const cbct_solve_opts *o) {
+    if (!g || !b || !x || !o) { set_error("solver: null argument"); return CBCT_EINVAL; }
+    if (o->iters < 1) { set_error("solver: iters must be >= 1"); return CBCT_EINVAL; }
+    if (o->storage != CBCT_F32 && o->storage != CBCT_F16 && o->storage != CBCT_BF16) {
+        set_error("solver: unknown storage type");
+        return CBCT_EINVAL;
+    }
+    if (!(o->lambda >= 0.0) || !std::isfinite(o->lambda)) { set_error("solver: lambda must be finite and >= 0"); return CBCT_EINVAL; }
+    return CBCT_OK;
+}
+
+// Stage host b / x through device memory when needed.
+static cbct_status setup_io(const cbct_geometry *g, const float *b, float *x, Workspace &ws, SolveIO &io) {
+    const int64_t n = cbct_geometry_num_rays(g), m = cbct_geometry_num_voxels(g);
+    io.b_dev = b;
+    io.x_dev = x;
+    io.x_is_host = false;
+    io.x_host = nullptr;
+    if (!is_device_pointer(b)) {
+        float *bd = nullptr;
+        CBCT_CUDA_TRY(ws.alloc(&bd, (size_t)n));
+        CBCT_CUDA_TRY(cudaMemcpyAsync(bd, b, sizeof(float) * n, cudaMemcpyHostToDevice, ws.s));
+        io.b_dev = bd;
+    }
+    if (!is_device_pointer(x)) {
+        float *xd = nullptr;
+        CBCT_CUDA_TRY(ws.alloc(&xd, (size_t)m));
+        io.x_dev = xd;
+        io.x_is_host = true;
+        io.x_host = x;
+    }
+    CBCT_CUDA_TRY(cudaMemsetAsync(io.x_dev, 0, sizeof(float) * m, ws.s));
+    return CBCT_OK;
+}
+
+static cbct_status finish_io(const cbct_geometry *g, SolveIO &io, cudaStream_t s) {
+    if (io.x_is_host)
+        CBCT_CUDA_TRY(cudaMemcpyAsync(io.x_host, io.x_dev, sizeof(float) * cbct_geometry_num_voxels(g),
+                                      cudaMemcpyDeviceToHost, s));
+    return CBCT_OK;
+}
+
+static void copy_report(cbct_solve_report *rep, int done, const std::vector<double> &h, int iters) {
+    if (!rep) return;
+    rep->iters_done = done;
+    const int c = done < iters ? done : iters;
+    if (rep->resid_norm) std::memcpy(rep->resid_norm, h.data(), sizeof(double) * c);
+    if (rep->normal_resid_norm) std::memcpy(rep->normal_resid_norm, h.data() + iters, sizeof(double) * c);
+    if (rep->lambda_k) std::memcpy(rep->lambda_k, h.data() + 2 * iters, sizeof(double) * c);
+}
+
+template <typename T>
+static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
+                            cbct_solve_report *rep, cudaStream_t s, Method method) {
+    const DevGeom &g = geom->dev;
+    const int64_t n = cbct_geometry_num_rays(geom), m = cbct_geometry_num_voxels(geom);
+    const int iters = o->iters;
+    const int nf = forward_num_blocks(g), nb = backward_num_blocks(g);
+    Workspace ws(s);
+    SolveIO io;
+    cbct_status st = setup_io(geom, b, x, ws, io);
+    if (st != CBCT_OK) return st;
+
+    T *U = nullptr, *V = nullptr, *basis = nullptr;
+    float *w = nullptr, *h2 = nullptr;
+    double *pf = nullptr, *pb = nullptr, *pv = nullptr, *hist = nullptr;
+    double *alpha_arr = nullptr, *beta_arr = nullptr, *scale_arr = nullptr, *coef = nullptr, *work = nullptr;
+    GkState *dst = nullptr;
+    CBCT_CUDA_TRY(ws.alloc(&U, (size_t)n));
+    if (method == M_HYBRID) {
+        CBCT_CUDA_TRY(ws.alloc(&basis, (size_t)m * (iters + 1)));
+        CBCT_CUDA_TRY(ws.alloc(&alpha_arr, (size_t)iters + 2));
+        CBCT_CUDA_TRY(ws.alloc(&beta_arr, (size_t)iters + 2));
+        CBCT_CUDA_TRY(ws.alloc(&scale_arr, (size_t)iters + 2));
+        CBCT_CUDA_TRY(ws.alloc(&coef, (size_t)iters + 1));
+        CBCT_CUDA_TRY(ws.alloc(&work, (size_t)(iters + 1) * iters * 2 + 4 * (iters + 1)));
+        V = basis;
+    } else {
+        CBCT_CUDA_TRY(ws.alloc(&V, (size_t)m));
+        CBCT_CUDA_TRY(ws.alloc(&w, (size_t)m));
+        if (method == M_LSMR) CBCT_CUDA_TRY(ws.alloc(&h2, (size_t)m));
+    }
+    CBCT_CUDA_TRY(ws.alloc(&pf, (size_t)nf));
+    CBCT_CUDA_TRY(ws.alloc(&pb, (size_t)nb));
+    CBCT_CUDA_TRY(ws.alloc(&pv, (size_t)VEC_BLOCKS));
+    CBCT_CUDA_TRY(ws.alloc(&hist, (size_t)3 * iters));
+    CBCT_CUDA_TRY(ws.alloc(&dst, 1));
+    CBCT_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * 3 * iters, s));
+
+    Tracker tr;
+    tr.profile = o->profile != 0;
+    tr.s = s;
+    GkState init;
+    std::memset(&init, 0, sizeof init);
+    init.damp = method == M_HYBRID ? 0.0 : o->lambda;
+    init.sqrt_n = std::sqrt((double)n);
+    init.sqrt_m = std::sqrt((double)m);
+    init.scaled = std::is_same<T, __half>::value ? 1 : 0;
+    CBCT_CUDA_TRY(cudaMemcpyAsync(dst, &init, sizeof init, cudaMemcpyHostToDevice, s));
+    const cbct_dtype t = o->storage;
+    const int *stop = &dst->stop;
+
+    auto fwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
+        cbct_status r = tr.mark(0);
+        if (r == CBCT_OK) r = launch_forward(g, in, out, t, e, s);
+        if (r == CBCT_OK) r = tr.mark(0);
+        ++tr.launches;
+        ++tr.fwd;
+        return r;
+    };
+    auto bwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
+        cbct_status r = tr.mark(1);
+        if (r == CBCT_OK) r = launch_backward(g, in, out, t, e, s);
+        if (r == CBCT_OK) r = tr.mark(1);
+        ++tr.launches;
+        ++tr.bwd;
+        return r;
+    };
+
+    // beta_1 u_1 = b
+    k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, n, pv);
+    gk_begin<<<1, RED_THREADS, 0, s>>>(dst, pv, VEC_BLOCKS);
+    k_scale_to<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, U, n, &dst->c0, stop);
+    tr.launches += 3;
+    CBCT_CUDA_TRY(cudaGetLastError());
+    if (method == M_HYBRID) {
+        double one = 1.0;
+        CBCT_CUDA_TRY(cudaMemcpyAsync(scale_arr, &one, sizeof one, cudaMemcpyHostToDevice, s));
+    }
+    // alpha_1 v_1 = A^T u_1
+    {
+        Epilogue e{&dst->ba, &dst->bb, 0, 0, pb, stop, nullptr};
+        st = bwd(U, V, e);
+        if (st != CBCT_OK) return st;
+    }
+    gk_begin2<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method);
+    ++tr.launches;
+    if (method == M_LSQR)
+        k_start_dirs<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, w, nullptr, nullptr, m, dst);
+    else if (method == M_LSMR)
+        k_start_dirs<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, w, h2, nullptr, m, dst);
+    if (method != M_HYBRID) ++tr.launches;
+    CBCT_CUDA_TRY(cudaGetLastError());
+    if (method == M_HYBRID) {
+        // record beta_1, alpha_1 once gk_begin2 ran
+        CBCT_CUDA_TRY(cudaMemcpyAsync(beta_arr, &dst->beta, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CBCT_CUDA_TRY(cudaMemcpyAsync(alpha_arr, &dst->alpha, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+
+    double *hist_r = hist, *hist_n = hist + iters, *hist_l = hist + 2 * iters;
+    int k = 0;
+    auto one_iteration = [&]() -> cbct_status {
+        T *Vin = method == M_HYBRID ? basis + (size_t)k * m : V;
+        T *Vout = method == M_HYBRID ? basis + (size_t)(k + 1) * m : V;
+        Epilogue ef{&dst->fa, &dst->fb, 0, 0, pf, stop, nullptr};
+        cbct_status r = fwd(Vin, U, ef);
+        if (r != CBCT_OK) return r;
+        gk_after_forward<<<1, RED_THREADS, 0, s>>>(dst, pf, nf, beta_arr);
+        Epilogue eb{&dst->ba, &dst->bb, 0, 0, pb, stop, method == M_HYBRID ? (const void *)Vin : nullptr};
+        r = bwd(U, Vout, eb);
+        if (r != CBCT_OK) return r;
+        gk_after_backward<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method, hist_r, hist_n, alpha_arr,
+                                                     scale_arr, iters);
+        tr.launches += 3;            // two finalize kernels + the update / projected solve
+        if (method == M_LSQR) {
+            k_lsqr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.x_dev, w, m, dst);
+        } else if (method == M_LSMR) {
+            k_lsmr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.x_dev, w, h2, m, dst);
+        } else {
+            r = launch_projected_solve(alpha_arr, beta_arr, scale_arr, &dst->iter, stop, (int)o->rule, o->lambda,
+                                       work, iters, coef, hist_l, hist_r, s);
+            if (r != CBCT_OK) return r;
+        }
+        CBCT_CUDA_TRY(cudaGetLastError());
+        return CBCT_OK;
+    };
+    if (method == M_HYBRID) {
+        for (k = 0; k < iters; ++k) {
+            st = one_iteration();
+            if (st != CBCT_OK) return st;
+        }
+    } else {
+        const Tracker before = tr.snapshot();
+        int replays = 0;
+        st = run_iterations(iters, o->use_graph != 0 && !tr.profile, s, one_iteration, &replays);
+        if (st != CBCT_OK) return st;
+        tr.scale_since(before, replays);
+    }
+
+    // read back the state to learn how many iterations completed
+    GkState fin;
+    std::vector<double> h((size_t)3 * iters);
+    CBCT_CUDA_TRY(cudaMemcpyAsync(&fin, dst, sizeof fin, cudaMemcpyDeviceToHost, s));
+    CBCT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * 3 * iters, cudaMemcpyDeviceToHost, s));
+    CBCT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (method == M_HYBRID && fin.iter > 0) {
+        // x_k = V_k y_k with the coefficients of the last completed projected solve
+        k_combine<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(basis, coef, fin.iter, m, io.x_dev);
+        ++tr.launches;
+        CBCT_CUDA_TRY(cudaGetLastError());
+    }
+    st = finish_io(geom, io, s);
+    if (st != CBCT_OK) return st;
+    if (io.x_is_host || method == M_HYBRID) CBCT_CUDA_TRY(cudaStreamSynchronize(s));
+    copy_report(rep, fin.iter, h, iters);
+    tr.fill(rep);
+    if (fin.status == CBCT_EBREAKDOWN) set_error("Krylov breakdown: a norm became zero or non-finite");
+    return (cbct_status)fin.status;
+}
+
+static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
+                              cbct_solve_report *rep, cudaStream_t s) {
+    const DevGeom &g = geom->dev;
+    const int64_t n = cbct_geometry_num_rays(geom), m = cbct_geometry_num_voxels(geom);
+    const int iters = o->iters;
+    const int nf = forward_num_blocks(g);
+    Workspace ws(s);
+    SolveIO io;
+    cbct_status st = setup_io(geom, b, x, ws, io);
+    if (st != CBCT_OK) return st;
+    float *r = nullptr, *q = nullptr, *sv = nullptr, *p = nullptr;
+    double *pq = nullptr, *pp = nullptr, *pr = nullptr, *ps = nullptr, *hist = nullptr;
+    CgState *dst = nullptr;
+    CBCT_CUDA_TRY(ws.alloc(&r, (size_t)n));
+    CBCT_CUDA_TRY(ws.alloc(&q, (size_t)n));
+    CBCT_CUDA_TRY(ws.alloc(&sv, (size_t)m));
+    CBCT_CUDA_TRY(ws.alloc(&p, (size_t)m));
+    CBCT_CUDA_TRY(ws.alloc(&pq, (size_t)nf));
+    CBCT_CUDA_TRY(ws.alloc(&pp, (size_t)VEC_BLOCKS));
+    CBCT_CUDA_TRY(ws.alloc(&pr, (size_t)VEC_BLOCKS));
+    CBCT_CUDA_TRY(ws.alloc(&ps, (size_t)VEC_BLOCKS));
+    CBCT_CUDA_TRY(ws.alloc(&hist, (size_t)3 * iters));
+    CBCT_CUDA_TRY(ws.alloc(&dst, 1));
+    CBCT_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * 3 * iters, s));
+    Tracker tr;
+    tr.profile = o->profile != 0;
+    tr.s = s;
+    auto fwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
+        cbct_status r = tr.mark(0);
+        if (r == CBCT_OK) r = launch_forward(g, in, out, CBCT_F32, e, s);
+        if (r == CBCT_OK) r = tr.mark(0);
+        ++tr.launches;
+        ++tr.fwd;
+        return r;
+    };
+    auto bwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
+        cbct_status r = tr.mark(1);
+        if (r == CBCT_OK) r = launch_backward(g, in, out, CBCT_F32, e, s);
+        if (r == CBCT_OK) r = tr.mark(1);
+        ++tr.launches;
+        ++tr.bwd;
+        return r;
+    };
+    CgState init{};
+    init.lam2 = o->lambda * o->lambda;
+    CBCT_CUDA_TRY(cudaMemcpyAsync(dst, &init, sizeof init, cudaMemcpyHostToDevice, s));
+    const int *stop = &dst->stop;
+
+    // r = b; s = A^T r; gamma = ||s||^2; p = s
+    k_copy_sumsq<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, r, nullptr, n, nullptr, nullptr);
+    ++tr.launches;
+    {
+        Epilogue e{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
+        st = bwd(r, sv, e);
+        if (st != CBCT_OK) return st;
+    }
+    k_copy_sumsq<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sv, p, nullptr, m, pp, nullptr);
+    cg_begin<<<1, RED_THREADS, 0, s>>>(dst, pp, VEC_BLOCKS);
+    tr.launches += 2;
+    CBCT_CUDA_TRY(cudaGetLastError());
+
+    double *hist_r = hist, *hist_n = hist + iters;
+    auto one_iteration = [&]() -> cbct_status {
+        Epilogue ef{nullptr, nullptr, 1.0, 0.0, pq, stop, nullptr};
+        cbct_status rr = fwd(p, q, ef);
+        if (rr != CBCT_OK) return rr;
+        cg_after_forward<<<1, RED_THREADS, 0, s>>>(dst, pq, nf, pp, VEC_BLOCKS);
+        k_cg_r<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(r, q, n, pr, dst);
+        Epilogue eb{nullptr, nullptr, 1.0, 0.0, nullptr, stop, nullptr};
+        rr = bwd(r, sv, eb);
+        if (rr != CBCT_OK) return rr;
+        k_cg_xs<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.x_dev, sv, p, m, ps, dst);
+        cg_after_backward<<<1, RED_THREADS, 0, s>>>(dst, ps, VEC_BLOCKS, pr, VEC_BLOCKS, hist_r, hist_n, iters);
+        k_cg_p<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(p, sv, m, pp, dst);
+        tr.launches += 5;
+        CBCT_CUDA_TRY(cudaGetLastError());
+        return CBCT_OK;
+    };
+    const Tracker before = tr.snapshot();
+    int replays = 0;
+    st = run_iterations(iters, o->use_graph != 0 && !tr.profile, s, one_iteration, &replays);
+    if (st != CBCT_OK) return st;
+    tr.scale_since(before, replays);
+    CgState fin;
+    std::vector<double> h((size_t)3 * iters);
+    CBCT_CUDA_TRY(cudaMemcpyAsync(&fin, dst, sizeof fin, cudaMemcpyDeviceToHost, s));
+    CBCT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * 3 * iters, cudaMemcpyDeviceToHost, s));
+    st = finish_io(geom, io, s);
+    if (st != CBCT_OK) return st;
+    CBCT_CUDA_TRY(cudaStreamSynchronize(s));
+    copy_report(rep, fin.iter, h, iters);
+    tr.fill(rep);
+    if (fin.status == CBCT_EBREAKDOWN) set_error("Krylov breakdown: a norm became zero or non-finite");
+    return (cbct_status)fin.status;
+}
+
+static cbct_status dispatch_gk(const cbct_geometry *g, const float *b, float *x, const cbct_solve_opts *o,
+                               cbct_solve_report *rep, cbct_stream stream, Method method) {
+    cbct_status st = check_solve_args(g, b, x, o);
+    if (st != CBCT_OK) return st;
+    if (method == M_HYBRID && o->rule != CBCT_LAMBDA_FIXED && o->rule != CBCT_LAMBDA_GCV) {
+        set_error("hybrid LSQR: unknown lambda rule");
+        return CBCT_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (o->storage) {
+    case CBCT_F16: return gk_solve<__half>(g, b, x, o, rep, s, method);
+    case CBCT_BF16: return gk_solve<__nv_bfloat16>(g, b, x, o, rep, s, method);
+    default: return gk_solve<float>(g, b, x, o, rep, s, method);
+    }
+}
+
+}  // namespace cbct
+
+using namespace cbct;
+
+extern "C" cbct_status cbct_lsqr_solve(const cbct_geometry *g, const float *b, float *x, const cbct_solve_opts *o,
+                                       cbct_solve_report *rep, cbct_stream stream) {
+    return dispatch_gk(g, b, x, o, rep, stream, M_LSQR);
+}
+
+extern "C" cbct_status cbct_lsmr_solve(const cbct_geometry *g, const float *b, float *x, const cbct_solve_opts *o,
+                                       cbct_solve_report *rep, cbct_stream stream) {
+    return dispatch_gk(g, b, x, o, rep, stream, M_LSMR);
+}
+
+extern "C" cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *g, const float *b, float *x,
+                                              const cbct_solve_opts *o, cbct_solve_report *rep, cbct_stream stream) {
+    return dispatch_gk(g, b, x, o, rep, stream, M_HYBRID);
+}
+
+extern "C" cbct_status cbct_cgls_solve(const cbct_geometry *g, const float *b, float *x, const cbct_solve_opts *o,
+                                       cbct_solve_report *rep, cbct_stream stream) {
+    cbct_status st = check_solve_args(g, b, x, o);
+    if (st != CBCT_OK) return st;
+    if (o->storage != CBCT_F32) {
+        set_error("CGLS supports FP32 storage only");
+        return CBCT_EINVAL;
+    }
+    return cgls_solve(g, b, x, o, rep, (cudaStream_t)stream);
+}

@@ -172,13 +172,12 @@ def ellipsoid_phantom(g: Geometry, n_ellipsoids: int = 10, seed: int = 0, scale:
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     ext = np.array([g.nx * g.dx, g.ny * g.dy, g.nz * g.dz])
-    zc = _voxel_centres(g, 2)[:, None, None]
-    yc = _voxel_centres(g, 1)[None, :, None]
-    xc = _voxel_centres(g, 0)[None, None, :]
+    cz, cy, cx = _voxel_centres(g, 2), _voxel_centres(g, 1), _voxel_centres(g, 0)
     vol = np.zeros(g.vol_shape, dtype=np.float64)
     if cylinder:
         r = 0.45 * min(ext[0], ext[1])
-        inside = (xc ** 2 + yc ** 2 <= r * r) & (np.abs(zc) <= 0.4 * ext[2])
+        inside = ((cx[None, None, :] ** 2 + cy[None, :, None] ** 2 <= r * r)
+                  & (np.abs(cz)[:, None, None] <= 0.4 * ext[2]))
         vol[np.broadcast_to(inside, vol.shape)] = 0.3
     for _ in range(n_ellipsoids):
         c = rng.uniform(-0.35, 0.35, 3) * ext
@@ -186,13 +185,22 @@ def ellipsoid_phantom(g: Geometry, n_ellipsoids: int = 10, seed: int = 0, scale:
         phi = rng.uniform(0.0, math.pi)
         rho = rng.uniform(0.0, 1.0)
         cp, sp = math.cos(phi), math.sin(phi)
+        # only voxel centres inside the ellipsoid's bounding sphere can be inside it
+        rmax = float(a.max())
+        sl = []
+        for centres, cc in ((cz, c[2]), (cy, c[1]), (cx, c[0])):
+            idx = np.nonzero(np.abs(centres - cc) <= rmax)[0]
+            sl.append(slice(idx[0], idx[-1] + 1) if idx.size else slice(0, 0))
+        oz = (cz[sl[0]] - c[2])[:, None, None]
+        oy = (cy[sl[1]] - c[1])[None, :, None]
+        ox = (cx[sl[2]] - c[0])[None, None, :]
         # rotate voxel-centre offsets into the ellipsoid frame (rotation about z)
-        ox, oy, oz = xc - c[0], yc - c[1], zc - c[2]
         ex = (cp * ox + sp * oy) / a[0]
         ey = (-sp * ox + cp * oy) / a[1]
         ez = oz / a[2]
         inside = ex * ex + ey * ey + ez * ez <= 1.0
-        vol[np.broadcast_to(inside, vol.shape)] = rho
+        sub = vol[sl[0], sl[1], sl[2]]
+        sub[np.broadcast_to(inside, sub.shape)] = rho
     return (vol * scale).astype(dtype)
 
 

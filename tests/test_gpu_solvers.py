@@ -1,0 +1,199 @@
+"""GPU solvers (C ABI) against the FP64 oracle's textbook recurrences.
+
+Bar: iterates after k steps within 1e-4 relative of the oracle's FP64 iterate
+given the same b; lambda_k of hybrid LSQR within 1e-3 relative.  The
+configurations are the benchmark's small case (32^3, noiseless, CGLS 20) and a
+reduced copy of the 256^3 medical case with the same magnification and photon
+noise (LSQR / LSMR 30, LSMR damped by 1e-2 ||b||).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import krylov
+
+pytestmark = pytest.mark.gpu
+
+ITER_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def cbct():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2211_14212_gb300 import cbct as mod
+    return mod
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_solve(g, b, method, iters, **kw):
+    """FP64 oracle solve, cached per (geometry, method, iterations, options)."""
+    key = (id(g), method, iters, tuple(sorted(kw.items())))
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = getattr(krylov, method)(oracle.Operator(g), b, iters, **kw)
+    return _ORACLE_CACHE[key]
+
+
+def rel(a, ref):
+    a = np.asarray(a, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+@pytest.fixture(scope="module")
+def c1_problem():
+    g = synth.config("c1")
+    x_true = synth.ellipsoid_phantom(g, 10, seed=0)
+    b = oracle.project(g, x_true.astype(np.float64)).ravel()     # noiseless, from the oracle
+    return g, x_true, b
+
+
+def medium_geometry():
+    """64^3 x 4 mm, 128^2 x 3.2 mm detector, 90 angles, DSO 1000 / DSD 1536: the
+    256^3 medical case's field of view and magnification at 1/4 resolution."""
+    return synth.Geometry(64, 64, 64, 4.0, 4.0, 4.0, 128, 128, 3.2, 3.2, 1000.0, 1536.0,
+                          synth.circular_angles(90))
+
+
+@pytest.fixture(scope="module")
+def medium_problem():
+    g = medium_geometry()
+    x_true = synth.ellipsoid_phantom(g, 10, seed=1, scale=0.02)
+    b_clean = oracle.project(g, x_true.astype(np.float64))
+    b = synth.poisson_log_noise(b_clean, 1e5, seed=2).astype(np.float64).ravel()
+    return g, x_true, b
+
+
+def test_cgls_c1(cbct, c1_problem):
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    x, rep = cbct.cgls(geom, dev(b), 20)
+    x_ref, h = krylov.cgls(oracle.Operator(g), b, 20)
+    assert rep.iters_done == 20
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+    np.testing.assert_allclose(rep.resid, h["resid"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("method", ["lsqr", "lsmr"])
+def test_gk_solvers_c1(cbct, c1_problem, method):
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    x, rep = getattr(cbct, method)(geom, dev(b), 30)
+    x_ref, h = oracle_solve(g, b, method, 30)
+    assert rep.iters_done == 30
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+    np.testing.assert_allclose(rep.normal_resid, h["normal_resid"], rtol=2e-2)
+
+
+@pytest.mark.parametrize("method,damp_frac", [("lsqr", 0.0), ("lsmr", 0.0), ("lsmr", 1e-2), ("cgls", 0.0)])
+def test_noisy_medium(cbct, medium_problem, method, damp_frac):
+    g, _, b = medium_problem
+    lam = damp_frac * float(np.linalg.norm(b))
+    geom = cbct.Geometry(g)
+    x, rep = getattr(cbct, method)(geom, dev(b), 30, lam=lam)
+    x_ref, h = oracle_solve(g, b, method, 30, damp=lam)
+    assert rep.iters_done == 30
+    err = rel(x.cpu().numpy(), x_ref)
+    print("%s lam=%g: rel err vs FP64 oracle after 30 iterations %.3g" % (method, lam, err))
+    assert err <= ITER_TOL
+
+
+def test_residual_histories(cbct, c1_problem):
+    """LSQR's ||r_k|| and LSMR's ||A^T r_k|| estimates decrease (Sec. 2.1.1-2.1.3) and
+    LSQR's estimate matches the explicit residual of the GPU iterate."""
+    import torch
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    bd = dev(b)
+    x, rep = cbct.lsqr(geom, bd, 15)
+    r = rep.resid
+    assert np.all(np.diff(r) <= 1e-6 * r[0])
+    explicit = torch.linalg.vector_norm((bd.view(g.proj_shape) - cbct.project(geom, x)).double()).item()
+    assert abs(explicit - r[-1]) <= 1e-4 * np.linalg.norm(b)
+    _, rep = cbct.lsmr(geom, bd, 15)
+    n = rep.normal_resid
+    assert np.all(np.diff(n) <= 1e-6 * n[0])
+
+
+@pytest.mark.parametrize("rule,lam", [("gcv", 0.0), ("fixed", 5.0)])
+def test_hybrid_lsqr(cbct, medium_problem, rule, lam):
+    g, _, b = medium_problem
+    geom = cbct.Geometry(g)
+    k = 20
+    x, rep = cbct.hybrid_lsqr(geom, dev(b), k, rule=rule, lam=lam)
+    x_ref, h = oracle_solve(g, b, "hybrid_lsqr", k, rule=rule, lam=lam)
+    assert rep.iters_done == k
+    np.testing.assert_allclose(rep.lam, h["lambda"], rtol=1e-3)
+    np.testing.assert_allclose(rep.resid, h["resid"], rtol=1e-4)
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+
+
+def test_hybrid_fixed_equals_damped_lsqr_on_gpu(cbct, c1_problem):
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    xh, _ = cbct.hybrid_lsqr(geom, dev(b), 12, rule="fixed", lam=3.0)
+    xl, _ = cbct.lsqr(geom, dev(b), 12, lam=3.0)
+    assert rel(xh.cpu().numpy(), xl.cpu().numpy()) <= 1e-4
+
+
+@pytest.mark.parametrize("storage,bound", [("f16", 5e-3), ("bf16", 3e-2)])
+@pytest.mark.parametrize("method", ["lsqr", "lsmr", "hybrid_lsqr"])
+def test_reduced_precision_storage(cbct, medium_problem, storage, bound, method):
+    """Error of each storage variant against the FP64 oracle (reported, and bounded)."""
+    g, _, b = medium_problem
+    geom = cbct.Geometry(g)
+    x, rep = getattr(cbct, method)(geom, dev(b), 20, storage=storage)
+    ref = oracle_solve(g, b, method, 20)[0]
+    x32 = getattr(cbct, method)(geom, dev(b), 20)[0]
+    err, err32 = rel(x.cpu().numpy(), ref), rel(x32.cpu().numpy(), ref)
+    print("%s %s storage: rel err vs FP64 %.3g (FP32 storage %.3g)" % (method, storage, err, err32))
+    assert rep.iters_done == 20 and err <= bound
+
+
+def test_graph_replay_matches_plain_launches(cbct, c1_problem):
+    import torch
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xg, rg = cbct.lsqr(geom, dev(b), 10, use_graph=True, stream=s)
+        xp, rp = cbct.lsqr(geom, dev(b), 10, use_graph=False, stream=s)
+    s.synchronize()
+    assert rel(xg.cpu().numpy(), xp.cpu().numpy()) <= 1e-6
+    np.testing.assert_allclose(rg.resid, rp.resid, rtol=1e-6)
+
+
+def test_host_buffers(cbct, c1_problem):
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    xh, rh = cbct.lsqr(geom, b.astype(np.float32), 8)
+    xd, rd = cbct.lsqr(geom, dev(b), 8)
+    assert isinstance(xh, np.ndarray)
+    assert rel(xh, xd.cpu().numpy()) <= 1e-6
+
+
+def test_zero_rhs(cbct, c1_problem):
+    g, _, _ = c1_problem
+    geom = cbct.Geometry(g)
+    for fn in (cbct.cgls, cbct.lsqr, cbct.lsmr, cbct.hybrid_lsqr):
+        x, rep = fn(geom, dev(np.zeros(g.num_rays)), 5)
+        assert rep.iters_done == 0
+        assert float(x.abs().max()) == 0.0
+
+
+def test_rejects_bad_storage_for_cgls(cbct, c1_problem):
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    with pytest.raises(cbct.CbctError):
+        cbct.cgls(geom, dev(b), 3, storage="f16")
