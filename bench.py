@@ -308,6 +308,44 @@ def run_ours(args):
     return 0
 
 
+def run_projectors(args):
+    """Standalone forward / backward projector launches on the workload (per-kernel timing)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2211_14212_gb300 import cbct
+    g, config = workload_config()
+    dev = torch.device("cuda", 0)
+    geom = cbct.Geometry(g)
+    x = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=1, scale=0.02)).to(dev)
+    y = torch.empty(geom.proj_shape, device=dev)
+    xb = torch.empty(geom.vol_shape, device=dev)
+    nnz = cbct.count_nnz(geom)
+    s = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        cbct.project(geom, x, out=y)
+        cbct.backproject(geom, y, out=xb)
+    torch.cuda.synchronize()
+    times = {"forward": [], "backward": []}
+    for _ in range(args.steps):
+        for name, fn in (("forward", lambda: cbct.project(geom, x, out=y)),
+                         ("backward", lambda: cbct.backproject(geom, y, out=xb))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            times[name].append(e0.elapsed_time(e1))
+    out = {"mode": "projectors", "config": config, "nnz": nnz}
+    for name, t in times.items():
+        ms = statistics.median(t)
+        out[name] = {"ms": ms, "gupdates_per_s": nnz / (ms * 1e-3) / 1e9,
+                     "gather_gbs": nnz * BYTES_PER_UPDATE / (ms * 1e-3) / 1e9}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,9 +353,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["solve", "projectors"], default="solve",
+                    help="solve: the benchmark step (default); projectors: standalone A / A^T timing")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.mode == "projectors":
+        sys.exit(run_projectors(args))
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
 
 

@@ -15,20 +15,24 @@ namespace cbct {
 // ---------------------------------------------------------------- geometry
 //
 // Every ray is parametrised by alpha along d' = (pixel - source), with alpha = 0
-// where the ray crosses the plane through the rotation axis parallel to the
-// detector (so alpha stays small, |alpha| < ~0.2, inside the volume; the source
-// is at alpha = -dso/dsd, the pixel at 1 - dso/dsd).  The alpha at which ray
-// (a, iv, iu) crosses plane p of an axis is an affine function of p:
-//     alpha_x(p) = fma(p, Ax, Bx)   with (Ax, Bx, Ay, By) = ray_xy[a][iu]
-//     alpha_z(p) = fma(p, Az, Bz)   with (Az, Bz)         = ray_z[iv]
-// (x and y depend only on (angle, u); z only on v).  A == 0 marks a ray exactly
-// parallel to that axis' planes; B then holds the (fixed) voxel index on that
-// axis as a float.  The length of ray/voxel segment [alpha0, alpha1] is
+// at q, where the ray crosses the plane through the rotation axis parallel to
+// the detector (so |alpha| < ~0.2 inside the volume; the source is at
+// alpha = -dso/dsd, the pixel at 1 - dso/dsd).  The alpha at which ray
+// (a, iv, iu) crosses plane p of an axis is
+//     alpha_x(p) = (p * dx + P0x) * Ix     with (P0x, Ix, P0y, Iy) = ray_xy[a][iu]
+//     alpha_z(p) = (p * dz + P0z) * Iz     with (P0z, Iz)           = ray_z[iv]
+// where P0 = (lower volume face - q) along the axis and I = 1 / d'_axis (x and y
+// depend only on (angle, u); z only on v).  Subtracting before scaling keeps
+// every crossing accurate to a few ulps of alpha, also for rays that run
+// almost parallel to a plane.  I == 0 marks a ray exactly parallel to that
+// axis' planes; P0 then holds its (fixed) voxel index on that axis.  The
+// length of the ray/voxel segment [alpha0, alpha1] is
 // (alpha1 - alpha0) * ray_len[iv][iu].
 //
 // Forward and transposed kernels derive every alpha from these tables with
-// the same single fma, so the segment lengths they use are bit-identical and
-// A^T is the exact transpose of A up to the order of the FP32 sums.
+// the same two rounded operations (plane_alpha), so the segment lengths they
+// use are bit-identical and A^T is the exact transpose of A up to the order of
+// the FP32 sums.
 struct DevGeom {
     int nx, ny, nz;
     int nu, nv, nangles;

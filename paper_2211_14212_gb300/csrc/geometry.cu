@@ -27,20 +27,21 @@ static cbct_status invalid(const char *msg) {
     return CBCT_EINVAL;
 }
 
-// Affine map plane index -> alpha for one axis of one ray: alpha(p) = p*A + B,
-// from the ray origin q (alpha = 0) and direction component d along the axis.
-static void axis_map(double q, double d, double b0, double delta, int n, float *A, float *B) {
-    // exactly parallel rays keep a fixed voxel index (half-open voxels: floor)
+// Per-ray constants of one axis: P0 = b0 - q (lower volume face relative to the
+// ray origin q, mm) and I = 1 / d (d = direction component along the axis).
+// Exactly parallel rays keep a fixed voxel index (half-open voxels: floor),
+// stored in P0 with I = 0.
+static void axis_map(double q, double d, double b0, double delta, int n, float *P0, float *I) {
     if (d == 0.0) {
-        *A = 0.0f;
+        *I = 0.0f;
         double idx = std::floor((q - b0) / delta);
         if (idx < -1.0) idx = -1.0;
         if (idx > (double)n) idx = (double)n;
-        *B = (float)idx;
+        *P0 = (float)idx;
         return;
     }
-    *A = (float)(delta / d);
-    *B = (float)((b0 - q) / d);
+    *P0 = (float)(b0 - q);
+    *I = (float)(1.0 / d);
 }
 
 }  // namespace cbct

@@ -25,47 +25,54 @@ struct Axis {
     float p, e;
 };
 
+// Alpha at which a ray crosses plane p of one axis (plane spacing delta):
+// (p * delta + P0) * I, rounded twice.  Both projectors use only this.
+__device__ __forceinline__ float plane_alpha(float p, float delta, float P0, float I) {
+    return __fmul_rn(__fmaf_rn(p, delta, P0), I);
+}
+
 // Clip alpha interval [amin, amax] to the slab between planes plo and phi.
-// A == 0 marks a ray parallel to the planes whose voxel index is B.
-__device__ __forceinline__ void clip_slab(float A, float B, int plo, int phi,
+// I == 0 marks a ray parallel to the planes whose voxel index is P0.
+__device__ __forceinline__ void clip_slab(float P0, float I, float delta, int plo, int phi,
                                           float &amin, float &amax, bool &miss) {
-    if (A == 0.0f) {
-        if (!(B >= (float)plo && B < (float)phi)) miss = true;
+    if (I == 0.0f) {
+        if (!(P0 >= (float)plo && P0 < (float)phi)) miss = true;
         return;
     }
-    const float a0 = fmaf((float)plo, A, B), a1 = fmaf((float)phi, A, B);
+    const float a0 = plane_alpha((float)plo, delta, P0, I), a1 = plane_alpha((float)phi, delta, P0, I);
     amin = fmaxf(amin, fminf(a0, a1));
     amax = fminf(amax, fmaxf(a0, a1));
 }
 
 // Voxel index on one axis at alpha0 (the start of the traversal), restricted
-// to voxels [lo, hi).  The estimate from the plane coordinate is corrected by
-// comparing with the table alphas themselves, so the start voxel is exactly
+// to voxels [lo, hi).  The estimate from the ray position is corrected by
+// comparing with the crossing alphas themselves, so the start voxel is exactly
 // the one whose alpha interval [entry, exit) contains alpha0.
-__device__ __forceinline__ Axis axis_start(float A, float B, float alpha0, int lo, int hi) {
+__device__ __forceinline__ Axis axis_start(float P0, float I, float delta, float alpha0, int lo, int hi) {
     Axis st;
-    if (A == 0.0f) {            // parallel: fixed index, never crossed
-        st.i = (int)B;
+    if (I == 0.0f) {            // parallel: fixed index, never crossed
+        st.i = (int)P0;
         st.s = 0;
         st.p = 0.0f;
         st.e = FLT_MAX;
         return st;
     }
-    int i = (int)floorf((alpha0 - B) / A);
+    // position relative to the lower face: alpha * d - P0 = alpha / I - P0
+    int i = (int)floorf((__fdividef(alpha0, I) - P0) / delta);
     i = max(lo, min(hi - 1, i));
-    if (A > 0.0f) {             // alpha grows with the plane index: voxel i = [alpha(i), alpha(i+1))
-        if (i + 1 < hi && fmaf((float)(i + 1), A, B) <= alpha0) ++i;
-        if (i > lo && fmaf((float)i, A, B) > alpha0) --i;
+    if (I > 0.0f) {             // alpha grows with the plane index: voxel i = [alpha(i), alpha(i+1))
+        if (i + 1 < hi && plane_alpha((float)(i + 1), delta, P0, I) <= alpha0) ++i;
+        if (i > lo && plane_alpha((float)i, delta, P0, I) > alpha0) --i;
         st.s = 1;
         st.p = (float)(i + 1);
     } else {                    // alpha falls with the plane index: voxel i = [alpha(i+1), alpha(i))
-        if (i > lo && fmaf((float)i, A, B) <= alpha0) --i;
-        if (i + 1 < hi && fmaf((float)(i + 1), A, B) > alpha0) ++i;
+        if (i > lo && plane_alpha((float)i, delta, P0, I) <= alpha0) --i;
+        if (i + 1 < hi && plane_alpha((float)(i + 1), delta, P0, I) > alpha0) ++i;
         st.s = -1;
         st.p = (float)i;
     }
     st.i = i;
-    st.e = fmaf(st.p, A, B);
+    st.e = plane_alpha(st.p, delta, P0, I);
     return st;
 }
 
@@ -74,18 +81,18 @@ __device__ __forceinline__ Axis axis_start(float A, float B, float alpha0, int l
 // Linear index = ((k - lo_z) * sy + (j - lo_y)) * sx + (i - lo_x).
 // Returns false if the ray misses the box.
 template <typename F>
-__device__ __forceinline__ bool trace_box(float4 xy, float2 z, int lox, int hix, int loy, int hiy,
-                                          int loz, int hiz, int sxs, int sys, F &&f) {
+__device__ __forceinline__ bool trace_box(const DevGeom &g, float4 xy, float2 z, int lox, int hix, int loy,
+                                          int hiy, int loz, int hiz, int sxs, int sys, F &&f) {
     float amin = -FLT_MAX, amax = FLT_MAX;
     bool miss = false;
-    clip_slab(xy.x, xy.y, lox, hix, amin, amax, miss);
-    clip_slab(xy.z, xy.w, loy, hiy, amin, amax, miss);
-    clip_slab(z.x, z.y, loz, hiz, amin, amax, miss);
+    clip_slab(xy.x, xy.y, g.dx, lox, hix, amin, amax, miss);
+    clip_slab(xy.z, xy.w, g.dy, loy, hiy, amin, amax, miss);
+    clip_slab(z.x, z.y, g.dz, loz, hiz, amin, amax, miss);
     if (miss || !(amin < amax)) return false;
 
-    Axis ax = axis_start(xy.x, xy.y, amin, lox, hix);
-    Axis ay = axis_start(xy.z, xy.w, amin, loy, hiy);
-    Axis az = axis_start(z.x, z.y, amin, loz, hiz);
+    Axis ax = axis_start(xy.x, xy.y, g.dx, amin, lox, hix);
+    Axis ay = axis_start(xy.z, xy.w, g.dy, amin, loy, hiy);
+    Axis az = axis_start(z.x, z.y, g.dz, amin, loz, hiz);
     int idx = ((az.i - loz) * sys + (ay.i - loy)) * sxs + (ax.i - lox);
     const int stride_y = sxs, stride_z = sxs * sys;
     float cur = amin;
@@ -100,19 +107,19 @@ __device__ __forceinline__ bool trace_box(float4 xy, float2 z, int lox, int hix,
             if ((unsigned)(ax.i - lox) >= (unsigned)(hix - lox)) break;
             idx += ax.s;
             ax.p += (float)ax.s;
-            ax.e = fmaf(ax.p, xy.x, xy.y);
+            ax.e = plane_alpha(ax.p, g.dx, xy.x, xy.y);
         } else if (e == ay.e) {
             ay.i += ay.s;
             if ((unsigned)(ay.i - loy) >= (unsigned)(hiy - loy)) break;
             idx += ay.s * stride_y;
             ay.p += (float)ay.s;
-            ay.e = fmaf(ay.p, xy.z, xy.w);
+            ay.e = plane_alpha(ay.p, g.dy, xy.z, xy.w);
         } else {
             az.i += az.s;
             if ((unsigned)(az.i - loz) >= (unsigned)(hiz - loz)) break;
             idx += az.s * stride_z;
             az.p += (float)az.s;
-            az.e = fmaf(az.p, z.x, z.y);
+            az.e = plane_alpha(az.p, g.dz, z.x, z.y);
         }
     }
     return true;
@@ -146,7 +153,7 @@ forward_kernel(DevGeom g, const T *__restrict__ vol, T *__restrict__ proj, Epilo
                 acc += term;
             }
         };
-        trace_box(xy, zt, 0, g.nx, 0, g.ny, 0, g.nz, g.nx, g.ny, seg);
+        trace_box(g, xy, zt, 0, g.nx, 0, g.ny, 0, g.nz, g.nx, g.ny, seg);
         acc *= g.ray_len[(size_t)iv * g.nu + iu];
     }
     double sq = 0.0;
@@ -182,7 +189,7 @@ count_kernel(DevGeom g, unsigned long long *count) {
         const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
         const float2 zt = g.ray_z[iv];
         auto seg = [&](int, float len) { c += len > 0.0f; };
-        trace_box(xy, zt, 0, g.nx, 0, g.ny, 0, g.nz, g.nx, g.ny, seg);
+        trace_box(g, xy, zt, 0, g.nx, 0, g.ny, 0, g.nz, g.nx, g.ny, seg);
     }
     const double s = block_sum<FWD_THREADS>((double)c, red);
     if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)s);
@@ -282,7 +289,7 @@ backward_kernel(DevGeom g, const T *__restrict__ proj, T *__restrict__ vol, Epil
             const float4 xy = xya[iu];
             const float2 zt = g.ray_z[iv];
             auto seg = [&](int idx, float len) { atomicAdd(&sacc[idx], len * w); };
-            trace_box(xy, zt, bx, bx + ex, by, by + ey, bz, bz + ez, BWD_BX, BWD_BY, seg);
+            trace_box(g, xy, zt, bx, bx + ex, by, by + ey, bz, bz + ez, BWD_BX, BWD_BY, seg);
         }
     }
     __syncthreads();
