@@ -21,8 +21,14 @@
  * Ray segments (merged-alpha form): parametrise the ray as s + a (p - s),
  * a in [0, 1]; clip to the volume box by the slab method; collect every plane
  * crossing strictly inside the clipped interval; sort; each consecutive pair
- * (a_m, a_m+1) with a_m+1 > a_m lies in the voxel containing its midpoint, with
- * length (a_m+1 - a_m) |p - s|.
+ * (a_m, a_m+1) with a_m+1 > a_m is one segment of length (a_m+1 - a_m) |p - s|.
+ * Its voxel is the one the ray is in after the crossings it has passed: on an
+ * axis the ray crosses, the index follows from how many of that axis' plane
+ * crossings lie at or before the segment's midpoint (Siddon's index rule; the
+ * same voxel as the one containing the midpoint, but decided by comparing
+ * crossing parameters, so it stays exact for rays lying within rounding
+ * distance of a plane); on an axis the ray runs parallel to, the index is that
+ * of its fixed coordinate in the half-open voxels.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -67,10 +73,22 @@ static int cmp_double(const void *a, const void *b)
     return (x > y) - (x < y);
 }
 
-/* Capacity needed for the alpha list of one ray. */
+/* Capacity needed for the alpha list of one ray, plus the three per-axis crossing lists. */
 static int64_t alpha_capacity(const og_geom *g)
 {
-    return (int64_t)g->nx + g->ny + g->nz + 3 + 2;
+    return 2 * ((int64_t)g->nx + g->ny + g->nz + 3) + 2;
+}
+
+/* Number of entries of the monotone list a[0..n) that are <= x (increasing or decreasing list). */
+static int count_le(const double *a, int n, int increasing, double x)
+{
+    int lo = 0, hi = n;              /* binary search for the boundary */
+    if (increasing) {                /* entries <= x form a prefix */
+        while (lo < hi) { int mid = (lo + hi) / 2; if (a[mid] <= x) lo = mid + 1; else hi = mid; }
+        return lo;
+    }
+    while (lo < hi) { int mid = (lo + hi) / 2; if (a[mid] <= x) hi = mid; else lo = mid + 1; }
+    return n - lo;                   /* entries <= x form a suffix */
 }
 
 /*
@@ -107,13 +125,24 @@ static int ray_segments(const og_geom *g, int64_t ray, int64_t *idx, double *len
     }
     if (!(lo < hi)) return 0;
 
+    /* crossing parameter of every plane of every axis the ray is not parallel to */
+    double *cross[3];
+    double *tail = alpha + (g->nx + g->ny + g->nz + 3) + 2;
+    for (int c = 0; c < 3; ++c) {
+        cross[c] = tail;
+        if (d[c] != 0.0) {
+            for (int q = 0; q <= n[c]; ++q) cross[c][q] = (b0[c] + q * del[c] - s[c]) / d[c];
+            tail += n[c] + 1;
+        }
+    }
+
     int m = 0;
     alpha[m++] = lo;
     alpha[m++] = hi;
     for (int c = 0; c < 3; ++c) {
         if (d[c] == 0.0) continue;
         for (int q = 0; q <= n[c]; ++q) {
-            double a = (b0[c] + q * del[c] - s[c]) / d[c];
+            double a = cross[c][q];
             if (a > lo && a < hi) alpha[m++] = a;
         }
     }
@@ -127,8 +156,14 @@ static int ray_segments(const og_geom *g, int64_t ray, int64_t *idx, double *len
         int64_t ijk[3];
         int inside = 1;
         for (int c = 0; c < 3; ++c) {
-            double pos = s[c] + mid * d[c];
-            ijk[c] = (int64_t)floor((pos - b0[c]) / del[c]);
+            if (d[c] != 0.0) {
+                /* planes crossed so far: increasing coordinate -> voxel (crossed - 1),
+                   decreasing coordinate -> voxel n - crossed */
+                int crossed = count_le(cross[c], n[c] + 1, d[c] > 0.0, mid);
+                ijk[c] = d[c] > 0.0 ? crossed - 1 : n[c] - crossed;
+            } else {
+                ijk[c] = (int64_t)floor((s[c] - b0[c]) / del[c]);
+            }
             if (ijk[c] < 0 || ijk[c] >= n[c]) inside = 0;
         }
         if (!inside) continue;
