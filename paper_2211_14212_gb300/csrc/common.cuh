@@ -128,10 +128,15 @@ cbct_status cuda_fail(cudaError_t err, const char *what);
     } while (0)
 
 // Kernel launchers (projector.cu).  All return CBCT_OK or a CUDA failure.
+// launch_forward reads a z-fastest volume x[j][i][k].
 cbct_status launch_forward(const DevGeom &g, const void *x, void *y, cbct_dtype t,
                            const Epilogue &epi, cudaStream_t s);
+// Volumes: the forward kernel reads, and the solvers keep, the z-fastest layout
+// x[j][i][k]; the ABI uses x[k][j][i].  launch_backward writes either.
 cbct_status launch_backward(const DevGeom &g, const void *y, void *x, cbct_dtype t,
-                            const Epilogue &epi, cudaStream_t s);
+                            const Epilogue &epi, cudaStream_t s, bool zfast);
+cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_zfast,
+                            cudaStream_t s);
 cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaStream_t s);
 int forward_num_blocks(const DevGeom &g);
 int backward_num_blocks(const DevGeom &g);

@@ -400,7 +400,8 @@ k_cg_p(float *__restrict__ p, const float *__restrict__ s, int64_t n, double *pa
 
 struct SolveIO {
     const float *b_dev;
-    float *x_dev;
+    float *x_dev;         // caller layout x[k][j][i] (device; staging buffer for host x)
+    float *xz;            // the iterate in the solvers' z-fastest layout x[j][i][k]
     bool x_is_host;
     float *x_host;
 };
@@ -436,11 +437,15 @@ static cbct_status setup_io(const cbct_geometry *g, const float *b, float *x, Wo
         io.x_is_host = true;
         io.x_host = x;
     }
-    CBCT_CUDA_TRY(cudaMemsetAsync(io.x_dev, 0, sizeof(float) * m, ws.s));
+    CBCT_CUDA_TRY(ws.alloc(&io.xz, (size_t)m));
+    CBCT_CUDA_TRY(cudaMemsetAsync(io.xz, 0, sizeof(float) * m, ws.s));
     return CBCT_OK;
 }
 
+// x (caller layout) <- the z-fastest iterate; then to the host if x is a host buffer.
 static cbct_status finish_io(const cbct_geometry *g, SolveIO &io, cudaStream_t s) {
+    cbct_status st = launch_relayout(g->dev, io.xz, io.x_dev, CBCT_F32, false, s);
+    if (st != CBCT_OK) return st;
     if (io.x_is_host)
         CBCT_CUDA_TRY(cudaMemcpyAsync(io.x_host, io.x_dev, sizeof(float) * cbct_geometry_num_voxels(g),
                                       cudaMemcpyDeviceToHost, s));
@@ -517,7 +522,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     };
     auto bwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(1);
-        if (r == CBCT_OK) r = launch_backward(g, in, out, t, e, s);
+        if (r == CBCT_OK) r = launch_backward(g, in, out, t, e, s, true);
         if (r == CBCT_OK) r = tr.mark(1);
         ++tr.launches;
         ++tr.bwd;
@@ -570,9 +575,9 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
                                                      scale_arr, iters);
         tr.launches += 3;            // two finalize kernels + the update / projected solve
         if (method == M_LSQR) {
-            k_lsqr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.x_dev, w, m, dst);
+            k_lsqr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.xz, w, m, dst);
         } else if (method == M_LSMR) {
-            k_lsmr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.x_dev, w, h2, m, dst);
+            k_lsmr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.xz, w, h2, m, dst);
         } else {
             r = launch_projected_solve(alpha_arr, beta_arr, scale_arr, &dst->iter, stop, (int)o->rule, o->lambda,
                                        work, iters, coef, hist_l, hist_r, s);
@@ -602,12 +607,13 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     CBCT_CUDA_TRY(cudaStreamSynchronize(s));
     if (method == M_HYBRID && fin.iter > 0) {
         // x_k = V_k y_k with the coefficients of the last completed projected solve
-        k_combine<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(basis, coef, fin.iter, m, io.x_dev);
+        k_combine<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(basis, coef, fin.iter, m, io.xz);
         ++tr.launches;
         CBCT_CUDA_TRY(cudaGetLastError());
     }
     st = finish_io(geom, io, s);
     if (st != CBCT_OK) return st;
+    ++tr.launches;                   // the final re-layout of x
     if (io.x_is_host || method == M_HYBRID) CBCT_CUDA_TRY(cudaStreamSynchronize(s));
     copy_report(rep, fin.iter, h, iters);
     tr.fill(rep);
@@ -652,7 +658,7 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     };
     auto bwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(1);
-        if (r == CBCT_OK) r = launch_backward(g, in, out, CBCT_F32, e, s);
+        if (r == CBCT_OK) r = launch_backward(g, in, out, CBCT_F32, e, s, true);
         if (r == CBCT_OK) r = tr.mark(1);
         ++tr.launches;
         ++tr.bwd;
@@ -686,7 +692,7 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
         Epilogue eb{nullptr, nullptr, 1.0, 0.0, nullptr, stop, nullptr};
         rr = bwd(r, sv, eb);
         if (rr != CBCT_OK) return rr;
-        k_cg_xs<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.x_dev, sv, p, m, ps, dst);
+        k_cg_xs<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.xz, sv, p, m, ps, dst);
         cg_after_backward<<<1, RED_THREADS, 0, s>>>(dst, ps, VEC_BLOCKS, pr, VEC_BLOCKS, hist_r, hist_n, iters);
         k_cg_p<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(p, sv, m, pp, dst);
         tr.launches += 5;
@@ -704,6 +710,7 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     CBCT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * 3 * iters, cudaMemcpyDeviceToHost, s));
     st = finish_io(geom, io, s);
     if (st != CBCT_OK) return st;
+    ++tr.launches;                   // the final re-layout of x
     CBCT_CUDA_TRY(cudaStreamSynchronize(s));
     copy_report(rep, fin.iter, h, iters);
     tr.fill(rep);

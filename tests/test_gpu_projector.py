@@ -46,6 +46,16 @@ def elementwise_tol(ref, rel=REL_L2):
     return 4 * rel * np.abs(ref) + 1e-5 * np.abs(ref).max()
 
 
+def assert_elementwise(got, ref, rel=REL_L2, what="", idx=None):
+    tol = elementwise_tol(ref, rel)
+    bad = np.abs(got - ref) > tol
+    if bad.any():
+        w = int(np.argmax(np.abs(got - ref) - tol))
+        where = int(idx[w]) if idx is not None else w
+        raise AssertionError("%s: %d elements off; worst at %d: got %r ref %r tol %r"
+                             % (what, int(bad.sum()), where, got.flat[w], ref.flat[w], tol.flat[w]))
+
+
 def assert_close(got, ref, rel=REL_L2):
     got = np.asarray(got, np.float64).reshape(ref.shape)
     if not np.any(ref):
@@ -164,7 +174,7 @@ def test_c2_forward_sampled_rays(cbct, c2_inputs):
     ref = oracle.project_rays(g, x.astype(np.float64), rays)
     got = y[rays].astype(np.float64)
     assert rel_l2(got, ref) <= REL_L2
-    assert np.all(np.abs(got - ref) <= elementwise_tol(ref))
+    assert_elementwise(got, ref, what="sampled rays", idx=rays)
 
 
 def test_c2_backward_sampled_voxels(cbct, c2_inputs):
@@ -177,7 +187,7 @@ def test_c2_backward_sampled_voxels(cbct, c2_inputs):
     ref = oracle.backproject_voxels(g, yh.astype(np.float64), vox)
     got = x[vox].astype(np.float64)
     assert rel_l2(got, ref) <= REL_L2
-    assert np.all(np.abs(got - ref) <= elementwise_tol(ref))
+    assert_elementwise(got, ref, what="sampled voxels", idx=vox)
 
 
 def test_c2_dot_product(cbct, c2_inputs):

@@ -66,10 +66,13 @@ class RoundedOperator:
         return self.op.rmatvec(y).astype(np.float32).astype(np.float64)
 
 
-def drift_check(cbct_fn, g, b, method, iters, ks, **kw):
+def drift_check(cbct_fn, g, b, method, iters, ks, hist=None, **kw):
     """Compare GPU iterates x_k (k in ks) with the FP64 oracle's; the bar at k is
-    max(1e-4, 10 x the oracle's own sensitivity to FP32 rounding of A)."""
-    exact = oracle_solve(g, b, method, iters, keep_iterates=True, **kw)[1]["iterates"]
+    max(1e-4, 10 x the oracle's own sensitivity to FP32 rounding of A).  The
+    GPU residual history `hist` (if given) is held to 1e-4 relative at the
+    iterations where that sensitivity is below 1e-5."""
+    h_exact = oracle_solve(g, b, method, iters, keep_iterates=True, **kw)[1]
+    exact = h_exact["iterates"]
     key = (id(g), method, iters, "rounded", tuple(sorted(kw.items())))
     if key not in _ORACLE_CACHE:
         _ORACLE_CACHE[key] = getattr(krylov, method)(RoundedOperator(oracle.Operator(g)), b, iters,
@@ -86,6 +89,11 @@ def drift_check(cbct_fn, g, b, method, iters, ks, **kw):
     print("%s drift curve:\n  %s" % (method, "\n  ".join(lines)))
     # the 1e-4 bar itself applies wherever FP32 can meet it
     assert any(rel(rounded[k - 1], exact[k - 1]) < 1e-5 for k in ks)
+    if hist is not None:
+        well = [k for k in range(1, iters + 1) if rel(rounded[k - 1], exact[k - 1]) < 1e-5]
+        got = np.array([hist[k - 1] for k in well])
+        ref = np.array([h_exact["resid"][k - 1] for k in well])
+        np.testing.assert_allclose(got, ref, rtol=1e-4)
 
 
 def rel(a, ref):
@@ -122,10 +130,9 @@ def test_cgls_c1(cbct, c1_problem):
     g, _, b = c1_problem
     geom = cbct.Geometry(g)
     x, rep = cbct.cgls(geom, dev(b), 20)
-    h = oracle_solve(g, b, "cgls", 20, keep_iterates=True)[1]
     assert rep.iters_done == 20
-    np.testing.assert_allclose(rep.resid, h["resid"], rtol=1e-4)
-    drift_check(lambda k: cbct.cgls(geom, dev(b), k)[0].cpu().numpy(), g, b, "cgls", 20, (5, 10, 15, 20))
+    drift_check(lambda k: cbct.cgls(geom, dev(b), k)[0].cpu().numpy(), g, b, "cgls", 20, (5, 10, 15, 20),
+                hist=rep.resid)
 
 
 @pytest.mark.parametrize("method", ["lsqr", "lsmr"])
@@ -133,11 +140,9 @@ def test_gk_solvers_c1(cbct, c1_problem, method):
     g, _, b = c1_problem
     geom = cbct.Geometry(g)
     x, rep = getattr(cbct, method)(geom, dev(b), 30)
-    h = oracle_solve(g, b, method, 30, keep_iterates=True)[1]
     assert rep.iters_done == 30
-    np.testing.assert_allclose(rep.resid, h["resid"], rtol=1e-3)
     drift_check(lambda k: getattr(cbct, method)(geom, dev(b), k)[0].cpu().numpy(), g, b, method, 30,
-                (5, 10, 15, 20, 25, 30))
+                (5, 10, 15, 20, 25, 30), hist=rep.resid)
 
 
 @pytest.mark.parametrize("method,damp_frac", [("lsqr", 0.0), ("lsmr", 0.0), ("lsmr", 1e-2), ("cgls", 0.0)])
@@ -146,11 +151,9 @@ def test_noisy_medium(cbct, medium_problem, method, damp_frac):
     lam = damp_frac * float(np.linalg.norm(b))
     geom = cbct.Geometry(g)
     x, rep = getattr(cbct, method)(geom, dev(b), 30, lam=lam)
-    h = oracle_solve(g, b, method, 30, damp=lam, keep_iterates=True)[1]
     assert rep.iters_done == 30
-    np.testing.assert_allclose(rep.resid, h["resid"], rtol=1e-4)
     drift_check(lambda k: getattr(cbct, method)(geom, dev(b), k, lam=lam)[0].cpu().numpy(), g, b, method, 30,
-                (5, 10, 15, 20, 25, 30), damp=lam)
+                (5, 10, 15, 20, 25, 30), hist=rep.resid, damp=lam)
 
 
 def test_residual_histories(cbct, c1_problem):
