@@ -17,17 +17,17 @@ namespace cbct {
 // Every ray is parametrised by alpha along d' = (pixel - source), with alpha = 0
 // at q, where the ray crosses the plane through the rotation axis parallel to
 // the detector (so |alpha| < ~0.2 inside the volume; the source is at
-// alpha = -dso/dsd, the pixel at 1 - dso/dsd).  The alpha at which ray
-// (a, iv, iu) crosses plane p of an axis is
-//     alpha_x(p) = (p * dx + P0x) * Ix     with (P0x, Ix, P0y, Iy) = ray_xy[a][iu]
-//     alpha_z(p) = (p * dz + P0z) * Iz     with (P0z, Iz)           = ray_z[iv]
-// where P0 = (lower volume face - q) along the axis and I = 1 / d'_axis (x and y
-// depend only on (angle, u); z only on v).  Subtracting before scaling keeps
-// every crossing accurate to a few ulps of alpha, also for rays that run
-// almost parallel to a plane.  I == 0 marks a ray exactly parallel to that
-// axis' planes; P0 then holds its (fixed) voxel index on that axis.  The
-// length of the ray/voxel segment [alpha0, alpha1] is
-// (alpha1 - alpha0) * ray_len[iv][iu].
+// alpha = -dso/dsd, the pixel at 1 - dso/dsd).  For each axis a ray stores
+// the index pq of the voxel plane nearest to q, the offset f = plane(pq) - q
+// (|f| <= delta/2) and I = 1 / d'_axis.  The alpha at which it crosses plane p is
+//     alpha(p) = ((p - pq) * delta + f) * I
+// (x, y from ray_xy / ray_xyq [a][iu]; z from ray_z[iv]).  Measuring planes from
+// the one nearest to q keeps every crossing exact to a few ulps of its distance
+// from q, so rays meeting planes at glancing angles (rows near the mid-plane,
+// columns near the centre at 0/90/180/270 degrees) keep their crossings in
+// place.  I == 0 marks a ray exactly parallel to that axis' planes; pq then
+// holds its (fixed) voxel index.  The length of the ray/voxel segment
+// [alpha0, alpha1] is (alpha1 - alpha0) * ray_len[iv][iu].
 //
 // Forward and transposed kernels derive every alpha from these tables with
 // the same two rounded operations (plane_alpha), so the segment lengths they
@@ -40,8 +40,9 @@ struct DevGeom {
     float du, dv;            // mm
     float bx0, by0, bz0;     // lower corner of the volume, mm
     float dx, dy, dz;        // voxel size, mm
-    const float4 *ray_xy;    // [nangles][nu]
-    const float2 *ray_z;     // [nv]
+    const float4 *ray_xy;    // [nangles][nu]: (fx, Ix, fy, Iy)
+    const float2 *ray_xyq;   // [nangles][nu]: (pqx, pqy)
+    const float4 *ray_z;     // [nv]: (fz, Iz, pqz, 0)
     const float *ray_len;    // [nv][nu]
     const float2 *trig;      // [nangles] (cos t, sin t), for footprint windows only
 };

@@ -27,20 +27,23 @@ static cbct_status invalid(const char *msg) {
     return CBCT_EINVAL;
 }
 
-// Per-ray constants of one axis: P0 = b0 - q (lower volume face relative to the
-// ray origin q, mm) and I = 1 / d (d = direction component along the axis).
-// Exactly parallel rays keep a fixed voxel index (half-open voxels: floor),
-// stored in P0 with I = 0.
-static void axis_map(double q, double d, double b0, double delta, int n, float *P0, float *I) {
+// Per-ray constants of one axis: the index pq of the plane nearest to the ray
+// origin q, the offset f = plane(pq) - q (mm) and I = 1 / d (d = direction
+// component along the axis).  Exactly parallel rays keep a fixed voxel index
+// (half-open voxels: floor), stored in pq with I = 0.
+static void axis_map(double q, double d, double b0, double delta, int n, float *f, float *I, float *pq) {
     if (d == 0.0) {
         *I = 0.0f;
+        *f = 0.0f;
         double idx = std::floor((q - b0) / delta);
         if (idx < -1.0) idx = -1.0;
         if (idx > (double)n) idx = (double)n;
-        *P0 = (float)idx;
+        *pq = (float)idx;
         return;
     }
-    *P0 = (float)(b0 - q);
+    const double p = std::nearbyint((q - b0) / delta);
+    *pq = (float)p;
+    *f = (float)((b0 + p * delta) - q);
     *I = (float)(1.0 / d);
 }
 
@@ -79,7 +82,8 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
     const double bx0 = -0.5 * nx * d->dx, by0 = -0.5 * ny * d->dy, bz0 = -0.5 * nz * d->dz;
 
     std::vector<float4> xy((size_t)na * nu);
-    std::vector<float2> zt(nv);
+    std::vector<float2> xyq((size_t)na * nu);
+    std::vector<float4> zt(nv);
     std::vector<float> len((size_t)nv * nu);
     std::vector<float2> trig(na);
     for (int a = 0; a < na; ++a) {
@@ -91,15 +95,17 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
             const double dxw = -dsd * ct - u * st, dyw = -dsd * st + u * ct;
             const double qx = -u * m * st, qy = u * m * ct;
             float4 e;
-            axis_map(qx, dxw, bx0, d->dx, nx, &e.x, &e.y);
-            axis_map(qy, dyw, by0, d->dy, ny, &e.z, &e.w);
+            float2 q;
+            axis_map(qx, dxw, bx0, d->dx, nx, &e.x, &e.y, &q.x);
+            axis_map(qy, dyw, by0, d->dy, ny, &e.z, &e.w, &q.y);
             xy[(size_t)a * nu + iu] = e;
+            xyq[(size_t)a * nu + iu] = q;
         }
     }
     for (int iv = 0; iv < nv; ++iv) {
         const double v = (iv - 0.5 * (nv - 1)) * d->dv;
-        float2 e;
-        axis_map(v * m, v, bz0, d->dz, nz, &e.x, &e.y);
+        float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        axis_map(v * m, v, bz0, d->dz, nz, &e.x, &e.y, &e.z);
         zt[iv] = e;
         for (int iu = 0; iu < nu; ++iu) {
             const double u = (iu - 0.5 * (nu - 1)) * d->du;
@@ -116,15 +122,18 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
     g->desc.angles_rad = g->angles;
 
     auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t s_xy = align(xy.size() * sizeof(float4)), s_z = align(zt.size() * sizeof(float2));
+    const size_t s_xy = align(xy.size() * sizeof(float4)), s_q = align(xyq.size() * sizeof(float2));
+    const size_t s_z = align(zt.size() * sizeof(float4));
     const size_t s_len = align(len.size() * sizeof(float)), s_tr = align(trig.size() * sizeof(float2));
+    const size_t o_q = s_xy, o_z = o_q + s_q, o_len = o_z + s_z, o_tr = o_len + s_len;
     cudaError_t err = cudaGetDevice(&g->device);
     char *mem = nullptr;
-    if (err == cudaSuccess) err = cudaMalloc(&mem, s_xy + s_z + s_len + s_tr);
+    if (err == cudaSuccess) err = cudaMalloc(&mem, o_tr + s_tr);
     if (err == cudaSuccess) err = cudaMemcpy(mem, xy.data(), xy.size() * sizeof(float4), cudaMemcpyHostToDevice);
-    if (err == cudaSuccess) err = cudaMemcpy(mem + s_xy, zt.data(), zt.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (err == cudaSuccess) err = cudaMemcpy(mem + s_xy + s_z, len.data(), len.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (err == cudaSuccess) err = cudaMemcpy(mem + s_xy + s_z + s_len, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(mem + o_q, xyq.data(), xyq.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(mem + o_z, zt.data(), zt.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(mem + o_len, len.data(), len.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(mem + o_tr, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) {
         if (mem) cudaFree(mem);
         delete[] g->angles;
@@ -138,9 +147,10 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
     dg.bx0 = (float)bx0; dg.by0 = (float)by0; dg.bz0 = (float)bz0;
     dg.dx = (float)d->dx; dg.dy = (float)d->dy; dg.dz = (float)d->dz;
     dg.ray_xy = reinterpret_cast<const float4 *>(mem);
-    dg.ray_z = reinterpret_cast<const float2 *>(mem + s_xy);
-    dg.ray_len = reinterpret_cast<const float *>(mem + s_xy + s_z);
-    dg.trig = reinterpret_cast<const float2 *>(mem + s_xy + s_z + s_len);
+    dg.ray_xyq = reinterpret_cast<const float2 *>(mem + o_q);
+    dg.ray_z = reinterpret_cast<const float4 *>(mem + o_z);
+    dg.ray_len = reinterpret_cast<const float *>(mem + o_len);
+    dg.trig = reinterpret_cast<const float2 *>(mem + o_tr);
     *out = g;
     return CBCT_OK;
 }

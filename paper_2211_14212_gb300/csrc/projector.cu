@@ -26,29 +26,36 @@ namespace cbct {
 
 // ------------------------------------------------------------ ray traversal
 
-// Alpha at which a ray crosses plane p of one axis (plane spacing delta):
-// (p * delta + P0) * I, rounded twice.  Both projectors use only this.
-__device__ __forceinline__ float plane_alpha(float p, float delta, float P0, float I) {
-    return __fmul_rn(__fmaf_rn(p, delta, P0), I);
+// One axis of one ray: offset f = plane(pq) - q, inverse direction I, and the
+// index pq of the plane nearest to the ray origin (the fixed voxel index when
+// I == 0, a ray parallel to the axis' planes).
+struct RayAxis {
+    float f, I, pq;
+};
+
+// Alpha at which a ray crosses plane pq + r of one axis (plane spacing delta):
+// (r * delta + f) * I, rounded twice.  Both projectors use only this.
+__device__ __forceinline__ float plane_alpha(float r, float delta, const RayAxis &a) {
+    return __fmul_rn(__fmaf_rn(r, delta, a.f), a.I);
 }
 
 // One axis of the traversal: current voxel index i, step s (+1/-1, 0 when the
 // ray is parallel to the axis' planes), index of the plane through which the
-// ray leaves the current voxel (as float) and the alpha of that crossing.
+// ray leaves the current voxel (relative to pq, as float) and the alpha of
+// that crossing.
 struct Axis {
     int i, s;
-    float p, e;
+    float r, e;
 };
 
 // Clip alpha interval [amin, amax] to the slab between planes plo and phi.
-// I == 0 marks a ray parallel to the planes whose voxel index is P0.
-__device__ __forceinline__ void clip_slab(float P0, float I, float delta, int plo, int phi,
-                                          float &amin, float &amax, bool &miss) {
-    if (I == 0.0f) {
-        if (!(P0 >= (float)plo && P0 < (float)phi)) miss = true;
+__device__ __forceinline__ void clip_slab(const RayAxis &ra, float delta, int plo, int phi, float &amin,
+                                          float &amax, bool &miss) {
+    if (ra.I == 0.0f) {
+        if (!(ra.pq >= (float)plo && ra.pq < (float)phi)) miss = true;
         return;
     }
-    const float a0 = plane_alpha((float)plo, delta, P0, I), a1 = plane_alpha((float)phi, delta, P0, I);
+    const float a0 = plane_alpha((float)plo - ra.pq, delta, ra), a1 = plane_alpha((float)phi - ra.pq, delta, ra);
     amin = fmaxf(amin, fminf(a0, a1));
     amax = fminf(amax, fmaxf(a0, a1));
 }
@@ -59,53 +66,55 @@ __device__ __forceinline__ void clip_slab(float P0, float I, float delta, int pl
 // exactly the voxel whose alpha interval [entry, exit) contains alpha0.  The
 // exit crossing is returned; it is FLT_MAX when the ray is outside the range
 // and moving away from it.
-__device__ __forceinline__ Axis axis_start(float P0, float I, float delta, float alpha0, int lo, int hi) {
+__device__ __forceinline__ Axis axis_start(const RayAxis &ra, float delta, float alpha0, int lo, int hi) {
     Axis st;
-    if (I == 0.0f) {            // parallel: fixed index, never crossed
-        st.i = (int)P0;
+    if (ra.I == 0.0f) {         // parallel: fixed index, never crossed
+        st.i = (int)ra.pq;
         st.s = 0;
-        st.p = 0.0f;
+        st.r = 0.0f;
         st.e = FLT_MAX;
         return st;
     }
-    // position relative to the lower volume face: alpha * d - P0 = alpha / I - P0
-    int i = (int)floorf((__fdividef(alpha0, I) - P0) / delta);
+    // plane coordinate of the ray at alpha0: pq + (alpha0 / I - f) / delta
+    int i = (int)floorf(ra.pq + (__fdividef(alpha0, ra.I) - ra.f) / delta);
     i = max(lo - 1, min(hi, i));
-    if (I > 0.0f) {             // alpha grows with the plane index: voxel i = [alpha(i), alpha(i+1))
-        if (i < hi && plane_alpha((float)(i + 1), delta, P0, I) <= alpha0) ++i;
-        if (i >= lo && plane_alpha((float)i, delta, P0, I) > alpha0) --i;
+    auto al = [&](int p) { return plane_alpha((float)p - ra.pq, delta, ra); };
+    if (ra.I > 0.0f) {          // alpha grows with the plane index: voxel i = [alpha(i), alpha(i+1))
+        if (i < hi && al(i + 1) <= alpha0) ++i;
+        if (i >= lo && al(i) > alpha0) --i;
         st.s = 1;
-        st.p = (float)(i + 1);
-        st.e = i < hi ? plane_alpha(st.p, delta, P0, I) : FLT_MAX;
+        st.r = (float)(i + 1) - ra.pq;
+        st.e = i < hi ? plane_alpha(st.r, delta, ra) : FLT_MAX;
     } else {                    // alpha falls with the plane index: voxel i = [alpha(i+1), alpha(i))
-        if (i >= lo && plane_alpha((float)i, delta, P0, I) <= alpha0) --i;
-        if (i < hi && plane_alpha((float)(i + 1), delta, P0, I) > alpha0) ++i;
+        if (i >= lo && al(i) <= alpha0) --i;
+        if (i < hi && al(i + 1) > alpha0) ++i;
         st.s = -1;
-        st.p = (float)i;
-        st.e = i >= lo ? plane_alpha(st.p, delta, P0, I) : FLT_MAX;
+        st.r = (float)i - ra.pq;
+        st.e = i >= lo ? plane_alpha(st.r, delta, ra) : FLT_MAX;
     }
     st.i = i;
     return st;
 }
 
 // Walk one ray through the box [lox,hix) x [loy,hiy) x [loz,hiz) of voxels.
-// x/y are stepped together by the whole warp (xy is the same in every lane);
-// z is per lane.  For every segment inside the box it calls
+// x/y are stepped together by the whole warp (the xy tables are the same in
+// every lane); z is per lane.  For every segment inside the box it calls
 //     f(i, j, k, alpha_length)
 // in order along the ray.  Lanes whose ray lies outside the box in z simply
 // make no calls.  Returns false (uniformly) if the xy projection misses the box.
 template <typename F>
-__device__ __forceinline__ bool trace_column(const DevGeom &g, float4 xy, float2 z, int lox, int hix, int loy,
-                                             int hiy, int loz, int hiz, F &&f) {
+__device__ __forceinline__ bool trace_column(const DevGeom &g, const RayAxis &rx, const RayAxis &ry,
+                                             const RayAxis &rz, int lox, int hix, int loy, int hiy, int loz,
+                                             int hiz, F &&f) {
     float amin = -FLT_MAX, amax = FLT_MAX;
     bool miss = false;
-    clip_slab(xy.x, xy.y, g.dx, lox, hix, amin, amax, miss);
-    clip_slab(xy.z, xy.w, g.dy, loy, hiy, amin, amax, miss);
+    clip_slab(rx, g.dx, lox, hix, amin, amax, miss);
+    clip_slab(ry, g.dy, loy, hiy, amin, amax, miss);
     if (miss || !(amin < amax)) return false;
 
-    Axis ax = axis_start(xy.x, xy.y, g.dx, amin, lox, hix);
-    Axis ay = axis_start(xy.z, xy.w, g.dy, amin, loy, hiy);
-    Axis az = axis_start(z.x, z.y, g.dz, amin, loz, hiz);
+    Axis ax = axis_start(rx, g.dx, amin, lox, hix);
+    Axis ay = axis_start(ry, g.dy, amin, loy, hiy);
+    Axis az = axis_start(rz, g.dz, amin, loz, hiz);
     if (az.s == 0 && (az.i < loz || az.i >= hiz)) az.i = loz - 1;   // parallel outside: never inside
     float cur = amin;
     const int maxsteps = (hix - lox) + (hiy - loy) + 1;
@@ -118,24 +127,40 @@ __device__ __forceinline__ bool trace_column(const DevGeom &g, float4 xy, float2
             if (az.i >= loz && az.i < hiz) f(ax.i, ay.i, az.i, az.e - cur);
             cur = az.e;
             az.i += az.s;
-            az.p += (float)az.s;
-            az.e = (az.i >= loz && az.i < hiz) ? plane_alpha(az.p, g.dz, z.x, z.y) : FLT_MAX;
+            az.r += (float)az.s;
+            az.e = (az.i >= loz && az.i < hiz) ? plane_alpha(az.r, g.dz, rz) : FLT_MAX;
         }
         if (az.i >= loz && az.i < hiz) f(ax.i, ay.i, az.i, e - cur);
         cur = e;
         if (e == ax.e) {
             ax.i += ax.s;
             if ((unsigned)(ax.i - lox) >= (unsigned)(hix - lox)) break;
-            ax.p += (float)ax.s;
-            ax.e = plane_alpha(ax.p, g.dx, xy.x, xy.y);
+            ax.r += (float)ax.s;
+            ax.e = plane_alpha(ax.r, g.dx, rx);
         } else {
             ay.i += ay.s;
             if ((unsigned)(ay.i - loy) >= (unsigned)(hiy - loy)) break;
-            ay.p += (float)ay.s;
-            ay.e = plane_alpha(ay.p, g.dy, xy.z, xy.w);
+            ay.r += (float)ay.s;
+            ay.e = plane_alpha(ay.r, g.dy, ry);
         }
     }
     return true;
+}
+
+// Table entries of ray (a, iu, iv); rows outside [0, nv) get a z axis that is
+// parallel and outside every box, so the lane follows the warp without effect.
+__device__ __forceinline__ void load_ray(const DevGeom &g, int a, int iu, int iv, bool row_ok, RayAxis &rx,
+                                         RayAxis &ry, RayAxis &rz) {
+    const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
+    const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
+    rx = RayAxis{xy.x, xy.y, q.x};
+    ry = RayAxis{xy.z, xy.w, q.y};
+    if (row_ok) {
+        const float4 z = g.ray_z[iv];
+        rz = RayAxis{z.x, z.y, z.z};
+    } else {
+        rz = RayAxis{0.0f, 0.0f, (float)(g.nz + 1)};
+    }
 }
 
 // ------------------------------------------------------------- forward A x
@@ -158,9 +183,8 @@ forward_kernel(DevGeom g, const T *__restrict__ vol, T *__restrict__ proj, Epilo
     const bool valid = col_ok && iv < g.nv;
     float acc = 0.0f, comp = 0.0f;
     if (col_ok) {
-        const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
-        // rows past the detector edge follow the warp with a ray that never enters the volume
-        const float2 zt = valid ? g.ray_z[iv] : make_float2((float)(g.nz + 1), 0.0f);
+        RayAxis rx, ry, rz;
+        load_ray(g, a, iu, iv, valid, rx, ry, rz);
         const size_t nz = (size_t)g.nz, row = (size_t)g.nx * g.nz;
         auto seg = [&](int i, int j, int k, float len) {
             const float term = len * Storage<T>::load(vol + (size_t)j * row + (size_t)i * nz + k);
@@ -173,7 +197,7 @@ forward_kernel(DevGeom g, const T *__restrict__ vol, T *__restrict__ proj, Epilo
                 acc += term;
             }
         };
-        trace_column(g, xy, zt, 0, g.nx, 0, g.ny, 0, g.nz, seg);
+        trace_column(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, seg);
         if (valid) acc *= g.ray_len[(size_t)iv * g.nu + iu];
     }
     double sq = 0.0;
@@ -207,10 +231,10 @@ count_kernel(DevGeom g, unsigned long long *count) {
     const int a = blockIdx.z;
     int c = 0;
     if (iu < g.nu) {
-        const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
-        const float2 zt = iv < g.nv ? g.ray_z[iv] : make_float2((float)(g.nz + 1), 0.0f);
+        RayAxis rx, ry, rz;
+        load_ray(g, a, iu, iv, iv < g.nv, rx, ry, rz);
         auto seg = [&](int, int, int, float len) { c += len > 0.0f; };
-        trace_column(g, xy, zt, 0, g.nx, 0, g.ny, 0, g.nz, seg);
+        trace_column(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, seg);
     }
     const double s = block_sum<FWD_THREADS>((double)c, red);
     if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)s);
@@ -302,25 +326,23 @@ backward_kernel(DevGeom g, const T *__restrict__ proj, T *__restrict__ vol, Epil
         const int nblk = (iv1 - iv0 + 32) / 32;
         const int ntask = (iu1 - iu0 + 1) * nblk;
         const T *pa = proj + (size_t)a * g.nv * g.nu;
-        const float4 *xya = g.ray_xy + (size_t)a * g.nu;
         for (int task = warp; task < ntask; task += BWD_THREADS / 32) {
             const int iu = iu0 + task / nblk;
             const int iv = iv0 + (task % nblk) * 32 + lane;
-            const bool row_ok = iv <= iv1;
+            const bool row_ok = iv <= iv1;      // rows outside the window never enter the brick
             float w = 0.0f;
-            float2 zt = make_float2((float)(g.nz + 1), 0.0f);     // rows outside the window: never inside
             if (row_ok) {
                 const size_t pix = (size_t)iv * g.nu + iu;
                 w = Storage<T>::load(pa + pix) * g.ray_len[pix];
-                zt = g.ray_z[iv];
             }
             if (!__any_sync(0xffffffffu, w != 0.0f)) continue;
-            const float4 xy = xya[iu];
+            RayAxis rx, ry, rz;
+            load_ray(g, a, iu, iv, row_ok, rx, ry, rz);
             auto seg = [&](int i, int j, int k, float len) {
                 if (w != 0.0f && len > 0.0f)
                     atomicAdd(&sacc[((j - by) * BWD_BX + (i - bx)) * BWD_BZ + (k - bz)], len * w);
             };
-            trace_column(g, xy, zt, bx, bx + ex, by, by + ey, bz, bz + ez, seg);
+            trace_column(g, rx, ry, rz, bx, bx + ex, by, by + ey, bz, bz + ez, seg);
         }
     }
     __syncthreads();
