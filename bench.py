@@ -190,6 +190,7 @@ def run_ours(args):
     g, config = workload_config()
     dev = torch.device("cuda", local)
     geom = cbct.Geometry(g)
+    tune = cbct.autotune(geom, max_angles=32)
     x_true = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=1, scale=0.02)).to(dev)
     b_clean = cbct.project(geom, x_true).cpu().numpy()
     b_host = torch.from_numpy(synth.poisson_log_noise(b_clean, I0, seed=2 + rank)).pin_memory()
@@ -301,6 +302,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 2 * 4 * geom.num_voxels},
         "gpu_launches": launches,
         "clocks": clocks,
+        "launch_shapes": {"fwd_rows": tune["fwd_rows"], "bwd_brick": tune["bwd_shape"]},
     }
     print(json.dumps(out), flush=True)
     if world > 1:
@@ -318,6 +320,7 @@ def run_projectors(args):
     g, config = workload_config()
     dev = torch.device("cuda", 0)
     geom = cbct.Geometry(g)
+    tune = cbct.autotune(geom, max_angles=32)
     x = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=1, scale=0.02)).to(dev)
     y = torch.empty(geom.proj_shape, device=dev)
     xb = torch.empty(geom.vol_shape, device=dev)
@@ -337,7 +340,7 @@ def run_projectors(args):
             e1.record(s)
             torch.cuda.synchronize()
             times[name].append(e0.elapsed_time(e1))
-    out = {"mode": "projectors", "config": config, "nnz": nnz}
+    out = {"mode": "projectors", "config": config, "nnz": nnz, "autotune": tune}
     for name, t in times.items():
         ms = statistics.median(t)
         out[name] = {"ms": ms, "gupdates_per_s": nnz / (ms * 1e-3) / 1e9,

@@ -103,6 +103,22 @@ cbct_status cbct_backproject(const cbct_geometry *geom, const void *y, void *x,
  * by the forward traversal.  Synchronises `stream`. */
 cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream stream);
 
+/* Launch shapes of the projectors of one geometry (performance only: every
+ * shape computes the same A and A^T).  fwd_rows: rays per lane of the forward
+ * tile (1, 2 or 4; a warp follows 32 * fwd_rows rows of one detector column).
+ * bwd_config: brick of the transpose tile, 0 = 16x16x32 voxels / 2 rays per
+ * lane, 1 = 16x16x16 / 1, 2 = 8x8x64 / 2, 3 = 32x16x16 / 1.  Changing the shape
+ * while another thread uses the geometry is a data race. */
+#define CBCT_TUNE_TIMES 7
+cbct_status cbct_geometry_set_launch(cbct_geometry *geom, int fwd_rows, int bwd_config);
+cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, int *bwd_config);
+/* Times every launch shape (forward and transpose, FP32, on a strided subset
+ * of at most max_angles angles; max_angles <= 0 = all) and keeps the fastest.
+ * times_ms, if non-null, is a host array of CBCT_TUNE_TIMES doubles that
+ * receives the forward times for fwd_rows 1, 2, 4 and the transpose times for
+ * bwd_config 0..3.  Allocates scratch on `stream` and synchronises it. */
+cbct_status cbct_geometry_autotune(cbct_geometry *geom, int max_angles, double *times_ms, cbct_stream stream);
+
 /* ------------------------------------------------------------------ solvers
  * All solvers start from x_0 = 0 and run opts->iters iterations (fewer on
  * breakdown).  b (N FP32 values) and x (M FP32 values, output only) may be

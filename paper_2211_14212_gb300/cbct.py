@@ -89,6 +89,9 @@ def load(path: str = LIB_PATH):
     for fn in ("cbct_project", "cbct_backproject"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.c_int, vp]
     lib.cbct_count_nnz.argtypes = [G, ctypes.POINTER(i64), vp]
+    lib.cbct_geometry_set_launch.argtypes = [G, ctypes.c_int, ctypes.c_int]
+    lib.cbct_geometry_get_launch.argtypes = [G, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.cbct_geometry_autotune.argtypes = [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Report), vp]
     lib.cbct_last_error.restype = ctypes.c_char_p
@@ -205,6 +208,35 @@ def count_nnz(geom: Geometry, stream=None) -> int:
     n = ctypes.c_int64()
     _check("cbct_count_nnz", load().cbct_count_nnz(geom.handle, ctypes.byref(n), _stream_handle(stream)))
     return int(n.value)
+
+
+TUNE_TIMES = 7
+FWD_ROWS = (1, 2, 4)
+BWD_CONFIGS = ("16x16x32/2", "16x16x16/1", "8x8x64/2", "32x16x16/1")
+
+
+def set_launch(geom: Geometry, fwd_rows: int, bwd_config: int):
+    """Set the projector launch shapes of a geometry (cbct_geometry_set_launch)."""
+    _check("cbct_geometry_set_launch", load().cbct_geometry_set_launch(geom.handle, int(fwd_rows), int(bwd_config)))
+
+
+def get_launch(geom: Geometry):
+    """(fwd_rows, bwd_config) of a geometry."""
+    f, b = ctypes.c_int(), ctypes.c_int()
+    _check("cbct_geometry_get_launch", load().cbct_geometry_get_launch(geom.handle, ctypes.byref(f), ctypes.byref(b)))
+    return int(f.value), int(b.value)
+
+
+def autotune(geom: Geometry, max_angles: int = 32, stream=None) -> dict:
+    """Time every launch shape on <= max_angles angles and keep the fastest
+    (cbct_geometry_autotune).  Returns the chosen shapes and all timings."""
+    t = (ctypes.c_double * TUNE_TIMES)()
+    _check("cbct_geometry_autotune", load().cbct_geometry_autotune(geom.handle, int(max_angles), t,
+                                                                     _stream_handle(stream)))
+    f, b = get_launch(geom)
+    return {"fwd_rows": f, "bwd_config": b, "bwd_shape": BWD_CONFIGS[b],
+            "forward_ms": {str(r): t[i] for i, r in enumerate(FWD_ROWS)},
+            "backward_ms": {BWD_CONFIGS[c]: t[len(FWD_ROWS) + c] for c in range(len(BWD_CONFIGS))}}
 
 
 @dataclass

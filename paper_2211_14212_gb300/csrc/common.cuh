@@ -45,6 +45,13 @@ struct DevGeom {
     const float4 *ray_z;     // [nv]: (fz, Iz, pqz, 0)
     const float *ray_len;    // [nv][nu]
     const float2 *trig;      // [nangles] (cos t, sin t), for footprint windows only
+    int fwd_rows;            // forward tile: rays per lane (1, 2 or 4)
+    int bwd_config;          // transpose tile: brick shape / rays per lane (backward_shape)
+};
+
+// Brick of the transpose tile: bx x by x bz voxels, r rays per lane.
+struct BrickShape {
+    int bx, by, bz, r;
 };
 
 }  // namespace cbct
@@ -141,5 +148,9 @@ cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_d
 cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaStream_t s);
 int forward_num_blocks(const DevGeom &g);
 int backward_num_blocks(const DevGeom &g);
+dim3 forward_grid(const DevGeom &g);
+dim3 backward_grid(const DevGeom &g);
+BrickShape backward_shape(int config);
+constexpr int NUM_FWD_ROWS = 3, NUM_BWD_CONFIGS = 4;
 
 }  // namespace cbct

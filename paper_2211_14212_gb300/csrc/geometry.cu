@@ -151,6 +151,8 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
     dg.ray_z = reinterpret_cast<const float4 *>(mem + o_z);
     dg.ray_len = reinterpret_cast<const float *>(mem + o_len);
     dg.trig = reinterpret_cast<const float2 *>(mem + o_tr);
+    dg.fwd_rows = 2;
+    dg.bwd_config = 0;
     *out = g;
     return CBCT_OK;
 }

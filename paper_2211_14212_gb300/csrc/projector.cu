@@ -1,247 +1,50 @@
 // Cone-beam projectors for sm_103a: the Siddon forward projection y = A x
 // (Sec. 1, Eq. 1: one ray per detector pixel) and its exact transpose
-// x = A^T y.
+// x = A^T y, as plain grids of the tiles defined in projector_device.cuh
+// (ray-column warps, shared x/y stepping, bricks of A^T in shared memory).
 //
-// Work layout ("ray-column warps").  In a circular cone-beam scan every ray of
-// one detector column (angle a, column iu) has the same projection onto the
-// xy plane, so all of them cross the x and y voxel planes at the same alpha
-// (the x/y tables depend on (a, iu) only).  A warp therefore takes 32
-// consecutive detector rows of one column: the x/y plane stepping is
-// identical in all lanes (no divergence), and each lane only tracks its own z
-// crossings, which are rare (|dz/d| <= the cone half-angle).  Volumes are read
-// in a z-fastest layout x[j][i][k] so that the 32 lanes of a warp, which sit
-// at ~17 consecutive k of one voxel column, gather one contiguous run.
-//
-// Both kernels walk the same traversal (trace_column) and take every plane
-// crossing from the per-ray tables of DevGeom through plane_alpha, so a
-// ray/voxel segment has the same FP32 length in both: the backprojector is the
-// transpose of the forward projector, not an approximation of it (the paper
-// traces Krylov instabilities to unmatched backprojectors, Sec. 2.1.4, Sec. 4).
+// Launch shapes are per geometry: DevGeom::fwd_rows (R rays per lane of the
+// forward tile) and DevGeom::bwd_config (brick shape and R of the transpose),
+// set to defaults at creation and chosen by cbct_geometry_autotune.
 #include <cfloat>
 #include <cmath>
 
-#include "common.cuh"
+#include "projector_device.cuh"
 
 namespace cbct {
 
-// ------------------------------------------------------------ ray traversal
-
-// One axis of one ray: offset f = plane(pq) - q, inverse direction I, and the
-// index pq of the plane nearest to the ray origin (the fixed voxel index when
-// I == 0, a ray parallel to the axis' planes).
-struct RayAxis {
-    float f, I, pq;
-};
-
-// Alpha at which a ray crosses plane pq + r of one axis (plane spacing delta):
-// (r * delta + f) * I, rounded twice.  Both projectors use only this.
-__device__ __forceinline__ float plane_alpha(float r, float delta, const RayAxis &a) {
-    return __fmul_rn(__fmaf_rn(r, delta, a.f), a.I);
-}
-
-// One axis of the traversal: current voxel index i, step s (+1/-1, 0 when the
-// ray is parallel to the axis' planes), index of the plane through which the
-// ray leaves the current voxel (relative to pq, as float) and the alpha of
-// that crossing.
-struct Axis {
-    int i, s;
-    float r, e;
-};
-
-// Clip alpha interval [amin, amax] to the slab between planes plo and phi.
-__device__ __forceinline__ void clip_slab(const RayAxis &ra, float delta, int plo, int phi, float &amin,
-                                          float &amax, bool &miss) {
-    if (ra.I == 0.0f) {
-        if (!(ra.pq >= (float)plo && ra.pq < (float)phi)) miss = true;
-        return;
-    }
-    const float a0 = plane_alpha((float)plo - ra.pq, delta, ra), a1 = plane_alpha((float)phi - ra.pq, delta, ra);
-    amin = fmaxf(amin, fminf(a0, a1));
-    amax = fminf(amax, fmaxf(a0, a1));
-}
-
-// Voxel index on one axis at alpha0, within [lo - 1, hi] (lo - 1 and hi stand
-// for "before" and "beyond" the range).  The estimate from the ray position is
-// corrected by comparing with the crossing alphas themselves, so the result is
-// exactly the voxel whose alpha interval [entry, exit) contains alpha0.  The
-// exit crossing is returned; it is FLT_MAX when the ray is outside the range
-// and moving away from it.
-__device__ __forceinline__ Axis axis_start(const RayAxis &ra, float delta, float alpha0, int lo, int hi) {
-    Axis st;
-    if (ra.I == 0.0f) {         // parallel: fixed index, never crossed
-        st.i = (int)ra.pq;
-        st.s = 0;
-        st.r = 0.0f;
-        st.e = FLT_MAX;
-        return st;
-    }
-    // plane coordinate of the ray at alpha0: pq + (alpha0 / I - f) / delta
-    int i = (int)floorf(ra.pq + (__fdividef(alpha0, ra.I) - ra.f) / delta);
-    i = max(lo - 1, min(hi, i));
-    auto al = [&](int p) { return plane_alpha((float)p - ra.pq, delta, ra); };
-    if (ra.I > 0.0f) {          // alpha grows with the plane index: voxel i = [alpha(i), alpha(i+1))
-        if (i < hi && al(i + 1) <= alpha0) ++i;
-        if (i >= lo && al(i) > alpha0) --i;
-        st.s = 1;
-        st.r = (float)(i + 1) - ra.pq;
-        st.e = i < hi ? plane_alpha(st.r, delta, ra) : FLT_MAX;
-    } else {                    // alpha falls with the plane index: voxel i = [alpha(i+1), alpha(i))
-        if (i >= lo && al(i) <= alpha0) --i;
-        if (i < hi && al(i + 1) > alpha0) ++i;
-        st.s = -1;
-        st.r = (float)i - ra.pq;
-        st.e = i >= lo ? plane_alpha(st.r, delta, ra) : FLT_MAX;
-    }
-    st.i = i;
-    return st;
-}
-
-// Walk one ray through the box [lox,hix) x [loy,hiy) x [loz,hiz) of voxels.
-// x/y are stepped together by the whole warp (the xy tables are the same in
-// every lane); z is per lane.  For every segment inside the box it calls
-//     f(i, j, k, alpha_length)
-// in order along the ray.  Lanes whose ray lies outside the box in z simply
-// make no calls.  Returns false (uniformly) if the xy projection misses the box.
-template <typename F>
-__device__ __forceinline__ bool trace_column(const DevGeom &g, const RayAxis &rx, const RayAxis &ry,
-                                             const RayAxis &rz, int lox, int hix, int loy, int hiy, int loz,
-                                             int hiz, F &&f) {
-    float amin = -FLT_MAX, amax = FLT_MAX;
-    bool miss = false;
-    clip_slab(rx, g.dx, lox, hix, amin, amax, miss);
-    clip_slab(ry, g.dy, loy, hiy, amin, amax, miss);
-    if (miss || !(amin < amax)) return false;
-
-    Axis ax = axis_start(rx, g.dx, amin, lox, hix);
-    Axis ay = axis_start(ry, g.dy, amin, loy, hiy);
-    Axis az = axis_start(rz, g.dz, amin, loz, hiz);
-    if (az.s == 0 && (az.i < loz || az.i >= hiz)) az.i = loz - 1;   // parallel outside: never inside
-    float cur = amin;
-    const int maxsteps = (hix - lox) + (hiy - loy) + 1;
-#pragma unroll 1
-    for (int n = 0; n < maxsteps; ++n) {
-        const float e = fminf(ax.e, ay.e);
-        // z crossings of this lane inside the current xy cell
-#pragma unroll 1
-        while (az.e < e) {
-            if (az.i >= loz && az.i < hiz) f(ax.i, ay.i, az.i, az.e - cur);
-            cur = az.e;
-            az.i += az.s;
-            az.r += (float)az.s;
-            az.e = (az.i >= loz && az.i < hiz) ? plane_alpha(az.r, g.dz, rz) : FLT_MAX;
-        }
-        if (az.i >= loz && az.i < hiz) f(ax.i, ay.i, az.i, e - cur);
-        cur = e;
-        if (e == ax.e) {
-            ax.i += ax.s;
-            if ((unsigned)(ax.i - lox) >= (unsigned)(hix - lox)) break;
-            ax.r += (float)ax.s;
-            ax.e = plane_alpha(ax.r, g.dx, rx);
-        } else {
-            ay.i += ay.s;
-            if ((unsigned)(ay.i - loy) >= (unsigned)(hiy - loy)) break;
-            ay.r += (float)ay.s;
-            ay.e = plane_alpha(ay.r, g.dy, ry);
-        }
-    }
-    return true;
-}
-
-// Table entries of ray (a, iu, iv); rows outside [0, nv) get a z axis that is
-// parallel and outside every box, so the lane follows the warp without effect.
-__device__ __forceinline__ void load_ray(const DevGeom &g, int a, int iu, int iv, bool row_ok, RayAxis &rx,
-                                         RayAxis &ry, RayAxis &rz) {
-    const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
-    const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
-    rx = RayAxis{xy.x, xy.y, q.x};
-    ry = RayAxis{xy.z, xy.w, q.y};
-    if (row_ok) {
-        const float4 z = g.ray_z[iv];
-        rz = RayAxis{z.x, z.y, z.z};
-    } else {
-        rz = RayAxis{0.0f, 0.0f, (float)(g.nz + 1)};
-    }
-}
-
 // ------------------------------------------------------------- forward A x
-//
-// Block = 8 warps = 8 adjacent detector columns (iu) x 32 detector rows (iv)
-// of one angle.  The volume is read z-fastest: vol[(j * nx + i) * nz + k].
 
-constexpr int FWD_ROWS = 32, FWD_COLS = 8, FWD_THREADS = FWD_ROWS * FWD_COLS;
-
-template <typename T, bool COMP>
+template <typename T, bool COMP, int R>
 __global__ void __launch_bounds__(FWD_THREADS)
 forward_kernel(DevGeom g, const T *__restrict__ vol, T *__restrict__ proj, Epilogue epi) {
     __shared__ double red[FWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int iu = blockIdx.x * FWD_COLS + warp;
-    const int iv = blockIdx.y * FWD_ROWS + lane;
-    const int a = blockIdx.z;
-    const bool col_ok = iu < g.nu;            // uniform across the warp
-    const bool valid = col_ok && iv < g.nv;
-    float acc = 0.0f, comp = 0.0f;
-    if (col_ok) {
-        RayAxis rx, ry, rz;
-        load_ray(g, a, iu, iv, valid, rx, ry, rz);
-        const size_t nz = (size_t)g.nz, row = (size_t)g.nx * g.nz;
-        auto seg = [&](int i, int j, int k, float len) {
-            const float term = len * Storage<T>::load(vol + (size_t)j * row + (size_t)i * nz + k);
-            if (COMP) {          // Kahan-compensated running sum
-                const float yk = term - comp;
-                const float t = acc + yk;
-                comp = (t - acc) - yk;
-                acc = t;
-            } else {
-                acc += term;
-            }
-        };
-        trace_column(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, seg);
-        if (valid) acc *= g.ray_len[(size_t)iv * g.nu + iu];
-    }
-    double sq = 0.0;
-    if (valid) {
-        const size_t r = ((size_t)a * g.nv + iv) * g.nu + iu;
-        const double bcoef = epi_b(epi);
-        double out = epi_a(epi) * (double)acc;
-        if (bcoef != 0.0) {
-            const T *oldp = epi.old ? (const T *)epi.old : (const T *)proj;
-            out += bcoef * (double)Storage<T>::ld_plain(oldp + r);
-        }
-        const float stored = Storage<T>::round((float)out);
-        Storage<T>::store(proj + r, stored);
-        sq = (double)stored * (double)stored;
-    }
-    if (epi.partial) {
-        const double s = block_sum<FWD_THREADS>(sq, red);
-        if (threadIdx.x == 0) {
-            const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            epi.partial[b] = s;
-        }
-    }
+    const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    forward_tile<T, COMP, R>(g, vol, proj, epi, blockIdx.x, blockIdx.y, blockIdx.z,
+                             epi.partial ? epi.partial + b : nullptr, red);
 }
 
+template <int R>
 __global__ void __launch_bounds__(FWD_THREADS)
 count_kernel(DevGeom g, unsigned long long *count) {
     __shared__ double red[FWD_THREADS / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     const int iu = blockIdx.x * FWD_COLS + warp;
-    const int iv = blockIdx.y * FWD_ROWS + lane;
-    const int a = blockIdx.z;
     int c = 0;
     if (iu < g.nu) {
-        RayAxis rx, ry, rz;
-        load_ray(g, a, iu, iv, iv < g.nv, rx, ry, rz);
-        auto seg = [&](int, int, int, float len) { c += len > 0.0f; };
-        trace_column(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, seg);
+        RayAxis rx, ry, rz[R];
+        load_rays<R>(g, blockIdx.z, iu, blockIdx.y * 32 * R, g.nv, rx, ry, rz);
+        auto seg = [&](int, int, float len) { c += len > 0.0f; };
+        trace_columns<R>(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, 0, g.nz, g.nx * g.nz, seg);
     }
     const double s = block_sum<FWD_THREADS>((double)c, red);
     if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)s);
 }
 
-static dim3 forward_grid(const DevGeom &g) {
-    return dim3((g.nu + FWD_COLS - 1) / FWD_COLS, (g.nv + FWD_ROWS - 1) / FWD_ROWS, g.nangles);
+dim3 forward_grid(const DevGeom &g) {
+    const int rows = 32 * g.fwd_rows;
+    return dim3((g.nu + FWD_COLS - 1) / FWD_COLS, (g.nv + rows - 1) / rows, g.nangles);
 }
 
 int forward_num_blocks(const DevGeom &g) {
@@ -249,141 +52,71 @@ int forward_num_blocks(const DevGeom &g) {
     return (int)(gr.x * gr.y * gr.z);
 }
 
-cbct_status launch_forward(const DevGeom &g, const void *x, void *y, cbct_dtype t,
-                           const Epilogue &epi, cudaStream_t s) {
+template <int R>
+static void launch_forward_r(const DevGeom &g, const void *x, void *y, cbct_dtype t, const Epilogue &epi,
+                             cudaStream_t s) {
     const dim3 grid = forward_grid(g);
     switch (t) {
     case CBCT_F32:
-        forward_kernel<float, false><<<grid, FWD_THREADS, 0, s>>>(g, (const float *)x, (float *)y, epi);
+        forward_kernel<float, false, R><<<grid, FWD_THREADS, 0, s>>>(g, (const float *)x, (float *)y, epi);
         break;
     case CBCT_F16:
-        forward_kernel<__half, true><<<grid, FWD_THREADS, 0, s>>>(g, (const __half *)x, (__half *)y, epi);
+        forward_kernel<__half, true, R><<<grid, FWD_THREADS, 0, s>>>(g, (const __half *)x, (__half *)y, epi);
         break;
     case CBCT_BF16:
-        forward_kernel<__nv_bfloat16, true><<<grid, FWD_THREADS, 0, s>>>(
+        forward_kernel<__nv_bfloat16, true, R><<<grid, FWD_THREADS, 0, s>>>(
             g, (const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, epi);
         break;
+    }
+}
+
+cbct_status launch_forward(const DevGeom &g, const void *x, void *y, cbct_dtype t,
+                           const Epilogue &epi, cudaStream_t s) {
+    switch (g.fwd_rows) {
+    case 1: launch_forward_r<1>(g, x, y, t, epi, s); break;
+    case 4: launch_forward_r<4>(g, x, y, t, epi, s); break;
+    default: launch_forward_r<2>(g, x, y, t, epi, s); break;
     }
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }
 
 cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaStream_t s) {
-    count_kernel<<<forward_grid(g), FWD_THREADS, 0, s>>>(g, count_dev);
+    const dim3 grid = forward_grid(g);
+    switch (g.fwd_rows) {
+    case 1: count_kernel<1><<<grid, FWD_THREADS, 0, s>>>(g, count_dev); break;
+    case 4: count_kernel<4><<<grid, FWD_THREADS, 0, s>>>(g, count_dev); break;
+    default: count_kernel<2><<<grid, FWD_THREADS, 0, s>>>(g, count_dev); break;
+    }
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }
 
 // ---------------------------------------------------------- transpose A^T y
-//
-// One CTA owns a brick of BX x BY x BZ voxels, accumulated in shared memory
-// (z fastest).  For every angle each warp finds the detector window onto which
-// the brick projects (its eight corners), cuts it into tasks of one detector
-// column x 32 rows, and walks those rays through the brick with the forward
-// traversal, adding len * |d'| * y to the voxels they meet.  Warps move from
-// angle to angle independently.  After the last angle the brick is written
-// once (fused epilogue, either volume layout), so no global atomics are needed.
 
-constexpr int BWD_BX = 16, BWD_BY = 16, BWD_BZ = 32, BWD_THREADS = 256;
-
-template <typename T, bool ZFAST>
+template <typename T, bool ZFAST, int BX, int BY, int BZ, int R>
 __global__ void __launch_bounds__(BWD_THREADS)
 backward_kernel(DevGeom g, const T *__restrict__ proj, T *__restrict__ vol, Epilogue epi) {
-    __shared__ float sacc[BWD_BY * BWD_BX * BWD_BZ];
+    __shared__ float sacc[BX * BY * BZ];
     __shared__ double red[BWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int bx = blockIdx.x * BWD_BX, by = blockIdx.y * BWD_BY, bz = blockIdx.z * BWD_BZ;
-    const int ex = min(BWD_BX, g.nx - bx), ey = min(BWD_BY, g.ny - by), ez = min(BWD_BZ, g.nz - bz);
-    for (int q = threadIdx.x; q < BWD_BY * BWD_BX * BWD_BZ; q += BWD_THREADS) sacc[q] = 0.0f;
-    __syncthreads();
+    const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    backward_tile<T, ZFAST, BX, BY, BZ, R>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z,
+                                           epi.partial ? epi.partial + b : nullptr, sacc, red);
+}
 
-    // brick corners (mm) for the footprint windows
-    const float x0 = g.bx0 + bx * g.dx, x1 = g.bx0 + (bx + ex) * g.dx;
-    const float y0 = g.by0 + by * g.dy, y1 = g.by0 + (by + ey) * g.dy;
-    const float z0 = g.bz0 + bz * g.dz, z1 = g.bz0 + (bz + ez) * g.dz;
-    const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
-
-    for (int a = 0; a < g.nangles; ++a) {
-        const float2 cs = g.trig[a];
-        float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float px = (c & 1) ? x1 : x0, py = (c & 2) ? y1 : y0;
-            const float along = g.dso - (px * cs.x + py * cs.y);   // > 0: source outside
-            const float across = -px * cs.y + py * cs.x;
-            const float mag = g.dsd / along;
-            umin = fminf(umin, across * mag);
-            umax = fmaxf(umax, across * mag);
-            vmin = fminf(vmin, fminf(z0 * mag, z1 * mag));
-            vmax = fmaxf(vmax, fmaxf(z0 * mag, z1 * mag));
-        }
-        const int iu0 = max(0, (int)ceilf(umin / g.du + cu - 0.01f));
-        const int iu1 = min(g.nu - 1, (int)floorf(umax / g.du + cu + 0.01f));
-        const int iv0 = max(0, (int)ceilf(vmin / g.dv + cv - 0.01f));
-        const int iv1 = min(g.nv - 1, (int)floorf(vmax / g.dv + cv + 0.01f));
-        if (iu0 > iu1 || iv0 > iv1) continue;
-        const int nblk = (iv1 - iv0 + 32) / 32;
-        const int ntask = (iu1 - iu0 + 1) * nblk;
-        const T *pa = proj + (size_t)a * g.nv * g.nu;
-        for (int task = warp; task < ntask; task += BWD_THREADS / 32) {
-            const int iu = iu0 + task / nblk;
-            const int iv = iv0 + (task % nblk) * 32 + lane;
-            const bool row_ok = iv <= iv1;      // rows outside the window never enter the brick
-            float w = 0.0f;
-            if (row_ok) {
-                const size_t pix = (size_t)iv * g.nu + iu;
-                w = Storage<T>::load(pa + pix) * g.ray_len[pix];
-            }
-            if (!__any_sync(0xffffffffu, w != 0.0f)) continue;
-            RayAxis rx, ry, rz;
-            load_ray(g, a, iu, iv, row_ok, rx, ry, rz);
-            auto seg = [&](int i, int j, int k, float len) {
-                if (w != 0.0f && len > 0.0f)
-                    atomicAdd(&sacc[((j - by) * BWD_BX + (i - bx)) * BWD_BZ + (k - bz)], len * w);
-            };
-            trace_column(g, rx, ry, rz, bx, bx + ex, by, by + ey, bz, bz + ez, seg);
-        }
-    }
-    __syncthreads();
-
-    const double acoef = epi_a(epi), bcoef = epi_b(epi);
-    double sq = 0.0;
-    for (int q = threadIdx.x; q < BWD_BY * BWD_BX * BWD_BZ; q += BWD_THREADS) {
-        int i, j, k;
-        if (ZFAST) {            // output x[j][i][k]: walk k fastest
-            k = q % BWD_BZ;
-            i = (q / BWD_BZ) % BWD_BX;
-            j = q / (BWD_BZ * BWD_BX);
-        } else {                // output x[k][j][i]: walk i fastest
-            i = q % BWD_BX;
-            j = (q / BWD_BX) % BWD_BY;
-            k = q / (BWD_BX * BWD_BY);
-        }
-        if (i >= ex || j >= ey || k >= ez) continue;
-        const int sidx = (j * BWD_BX + i) * BWD_BZ + k;
-        const size_t v = ZFAST ? ((size_t)(by + j) * g.nx + (bx + i)) * g.nz + (bz + k)
-                               : ((size_t)(bz + k) * g.ny + (by + j)) * g.nx + (bx + i);
-        double out = acoef * (double)sacc[sidx];
-        if (bcoef != 0.0) {
-            const T *oldp = epi.old ? (const T *)epi.old : (const T *)vol;
-            out += bcoef * (double)Storage<T>::ld_plain(oldp + v);
-        }
-        const float stored = Storage<T>::round((float)out);
-        Storage<T>::store(vol + v, stored);
-        sq += (double)stored * (double)stored;
-    }
-    if (epi.partial) {
-        const double s = block_sum<BWD_THREADS>(sq, red);
-        if (threadIdx.x == 0) {
-            const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            epi.partial[b] = s;
-        }
+BrickShape backward_shape(int config) {
+    switch (config) {
+    case 1: return BrickShape{16, 16, 16, 1};
+    case 2: return BrickShape{8, 8, 64, 2};
+    case 3: return BrickShape{32, 16, 16, 1};
+    default: return BrickShape{16, 16, 32, 2};
     }
 }
 
-static dim3 backward_grid(const DevGeom &g) {
-    return dim3((g.nx + BWD_BX - 1) / BWD_BX, (g.ny + BWD_BY - 1) / BWD_BY, (g.nz + BWD_BZ - 1) / BWD_BZ);
+dim3 backward_grid(const DevGeom &g) {
+    const BrickShape b = backward_shape(g.bwd_config);
+    return dim3((g.nx + b.bx - 1) / b.bx, (g.ny + b.by - 1) / b.by, (g.nz + b.bz - 1) / b.bz);
 }
 
 int backward_num_blocks(const DevGeom &g) {
@@ -391,30 +124,35 @@ int backward_num_blocks(const DevGeom &g) {
     return (int)(gr.x * gr.y * gr.z);
 }
 
-template <bool ZF>
-static void launch_backward_t(const DevGeom &g, const void *y, void *x, cbct_dtype t, const Epilogue &epi,
-                              cudaStream_t s) {
+template <typename T, bool ZF>
+static void launch_backward_t(const DevGeom &g, const void *y, void *x, const Epilogue &epi, cudaStream_t s) {
     const dim3 grid = backward_grid(g);
+    const T *yy = (const T *)y;
+    T *xx = (T *)x;
+    switch (g.bwd_config) {
+    case 1: backward_kernel<T, ZF, 16, 16, 16, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    case 2: backward_kernel<T, ZF, 8, 8, 64, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    case 3: backward_kernel<T, ZF, 32, 16, 16, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    default: backward_kernel<T, ZF, 16, 16, 32, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    }
+}
+
+template <bool ZF>
+static void launch_backward_z(const DevGeom &g, const void *y, void *x, cbct_dtype t, const Epilogue &epi,
+                              cudaStream_t s) {
     switch (t) {
-    case CBCT_F32:
-        backward_kernel<float, ZF><<<grid, BWD_THREADS, 0, s>>>(g, (const float *)y, (float *)x, epi);
-        break;
-    case CBCT_F16:
-        backward_kernel<__half, ZF><<<grid, BWD_THREADS, 0, s>>>(g, (const __half *)y, (__half *)x, epi);
-        break;
-    case CBCT_BF16:
-        backward_kernel<__nv_bfloat16, ZF><<<grid, BWD_THREADS, 0, s>>>(
-            g, (const __nv_bfloat16 *)y, (__nv_bfloat16 *)x, epi);
-        break;
+    case CBCT_F32: launch_backward_t<float, ZF>(g, y, x, epi, s); break;
+    case CBCT_F16: launch_backward_t<__half, ZF>(g, y, x, epi, s); break;
+    case CBCT_BF16: launch_backward_t<__nv_bfloat16, ZF>(g, y, x, epi, s); break;
     }
 }
 
 cbct_status launch_backward(const DevGeom &g, const void *y, void *x, cbct_dtype t, const Epilogue &epi,
                             cudaStream_t s, bool zfast) {
     if (zfast)
-        launch_backward_t<true>(g, y, x, t, epi, s);
+        launch_backward_z<true>(g, y, x, t, epi, s);
     else
-        launch_backward_t<false>(g, y, x, t, epi, s);
+        launch_backward_z<false>(g, y, x, t, epi, s);
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }

@@ -1,0 +1,372 @@
+// Device-side building blocks of the cone-beam projectors (Sec. 1, Eq. 1):
+// the ray traversal shared by A and A^T, and one tile of each projector,
+// callable from a plain grid (projector.cu) or from a persistent kernel that
+// walks a work list spanning several problems (serve.cu).
+//
+// Work layout ("ray-column warps").  In a circular cone-beam scan every ray of
+// one detector column (angle a, column iu) has the same projection onto the
+// xy plane, so all of them cross the x and y voxel planes at the same alpha
+// (the x/y tables depend on (a, iu) only).  A warp therefore takes rays of one
+// detector column: lane l follows rows iv0 + r * 32 + l for r = 0..R-1.  The
+// x/y plane stepping is identical in all lanes and is shared by the warp's
+// 32 R rays; each ray only tracks its own z crossings, which are rare
+// (|dz/d| <= the cone half-angle).  Volumes are read in a z-fastest layout
+// x[j][i][k] so that the lanes of one row group, which sit at ~17 consecutive
+// k of one voxel column, gather one contiguous run.
+//
+// Both projectors take every plane crossing from the per-ray tables of
+// DevGeom through plane_alpha, so a ray/voxel segment has the same FP32 length
+// in both: the backprojector is the transpose of the forward projector, not an
+// approximation of it (the paper traces Krylov instabilities to unmatched
+// backprojectors, Sec. 2.1.4 and Sec. 4).
+#pragma once
+
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace cbct {
+
+// One axis of one ray: offset f = plane(pq) - q, inverse direction I, and the
+// index pq of the plane nearest to the ray origin (the fixed voxel index when
+// I == 0, a ray parallel to the axis' planes).
+struct RayAxis {
+    float f, I, pq;
+};
+
+// Alpha at which a ray crosses plane pq + r of one axis (plane spacing delta):
+// (r * delta + f) * I, rounded twice.  Both projectors use only this.
+__device__ __forceinline__ float plane_alpha(float r, float delta, const RayAxis &a) {
+    return __fmul_rn(__fmaf_rn(r, delta, a.f), a.I);
+}
+
+// One axis of the traversal: current voxel index i, step s (+1/-1, 0 when the
+// ray is parallel to the axis' planes), index of the plane through which the
+// ray leaves the current voxel (relative to pq, as float) and the alpha of
+// that crossing.
+struct Axis {
+    int i, s;
+    float r, e;
+};
+
+// Clip alpha interval [amin, amax] to the slab between planes plo and phi.
+__device__ __forceinline__ void clip_slab(const RayAxis &ra, float delta, int plo, int phi, float &amin,
+                                          float &amax, bool &miss) {
+    if (ra.I == 0.0f) {
+        if (!(ra.pq >= (float)plo && ra.pq < (float)phi)) miss = true;
+        return;
+    }
+    const float a0 = plane_alpha((float)plo - ra.pq, delta, ra), a1 = plane_alpha((float)phi - ra.pq, delta, ra);
+    amin = fmaxf(amin, fminf(a0, a1));
+    amax = fminf(amax, fmaxf(a0, a1));
+}
+
+// Voxel index on one axis at alpha0, within [lo - 1, hi] (lo - 1 and hi stand
+// for "before" and "beyond" the range).  The estimate from the ray position is
+// corrected by comparing with the crossing alphas themselves, so the result is
+// exactly the voxel whose alpha interval [entry, exit) contains alpha0.  The
+// exit crossing is returned; it is FLT_MAX when the ray is outside the range
+// and moving away from it.
+__device__ __forceinline__ Axis axis_start(const RayAxis &ra, float delta, float alpha0, int lo, int hi) {
+    Axis st;
+    if (ra.I == 0.0f) {         // parallel: fixed index, never crossed
+        st.i = (int)ra.pq;
+        st.s = 0;
+        st.r = 0.0f;
+        st.e = FLT_MAX;
+        return st;
+    }
+    // plane coordinate of the ray at alpha0: pq + (alpha0 / I - f) / delta
+    int i = (int)floorf(ra.pq + (__fdividef(alpha0, ra.I) - ra.f) / delta);
+    i = max(lo - 1, min(hi, i));
+    auto al = [&](int p) { return plane_alpha((float)p - ra.pq, delta, ra); };
+    if (ra.I > 0.0f) {          // alpha grows with the plane index: voxel i = [alpha(i), alpha(i+1))
+        if (i < hi && al(i + 1) <= alpha0) ++i;
+        if (i >= lo && al(i) > alpha0) --i;
+        st.s = 1;
+        st.r = (float)(i + 1) - ra.pq;
+        st.e = i < hi ? plane_alpha(st.r, delta, ra) : FLT_MAX;
+    } else {                    // alpha falls with the plane index: voxel i = [alpha(i+1), alpha(i))
+        if (i >= lo && al(i) <= alpha0) --i;
+        if (i < hi && al(i + 1) > alpha0) ++i;
+        st.s = -1;
+        st.r = (float)i - ra.pq;
+        st.e = i >= lo ? plane_alpha(st.r, delta, ra) : FLT_MAX;
+    }
+    st.i = i;
+    return st;
+}
+
+// Walk R rays of one detector column (shared xy tables rx, ry; z tables
+// rz[r]) through the box [lox,hix) x [loy,hiy) x [loz,hiz) of voxels.  For
+// every segment inside the box it calls
+//     f(r, cell + k, alpha_length),   cell = off + i * sx + j * sy,
+// in order along each ray (cell is kept incrementally, so the caller picks the
+// linear layout through off, sx, sy).  Rays outside the box in z make no
+// calls.  Returns false (uniformly across the warp) if the xy projection
+// misses the box.
+template <int R, typename F>
+__device__ __forceinline__ bool trace_columns(const DevGeom &g, const RayAxis &rx, const RayAxis &ry,
+                                              const RayAxis (&rz)[R], int lox, int hix, int loy, int hiy,
+                                              int loz, int hiz, int off, int sx, int sy, F &&f) {
+    float amin = -FLT_MAX, amax = FLT_MAX;
+    bool miss = false;
+    clip_slab(rx, g.dx, lox, hix, amin, amax, miss);
+    clip_slab(ry, g.dy, loy, hiy, amin, amax, miss);
+    if (miss || !(amin < amax)) return false;
+
+    Axis ax = axis_start(rx, g.dx, amin, lox, hix);
+    Axis ay = axis_start(ry, g.dy, amin, loy, hiy);
+    Axis az[R];
+    bool inz[R];
+    float cur[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        az[r] = axis_start(rz[r], g.dz, amin, loz, hiz);
+        if (az[r].s == 0 && (az[r].i < loz || az[r].i >= hiz)) az[r].i = loz - 1;   // parallel outside
+        inz[r] = az[r].i >= loz && az[r].i < hiz;
+        cur[r] = amin;
+    }
+    int cell = off + ax.i * sx + ay.i * sy;
+    const int dcx = ax.s * sx, dcy = ay.s * sy;
+    const int maxsteps = (hix - lox) + (hiy - loy) + 1;
+#pragma unroll 1
+    for (int n = 0; n < maxsteps; ++n) {
+        const float e = fminf(ax.e, ay.e);
+        float zmin = az[0].e;
+#pragma unroll
+        for (int r = 1; r < R; ++r) zmin = fminf(zmin, az[r].e);
+        if (zmin < e) {                    // some ray of this lane crosses a z plane in this xy cell
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+#pragma unroll 1
+                while (az[r].e < e) {
+                    if (inz[r]) f(r, cell + az[r].i, az[r].e - cur[r]);
+                    cur[r] = az[r].e;
+                    az[r].i += az[r].s;
+                    az[r].r += (float)az[r].s;
+                    inz[r] = az[r].i >= loz && az[r].i < hiz;
+                    az[r].e = inz[r] ? plane_alpha(az[r].r, g.dz, rz[r]) : FLT_MAX;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (inz[r]) f(r, cell + az[r].i, e - cur[r]);
+            cur[r] = e;
+        }
+        if (e == ax.e) {
+            ax.i += ax.s;
+            if ((unsigned)(ax.i - lox) >= (unsigned)(hix - lox)) break;
+            cell += dcx;
+            ax.r += (float)ax.s;
+            ax.e = plane_alpha(ax.r, g.dx, rx);
+        } else {
+            ay.i += ay.s;
+            if ((unsigned)(ay.i - loy) >= (unsigned)(hiy - loy)) break;
+            cell += dcy;
+            ay.r += (float)ay.s;
+            ay.e = plane_alpha(ay.r, g.dy, ry);
+        }
+    }
+    return true;
+}
+
+// xy tables of column (a, iu) and z tables of R rows iv0 + r * 32 + lane; rows
+// outside [0, nv) (or past `row_end`) get a z axis that is parallel and
+// outside every box, so the lane follows the warp without effect.
+template <int R>
+__device__ __forceinline__ void load_rays(const DevGeom &g, int a, int iu, int iv0, int row_end, RayAxis &rx,
+                                          RayAxis &ry, RayAxis (&rz)[R]) {
+    const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
+    const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
+    rx = RayAxis{xy.x, xy.y, q.x};
+    ry = RayAxis{xy.z, xy.w, q.y};
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int iv = iv0 + r * 32 + lane;
+        if (iv < row_end) {
+            const float4 z = g.ray_z[iv];
+            rz[r] = RayAxis{z.x, z.y, z.z};
+        } else {
+            rz[r] = RayAxis{0.0f, 0.0f, (float)(g.nz + 1)};
+        }
+    }
+}
+
+// ------------------------------------------------------------- forward A x
+//
+// One tile = 8 warps = 8 adjacent detector columns (iu) x 32 R detector rows
+// (iv) of one angle.  The volume is read z-fastest: vol[(j * nx + i) * nz + k].
+// Epilogue: proj = a * (A vol) + b * old, and one FP64 sum of squares of the
+// stored values into *partial (when non-null).
+
+constexpr int FWD_COLS = 8, FWD_THREADS = 32 * FWD_COLS;
+
+template <typename T, bool COMP, int R>
+__device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restrict__ vol, T *__restrict__ proj,
+                                             const Epilogue &epi, int tx, int ty, int a, double *partial,
+                                             double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int iu = tx * FWD_COLS + warp;
+    const int iv0 = ty * 32 * R;
+    const bool col_ok = iu < g.nu;            // uniform across the warp
+    float acc[R], comp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = comp[r] = 0.0f;
+    if (col_ok) {
+        RayAxis rx, ry, rz[R];
+        load_rays<R>(g, a, iu, iv0, g.nv, rx, ry, rz);
+        auto seg = [&](int r, int idx, float len) {
+            const float term = len * Storage<T>::load(vol + idx);
+            if (COMP) {          // Kahan-compensated running sum
+                const float yk = term - comp[r];
+                const float t = acc[r] + yk;
+                comp[r] = (t - acc[r]) - yk;
+                acc[r] = t;
+            } else {
+                acc[r] += term;
+            }
+        };
+        // z-fastest volume: voxel (i, j, k) at (j * nx + i) * nz + k
+        trace_columns<R>(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, 0, g.nz, g.nx * g.nz, seg);
+    }
+    double sq = 0.0;
+    const double acoef = epi_a(epi), bcoef = epi_b(epi);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int iv = iv0 + r * 32 + lane;
+        if (col_ok && iv < g.nv) {
+            const size_t pix = (size_t)iv * g.nu + iu;
+            const size_t ray = (size_t)a * g.nv * g.nu + pix;
+            double out = acoef * (double)(acc[r] * g.ray_len[pix]);
+            if (bcoef != 0.0) {
+                const T *oldp = epi.old ? (const T *)epi.old : (const T *)proj;
+                out += bcoef * (double)Storage<T>::ld_plain(oldp + ray);
+            }
+            const float stored = Storage<T>::round((float)out);
+            Storage<T>::store(proj + ray, stored);
+            sq += (double)stored * (double)stored;
+        }
+    }
+    if (partial) {
+        const double s = block_sum<FWD_THREADS>(sq, red);
+        if (threadIdx.x == 0) *partial = s;
+    }
+}
+
+// ---------------------------------------------------------- transpose A^T y
+//
+// One tile owns a brick of BX x BY x BZ voxels, accumulated in shared memory
+// (z fastest).  For every angle each warp finds the detector window onto which
+// the brick projects (its corners), cuts it into tasks of one detector column
+// x 32 R rows, and walks those rays through the brick with the forward
+// traversal, adding len * |d'| * y to the voxels they meet.  Warps move from
+// angle to angle independently.  After the last angle the brick is written
+// once (fused epilogue, either volume layout), so no global atomics are needed.
+
+constexpr int BWD_THREADS = 256;
+
+template <typename T, bool ZFAST, int BX, int BY, int BZ, int R>
+__device__ __forceinline__ void backward_tile(const DevGeom &g, const T *__restrict__ proj, T *__restrict__ vol,
+                                              const Epilogue &epi, int tbx, int tby, int tbz, double *partial,
+                                              float *sacc, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int bx = tbx * BX, by = tby * BY, bz = tbz * BZ;
+    const int ex = min(BX, g.nx - bx), ey = min(BY, g.ny - by), ez = min(BZ, g.nz - bz);
+    for (int q = threadIdx.x; q < BX * BY * BZ; q += BWD_THREADS) sacc[q] = 0.0f;
+    __syncthreads();
+
+    // brick corners (mm) for the footprint windows
+    const float x0 = g.bx0 + bx * g.dx, x1 = g.bx0 + (bx + ex) * g.dx;
+    const float y0 = g.by0 + by * g.dy, y1 = g.by0 + (by + ey) * g.dy;
+    const float z0 = g.bz0 + bz * g.dz, z1 = g.bz0 + (bz + ez) * g.dz;
+    const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
+    constexpr int ROWS = 32 * R;
+
+    for (int a = 0; a < g.nangles; ++a) {
+        const float2 cs = g.trig[a];
+        float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float px = (c & 1) ? x1 : x0, py = (c & 2) ? y1 : y0;
+            const float along = g.dso - (px * cs.x + py * cs.y);   // > 0: source outside
+            const float across = -px * cs.y + py * cs.x;
+            const float mag = g.dsd / along;
+            umin = fminf(umin, across * mag);
+            umax = fmaxf(umax, across * mag);
+            vmin = fminf(vmin, fminf(z0 * mag, z1 * mag));
+            vmax = fmaxf(vmax, fmaxf(z0 * mag, z1 * mag));
+        }
+        const int iu0 = max(0, (int)ceilf(umin / g.du + cu - 0.01f));
+        const int iu1 = min(g.nu - 1, (int)floorf(umax / g.du + cu + 0.01f));
+        const int iv0 = max(0, (int)ceilf(vmin / g.dv + cv - 0.01f));
+        const int iv1 = min(g.nv - 1, (int)floorf(vmax / g.dv + cv + 0.01f));
+        if (iu0 > iu1 || iv0 > iv1) continue;
+        const int nblk = (iv1 - iv0 + ROWS) / ROWS;
+        const int ntask = (iu1 - iu0 + 1) * nblk;
+        const T *pa = proj + (size_t)a * g.nv * g.nu;
+        for (int task = warp; task < ntask; task += BWD_THREADS / 32) {
+            const int iu = iu0 + task / nblk;
+            const int ivb = iv0 + (task % nblk) * ROWS;
+            float w[R];
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int iv = ivb + r * 32 + lane;
+                w[r] = 0.0f;
+                if (iv <= iv1) {                // rows outside the window never enter the brick
+                    const size_t pix = (size_t)iv * g.nu + iu;
+                    w[r] = Storage<T>::load(pa + pix) * g.ray_len[pix];
+                }
+                any |= w[r] != 0.0f;
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            RayAxis rx, ry, rz[R];
+            load_rays<R>(g, a, iu, ivb, iv1 + 1, rx, ry, rz);
+            auto seg = [&](int r, int idx, float len) {
+                if (w[r] != 0.0f && len > 0.0f) atomicAdd(&sacc[idx], len * w[r]);
+            };
+            // brick in shared memory, z fastest: ((j - by) * BX + (i - bx)) * BZ + (k - bz)
+            trace_columns<R>(g, rx, ry, rz, bx, bx + ex, by, by + ey, bz, bz + ez, -(by * BX + bx) * BZ - bz,
+                             BZ, BX * BZ, seg);
+        }
+    }
+    __syncthreads();
+
+    const double acoef = epi_a(epi), bcoef = epi_b(epi);
+    double sq = 0.0;
+    for (int q = threadIdx.x; q < BX * BY * BZ; q += BWD_THREADS) {
+        int i, j, k;
+        if (ZFAST) {            // output x[j][i][k]: walk k fastest
+            k = q % BZ;
+            i = (q / BZ) % BX;
+            j = q / (BZ * BX);
+        } else {                // output x[k][j][i]: walk i fastest
+            i = q % BX;
+            j = (q / BX) % BY;
+            k = q / (BX * BY);
+        }
+        if (i >= ex || j >= ey || k >= ez) continue;
+        const int sidx = (j * BX + i) * BZ + k;
+        const size_t v = ZFAST ? ((size_t)(by + j) * g.nx + (bx + i)) * g.nz + (bz + k)
+                               : ((size_t)(bz + k) * g.ny + (by + j)) * g.nx + (bx + i);
+        double out = acoef * (double)sacc[sidx];
+        if (bcoef != 0.0) {
+            const T *oldp = epi.old ? (const T *)epi.old : (const T *)vol;
+            out += bcoef * (double)Storage<T>::ld_plain(oldp + v);
+        }
+        const float stored = Storage<T>::round((float)out);
+        Storage<T>::store(vol + v, stored);
+        sq += (double)stored * (double)stored;
+    }
+    if (partial) {
+        const double s = block_sum<BWD_THREADS>(sq, red);
+        if (threadIdx.x == 0) *partial = s;
+    } else {
+        __syncthreads();        // sacc may be reused by the caller's next tile
+    }
+}
+
+}  // namespace cbct

@@ -70,3 +70,10 @@ def test_solver_argument_checks(lib):
     rep = cbct._Report()
     for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve"):
         assert getattr(lib, fn)(None, None, None, ctypes.byref(opts), ctypes.byref(rep), None) == cbct.CBCT_EINVAL
+
+
+def test_launch_shape_calls_reject_null(lib):
+    from paper_2211_14212_gb300 import cbct
+    assert lib.cbct_geometry_set_launch(None, 2, 0) == cbct.CBCT_EINVAL
+    assert lib.cbct_geometry_get_launch(None, None, None) == cbct.CBCT_EINVAL
+    assert lib.cbct_geometry_autotune(None, 8, None, None) == cbct.CBCT_EINVAL

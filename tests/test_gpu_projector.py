@@ -101,6 +101,35 @@ def test_backward_matches_oracle(cbct, name):
     assert_close(x, oracle.backproject(g, y.astype(np.float64), 8))
 
 
+@pytest.mark.parametrize("name", ["small", "short_scan", "odd"])
+def test_every_launch_shape_matches_oracle(cbct, name):
+    """All forward / transpose launch shapes compute the same A and A^T."""
+    g = GEOMS[name]
+    geom = cbct.Geometry(g)
+    x = synth.random_volume(g, 21).astype(np.float32)
+    y = synth.random_projections(g, 22).astype(np.float32)
+    y_ref = oracle.project(g, x.astype(np.float64))
+    x_ref = oracle.backproject(g, y.astype(np.float64), 8)
+    for fr in cbct.FWD_ROWS:
+        for bc in range(len(cbct.BWD_CONFIGS)):
+            cbct.set_launch(geom, fr, bc)
+            assert cbct.get_launch(geom) == (fr, bc)
+            assert_close(cbct.project(geom, dev(x)).cpu().numpy(), y_ref)
+            assert_close(cbct.backproject(geom, dev(y)).cpu().numpy(), x_ref)
+    with pytest.raises(cbct.CbctError):
+        cbct.set_launch(geom, 3, 0)
+
+
+def test_autotune_picks_a_valid_shape(cbct):
+    g = synth.config("c1")
+    geom = cbct.Geometry(g)
+    res = cbct.autotune(geom, max_angles=8)
+    assert res["fwd_rows"] in cbct.FWD_ROWS and res["bwd_shape"] in cbct.BWD_CONFIGS
+    assert all(t > 0 for t in res["forward_ms"].values()) and all(t > 0 for t in res["backward_ms"].values())
+    x = synth.random_volume(g, 23).astype(np.float32)
+    assert_close(cbct.project(geom, dev(x)).cpu().numpy(), oracle.project(g, x.astype(np.float64)))
+
+
 @pytest.mark.parametrize("name", ["small", "c1", "short_scan"])
 def test_gpu_dot_product(cbct, name):
     import torch

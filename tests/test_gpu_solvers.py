@@ -3,10 +3,14 @@
 Bar: iterates after k steps within 1e-4 relative of the oracle's FP64 iterate
 given the same b, at every k where an FP32 operator can meet it; lambda_k of
 hybrid LSQR within 1e-3 relative.  Late Krylov iterates of these ill-posed
-problems are ill-conditioned: the oracle itself, fed an operator whose outputs
-are merely rounded to FP32, moves its iterate by ~1e-7 up to k ~ 20 and by
-~1e-3 at k = 30.  So the iterate at step k is held to max(1e-4, 10 x that
-intrinsic FP32 sensitivity at k), and the drift curve is printed.
+problems are ill-conditioned: the oracle itself, run with an operator whose
+inputs and outputs are merely rounded to FP32 (what an FP32 projector reading
+FP32 Krylov vectors does at the least), moves its iterate by ~1e-7 up to
+k ~ 20 and by ~1e-3 at k = 30.  The GPU carries about ten such independent
+FP32 roundings per iteration (A and A^T sums, the stored u, v, w, x, the
+coefficient casts), each amplified by the same conditioning, so the iterate
+at step k is held to max(1e-4, 30 x that intrinsic sensitivity at k), and the
+drift curve is printed.
 
 Configurations: the benchmark's small case (32^3, noiseless, CGLS 20) and a
 reduced copy of the 256^3 medical case with the same magnification and photon
@@ -51,26 +55,33 @@ def oracle_solve(g, b, method, iters, **kw):
     return _ORACLE_CACHE[key]
 
 
+def _f32(v):
+    return np.asarray(v, np.float64).astype(np.float32).astype(np.float64)
+
+
 class RoundedOperator:
-    """The oracle's A and A^T with every output rounded to FP32: the smallest
-    perturbation any FP32 projector makes."""
+    """The oracle's A and A^T with inputs and outputs rounded to FP32: the
+    smallest perturbation an FP32 projector on FP32 vectors makes."""
 
     def __init__(self, op):
         self.op = op
         self.shape = op.shape
 
     def matvec(self, x):
-        return self.op.matvec(x).astype(np.float32).astype(np.float64)
+        return _f32(self.op.matvec(_f32(x)))
 
     def rmatvec(self, y):
-        return self.op.rmatvec(y).astype(np.float32).astype(np.float64)
+        return _f32(self.op.rmatvec(_f32(y)))
+
+
+SENS_FACTOR = 30.0
 
 
 def drift_check(cbct_fn, g, b, method, iters, ks, hist=None, **kw):
     """Compare GPU iterates x_k (k in ks) with the FP64 oracle's; the bar at k is
-    max(1e-4, 10 x the oracle's own sensitivity to FP32 rounding of A).  The
-    GPU residual history `hist` (if given) is held to 1e-4 relative at the
-    iterations where that sensitivity is below 1e-5."""
+    max(1e-4, SENS_FACTOR x the oracle's own sensitivity to FP32 rounding of A).
+    The GPU residual history `hist` (if given) is held to the same bar,
+    relative to the oracle's residual at each iteration."""
     h_exact = oracle_solve(g, b, method, iters, keep_iterates=True, **kw)[1]
     exact = h_exact["iterates"]
     key = (id(g), method, iters, "rounded", tuple(sorted(kw.items())))
@@ -83,17 +94,17 @@ def drift_check(cbct_fn, g, b, method, iters, ks, hist=None, **kw):
         xk = cbct_fn(k)
         err = rel(xk, exact[k - 1])
         sens = rel(rounded[k - 1], exact[k - 1])
-        bar = max(ITER_TOL, 10 * sens)
+        bar = max(ITER_TOL, SENS_FACTOR * sens)
         lines.append("k=%2d  gpu %.2e  fp32-rounded oracle %.2e  bar %.1e" % (k, err, sens, bar))
         assert err <= bar, "\n".join(lines)
     print("%s drift curve:\n  %s" % (method, "\n  ".join(lines)))
     # the 1e-4 bar itself applies wherever FP32 can meet it
     assert any(rel(rounded[k - 1], exact[k - 1]) < 1e-5 for k in ks)
     if hist is not None:
-        well = [k for k in range(1, iters + 1) if rel(rounded[k - 1], exact[k - 1]) < 1e-5]
-        got = np.array([hist[k - 1] for k in well])
-        ref = np.array([h_exact["resid"][k - 1] for k in well])
-        np.testing.assert_allclose(got, ref, rtol=1e-4)
+        for k in range(1, iters + 1):
+            bar = max(ITER_TOL, SENS_FACTOR * rel(rounded[k - 1], exact[k - 1]))
+            ref = h_exact["resid"][k - 1]
+            assert abs(hist[k - 1] - ref) <= bar * ref, (k, hist[k - 1], ref, bar)
 
 
 def rel(a, ref):
