@@ -349,6 +349,113 @@ def run_projectors(args):
     return 0
 
 
+def serving_requests(count, scale, seed=3):
+    """The serving stream: volumes in {128, 192, 256, 384}^3 over a 256 mm field
+    of view, square detectors of 256..768 pixels (409.6 mm wide), 90..720 angles
+    over 360 deg or a 200 deg short scan, LSQR or LSMR with 20..40 iterations,
+    photon noise I0 = 5e4.  `scale` shrinks volumes and detectors (quick runs)."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        n = int(rng.choice([128, 192, 256, 384]))
+        nu = int(rng.integers(256, 769))
+        nangles = int(rng.integers(90, 721))
+        short = bool(rng.integers(0, 2))
+        n_s = max(16, int(round(n * scale / 8)) * 8)
+        nu_s = max(32, int(round(nu * scale)))
+        g = synth.serving_request_geometry(n_s, nu_s, nangles, short)
+        reqs.append({"geom": g, "solver": ["lsqr", "lsmr"][int(rng.integers(0, 2))],
+                     "iters": int(rng.integers(20, 41)), "seed": 1000 + i,
+                     "desc": [n_s, nu_s, nangles, "200deg" if short else "360deg"]})
+    return reqs
+
+
+def run_serving(args):
+    """Continuous-batching server vs the one-request-at-a-time solver on the
+    serving stream (Poisson arrivals at 0.8 of the one-at-a-time throughput)."""
+    import threading
+
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2211_14212_gb300 import cbct
+    dev = torch.device("cuda", 0)
+    reqs = serving_requests(args.requests, args.serving_scale)
+    gen = torch.Generator(device=dev)
+    # measured projections: GPU forward projection + Poisson photon noise (input generation)
+    for r in reqs:
+        g = r["geom"]
+        geom = cbct.Geometry(g)
+        x = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=r["seed"], scale=0.02)).to(dev)
+        b = cbct.project(geom, x)
+        gen.manual_seed(r["seed"])
+        counts = torch.poisson(5e4 * torch.exp(-b), generator=gen)
+        r["b"] = (-torch.log(torch.clamp(counts, min=1.0) / 5e4)).float().cpu().numpy().ravel()
+        del x, b, counts, geom
+    torch.cuda.synchronize()
+    # one request at a time (plain solver, host b and x: end to end)
+    service, keep = [], {}
+    for i, r in enumerate(reqs[:2]):                      # warm-up
+        getattr(cbct, r["solver"])(cbct.Geometry(r["geom"]), r["b"], 2)
+    for i, r in enumerate(reqs):
+        t0 = time.perf_counter()
+        geom = cbct.Geometry(r["geom"])
+        x, _ = getattr(cbct, r["solver"])(geom, r["b"], r["iters"])
+        service.append(time.perf_counter() - t0)
+        if i < 8:
+            keep[i] = x
+        del geom
+    total = sum(service)
+    rate = 0.8 * len(reqs) / total
+    rng = np.random.default_rng(4)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    arrivals -= arrivals[0]
+    finish, t = [], 0.0
+    for a, sv in zip(arrivals, service):
+        t = max(t, a) + sv
+        finish.append(t)
+    lat_plain = np.array(finish) - arrivals
+    plain = {"recon_per_s": len(reqs) / (finish[-1] - arrivals[0]), "p50_s": float(np.percentile(lat_plain, 50)),
+             "p99_s": float(np.percentile(lat_plain, 99)), "mean_service_s": total / len(reqs)}
+    # the server, fed in real time
+    srv = cbct.Server(int(args.serving_budget_gb * (1 << 30)), max_slots=args.serving_slots, use_graph=True)
+    ids = [None] * len(reqs)
+    t_start = time.perf_counter()
+
+    def feeder():
+        for i, (a, r) in enumerate(zip(arrivals, reqs)):
+            dt = a - (time.perf_counter() - t_start)
+            if dt > 0:
+                time.sleep(dt)
+            ids[i] = srv.submit(r["geom"], r["b"], r["solver"], r["iters"])
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    results = [srv.wait(i) for i in ids]
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([r.finish_s - r.submit_s for r in results])
+    first = min(r.submit_s for r in results)
+    last = max(r.finish_s for r in results)
+    diffs = [float(np.linalg.norm(results[i].x - keep[i]) / np.linalg.norm(keep[i])) for i in keep]
+    out = {"mode": "serving", "requests": len(reqs), "offered_load": 0.8, "arrival_rate_per_s": rate,
+           "scale": args.serving_scale, "unit": "recon/s",
+           "plain_one_at_a_time": plain,
+           "server": {"recon_per_s": len(reqs) / (last - first), "p50_s": float(np.percentile(lat, 50)),
+                      "p99_s": float(np.percentile(lat, 99)), "steps": stats["steps"],
+                      "graph_replays": stats["graph_replays"], "max_slots": args.serving_slots,
+                      "budget_gb": args.serving_budget_gb},
+           "max_rel_diff_server_vs_plain": max(diffs) if diffs else None,
+           "request_mix": [r["desc"] + [r["solver"], r["iters"]] for r in reqs]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,13 +463,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "projectors"], default="solve",
-                    help="solve: the benchmark step (default); projectors: standalone A / A^T timing")
+    ap.add_argument("--mode", choices=["solve", "projectors", "serving"], default="solve",
+                    help="solve: the benchmark step (default); projectors: standalone A / A^T timing; "
+                         "serving: continuous-batching server vs one request at a time")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--serving-scale", type=float, default=1.0)
+    ap.add_argument("--serving-slots", type=int, default=16)
+    ap.add_argument("--serving-budget-gb", type=float, default=96.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.mode == "projectors":
         sys.exit(run_projectors(args))
+    if args.mode == "serving":
+        sys.exit(run_serving(args))
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
 
 

@@ -177,6 +177,63 @@ cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *geom, const float *b, fl
                                    const cbct_solve_opts *opts, cbct_solve_report *report,
                                    cbct_stream stream);
 
+/* ------------------------------------------------------------------ serving
+ * A server reconstructs many scans concurrently on the current CUDA device
+ * ("continuous batching"; no counterpart in the paper, which solves one scan at
+ * a time).  Submitted requests wait in FIFO order and are admitted as slots
+ * while the device memory they need fits the budget; a library-owned worker
+ * thread then advances every admitted request by one Krylov iteration per step
+ * (one multi-instance launch per kernel for all of them), reads out finished
+ * results, frees their memory and admits waiting requests between steps.
+ * Each result equals the single-request solver's (same kernels, same
+ * reduction order) up to the FP32 rounding of the transpose's shared-memory
+ * accumulation.  Requests use FP32 storage and LSQR or LSMR.  All calls are
+ * thread-safe except cbct_server_destroy, which must not overlap any other
+ * call on the same server. */
+
+typedef struct cbct_server cbct_server;   /* opaque, library-owned */
+typedef enum { CBCT_SOLVER_LSQR = 0, CBCT_SOLVER_LSMR = 1 } cbct_solver;
+
+typedef struct {
+    size_t hbm_budget_bytes;   /* device memory the server may hold for requests (> 0) */
+    int max_slots;             /* most requests in flight at once (1..64) */
+    int use_graph;             /* nonzero: replay each step as one captured CUDA graph */
+} cbct_server_opts;
+
+typedef struct {
+    double submit_s;           /* host steady clock, seconds since the server was created */
+    double admit_s;            /* when the request got a slot */
+    double finish_s;           /* when its result was on the host */
+} cbct_request_times;
+
+/* Starts the worker thread on the current device. */
+cbct_status cbct_server_create(const cbct_server_opts *opts, cbct_server **out);
+/* Queues a request.  desc: the scan (validated like cbct_geometry_create);
+ * b_host: N FP32 measurements on the host, copied before returning; opts:
+ * iters >= 1, lambda = Tikhonov damping, storage must be CBCT_F32 (rule,
+ * use_graph and profile are ignored).  CBCT_EBUDGET if the request alone
+ * needs more than the budget.  *id identifies the request. */
+cbct_status cbct_server_submit(cbct_server *srv, const cbct_geometry_desc *desc, const float *b_host,
+                               cbct_solver solver, const cbct_solve_opts *opts, uint64_t *id);
+/* *done = 1 once the request's result is ready (CBCT_ENOTFOUND for unknown ids). */
+cbct_status cbct_server_poll(cbct_server *srv, uint64_t id, int *done);
+/* Waits up to timeout_s seconds (< 0: forever) for the request.  On time-out
+ * returns CBCT_ETIMEOUT and keeps the request.  Otherwise copies the result
+ * (M FP32 voxels, x[k][j][i]) into x_host, the histories into report (as for
+ * the solvers; may be NULL) and the timestamps into times (may be NULL),
+ * forgets the request and returns its status. */
+cbct_status cbct_server_wait(cbct_server *srv, uint64_t id, double timeout_s, float *x_host,
+                             cbct_solve_report *report, cbct_request_times *times);
+/* Counters: steps run, CUDA-graph replays, bytes currently held, requests in slots and waiting. */
+typedef struct {
+    int64_t steps, graph_replays;
+    size_t bytes_in_use;
+    int active, pending;
+} cbct_server_stats;
+cbct_status cbct_server_get_stats(cbct_server *srv, cbct_server_stats *stats);
+/* Stops the worker, drops waiting and active requests and frees everything. */
+void cbct_server_destroy(cbct_server *srv);
+
 /* Message describing the calling thread's most recent error ("" if none). */
 const char *cbct_last_error(void);
 

@@ -59,6 +59,19 @@ class _Report(ctypes.Structure):
                 ("backward_ms", ctypes.c_double)]
 
 
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class _Times(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("graph_replays", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
+                ("active", ctypes.c_int), ("pending", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -94,6 +107,15 @@ def load(path: str = LIB_PATH):
     lib.cbct_geometry_autotune.argtypes = [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Report), vp]
+    lib.cbct_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(ctypes.c_void_p)]
+    lib.cbct_server_submit.argtypes = [vp, ctypes.POINTER(_Desc), vp, ctypes.c_int, ctypes.POINTER(_Opts),
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    lib.cbct_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+    lib.cbct_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, vp, ctypes.POINTER(_Report),
+                                     ctypes.POINTER(_Times)]
+    lib.cbct_server_get_stats.argtypes = [vp, ctypes.POINTER(_ServerStats)]
+    lib.cbct_server_destroy.argtypes = [vp]
+    lib.cbct_server_destroy.restype = None
     lib.cbct_last_error.restype = ctypes.c_char_p
     lib.cbct_last_error.argtypes = []
     _lib = lib
@@ -121,6 +143,16 @@ def _dtype_code(t):
 
 
 STORAGE = {"f32": F32, "f16": F16, "bf16": BF16, F32: F32, F16: F16, BF16: BF16}
+
+
+def _desc_of(spec):
+    """A cbct_geometry_desc for any object carrying the scan parameters; returns
+    (desc, angles array that must outlive it)."""
+    angles = np.ascontiguousarray(np.asarray(spec.angles, dtype=np.float64))
+    d = _Desc(int(spec.nx), int(spec.ny), int(spec.nz), float(spec.dx), float(spec.dy), float(spec.dz),
+              int(spec.nu), int(spec.nv), float(spec.du), float(spec.dv), float(spec.dso), float(spec.dsd),
+              int(angles.shape[0]), angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return d, angles
 
 
 class Geometry:
@@ -311,3 +343,87 @@ def lsmr(geom, b, iters, lam=0.0, **kw):
 def hybrid_lsqr(geom, b, iters, rule="gcv", lam=0.0, **kw):
     """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lambda_k fixed or by GCV (Sec. 2.2.2)."""
     return _solve("cbct_hybrid_lsqr_solve", geom, b, iters, lam=lam, rule=rule, **kw)
+
+
+# ------------------------------------------------------------------ serving
+@dataclass
+class ServedResult:
+    x: np.ndarray
+    report: SolveReport
+    submit_s: float
+    admit_s: float
+    finish_s: float
+
+
+class Server:
+    """Continuous-batching server (cbct_server_*): requests of different scans
+    are admitted by device-memory budget and advanced together, one Krylov
+    iteration of every admitted request per step."""
+
+    SOLVERS = {"lsqr": 0, "lsmr": 1}
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, use_graph: bool = True):
+        lib = load()
+        o = _ServerOpts(int(hbm_budget_bytes), int(max_slots), 1 if use_graph else 0)
+        h = ctypes.c_void_p()
+        _check("cbct_server_create", lib.cbct_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, spec, b, solver="lsqr", iters=30, lam=0.0) -> int:
+        """Queue one reconstruction; b is copied (host FP32, N values)."""
+        d, angles = _desc_of(spec)
+        bh = np.ascontiguousarray(np.asarray(b, dtype=np.float32))
+        n = int(d.nangles) * d.nv * d.nu
+        if bh.size != n:
+            raise ValueError("b has %d values, expected %d" % (bh.size, n))
+        o = _Opts(int(iters), float(lam), 0, F32, 0, 0)
+        rid = ctypes.c_uint64()
+        _check("cbct_server_submit", load().cbct_server_submit(self._h, ctypes.byref(d), bh.ctypes.data,
+                                                                 self.SOLVERS[solver], ctypes.byref(o),
+                                                                 ctypes.byref(rid)))
+        self._shapes[rid.value] = ((spec.nz, spec.ny, spec.nx), int(iters))
+        return int(rid.value)
+
+    def poll(self, rid: int) -> bool:
+        done = ctypes.c_int()
+        _check("cbct_server_poll", load().cbct_server_poll(self._h, rid, ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, rid: int, timeout: float = -1.0) -> ServedResult:
+        """Block until the request is done (CbctError with status ETIMEOUT on time-out)."""
+        shape, iters = self._shapes[rid]
+        x = np.empty(shape, dtype=np.float32)
+        hr = np.zeros(iters)
+        hn = np.zeros(iters)
+        dp = ctypes.POINTER(ctypes.c_double)
+        rep = _Report(0, hr.ctypes.data_as(dp), hn.ctypes.data_as(dp), None)
+        t = _Times()
+        _check("cbct_server_wait", load().cbct_server_wait(self._h, rid, float(timeout), x.ctypes.data,
+                                                             ctypes.byref(rep), ctypes.byref(t)))
+        del self._shapes[rid]
+        k = rep.iters_done
+        return ServedResult(x, SolveReport(k, hr[:k].copy(), hn[:k].copy()), t.submit_s, t.admit_s, t.finish_s)
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check("cbct_server_get_stats", load().cbct_server_get_stats(self._h, ctypes.byref(st)))
+        return {"steps": st.steps, "graph_replays": st.graph_replays, "bytes_in_use": st.bytes_in_use,
+                "active": st.active, "pending": st.pending}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().cbct_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -127,6 +127,7 @@ __device__ __forceinline__ double block_sum(double v, double *scratch /* NT/32 d
 
 // ---------------------------------------------------------------- host side
 void set_error(const std::string &msg);
+cbct_status validate_geometry_desc(const cbct_geometry_desc *d);   // CBCT_EINVAL with a message
 cbct_status cuda_fail(cudaError_t err, const char *what);
 
 #define CBCT_CUDA_TRY(expr)                                     \

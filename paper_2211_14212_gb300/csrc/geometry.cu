@@ -53,29 +53,40 @@ using namespace cbct;
 
 extern "C" const char *cbct_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_geometry **out) {
-    if (!d || !out) return invalid("cbct_geometry_create: null argument");
-    *out = nullptr;
+namespace cbct {
+
+cbct_status validate_geometry_desc(const cbct_geometry_desc *d) {
+    if (!d) return invalid("geometry: null description");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nu < 1 || d->nv < 1 || d->nangles < 1)
-        return invalid("cbct_geometry_create: every count must be >= 1");
+        return invalid("geometry: every count must be >= 1");
     if (!(d->dx > 0 && d->dy > 0 && d->dz > 0 && d->du > 0 && d->dv > 0))
-        return invalid("cbct_geometry_create: voxel and pixel sizes must be > 0");
+        return invalid("geometry: voxel and pixel sizes must be > 0");
     if (!(d->dso > 0 && d->dsd > d->dso))
-        return invalid("cbct_geometry_create: need 0 < dso < dsd");
-    if (!d->angles_rad) return invalid("cbct_geometry_create: angles_rad is null");
+        return invalid("geometry: need 0 < dso < dsd");
+    if (!d->angles_rad) return invalid("geometry: angles_rad is null");
     const double hx = 0.5 * d->nx * d->dx, hy = 0.5 * d->ny * d->dy;
     const double rcyl = std::sqrt(hx * hx + hy * hy);
     if (!(d->dso > rcyl) || !(d->dsd - d->dso > rcyl))
-        return invalid("cbct_geometry_create: source and detector must lie outside the volume's circumscribed cylinder");
+        return invalid("geometry: source and detector must lie outside the volume's circumscribed cylinder");
     // index ranges: voxels addressed with int32, rays with int64
     if ((int64_t)d->nx * d->ny * d->nz >= (int64_t)1 << 31)
-        return invalid("cbct_geometry_create: more than 2^31-1 voxels");
+        return invalid("geometry: more than 2^31-1 voxels");
     if ((int64_t)d->nu * d->nv >= (int64_t)1 << 31)
-        return invalid("cbct_geometry_create: more than 2^31-1 pixels per projection");
+        return invalid("geometry: more than 2^31-1 pixels per projection");
     if (d->nangles > 65535 || d->nv > 65535 * 4)
-        return invalid("cbct_geometry_create: more than 65535 angles");
+        return invalid("geometry: more than 65535 angles");
     for (int a = 0; a < d->nangles; ++a)
-        if (!std::isfinite(d->angles_rad[a])) return invalid("cbct_geometry_create: non-finite angle");
+        if (!std::isfinite(d->angles_rad[a])) return invalid("geometry: non-finite angle");
+    return CBCT_OK;
+}
+
+}  // namespace cbct
+
+extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_geometry **out) {
+    if (!d || !out) return invalid("cbct_geometry_create: null argument");
+    *out = nullptr;
+    cbct_status vst = validate_geometry_desc(d);
+    if (vst != CBCT_OK) return vst;
 
     const int nx = d->nx, ny = d->ny, nz = d->nz, nu = d->nu, nv = d->nv, na = d->nangles;
     const double dsd = d->dsd, m = d->dso / d->dsd;

@@ -1,0 +1,678 @@
+// Continuous-batching reconstruction server.
+//
+// Requests (a scan, its measured projections b, LSQR or LSMR, an iteration
+// count, optional Tikhonov damping) are admitted into slots while the device
+// memory they need fits a budget.  Every step of the server advances every
+// active slot by one Krylov iteration with persistent multi-instance kernels:
+// one forward launch walks the forward tiles of all slots, one transpose
+// launch walks all their bricks, one launch per scalar step handles all slots
+// (one block each) and one launch updates all their vectors.  A slot finishes,
+// its result is copied out and its memory is freed while the others continue;
+// waiting requests are admitted between steps.  The launch topology of a step
+// does not depend on the mix (fixed persistent grids, a device slot table), so
+// one captured CUDA graph is replayed for every step.
+//
+// Each slot computes exactly what the single-request solver computes: the same
+// tiles, the same per-tile partial sums in the same order, the same scalar
+// steps (gk.cuh).  Only the order of the shared-memory accumulation in the
+// transpose tiles can differ between runs, so a result is the same alone and
+// in a mix up to FP32 rounding.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gk.cuh"
+#include "projector_device.cuh"
+
+namespace cbct {
+
+constexpr int SRV_MAX_SLOTS = 64;
+constexpr int SRV_FWD_ROWS = 2;                       // forward tile: 2 rays per lane
+constexpr int SRV_BX = 16, SRV_BY = 16, SRV_BZ = 32, SRV_BR = 2;   // transpose brick (configuration 0)
+
+struct SlotDev {
+    DevGeom g;
+    float *U, *V, *w, *x, *h2;
+    GkState *st;
+    double *pf, *pb, *hist_r, *hist_n;
+    int method, cap;
+    int fgx, fgy;          // forward tile grid (x: columns / 8, y: row groups); z: angles
+    int bgx, bgy;          // brick grid (x, y); z: bricks along z
+    int64_t m;             // voxels
+};
+
+struct SlotTable {
+    int n;                                  // slots in use (entries 0..n-1)
+    int fwd_start[SRV_MAX_SLOTS + 1];       // prefix sums of forward tiles
+    int bwd_start[SRV_MAX_SLOTS + 1];       // prefix sums of bricks
+    SlotDev s[SRV_MAX_SLOTS];
+};
+
+struct SlotStatus {
+    int iter, stop, status, pad;
+};
+
+// Largest s in [0, n) with start[s] <= item (start is non-decreasing).
+__device__ __forceinline__ int find_slot(const int *start, int n, int item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// U <- fa * A V + fb * U for every slot (forward tiles of all slots).
+__global__ void __launch_bounds__(FWD_THREADS) srv_forward(const SlotTable *tab) {
+    __shared__ double red[FWD_THREADS / 32];
+    const int n = tab->n;
+    const int total = tab->fwd_start[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int s = find_slot(tab->fwd_start, n, item);
+        const SlotDev &sd = tab->s[s];
+        if (sd.st->stop) continue;
+        const int local = item - tab->fwd_start[s];
+        const int tx = local % sd.fgx, ty = (local / sd.fgx) % sd.fgy, a = local / (sd.fgx * sd.fgy);
+        const Epilogue epi{&sd.st->fa, &sd.st->fb, 0.0, 0.0, nullptr, nullptr, nullptr};
+        forward_tile<float, false, SRV_FWD_ROWS>(sd.g, sd.V, sd.U, epi, tx, ty, a, sd.pf + local, red);
+    }
+}
+
+// V <- ba * A^T U + bb * V for every slot (bricks of all slots, z-fastest volumes).
+__global__ void __launch_bounds__(BWD_THREADS) srv_backward(const SlotTable *tab) {
+    __shared__ float sacc[SRV_BX * SRV_BY * SRV_BZ];
+    __shared__ double red[BWD_THREADS / 32];
+    const int n = tab->n;
+    const int total = tab->bwd_start[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int s = find_slot(tab->bwd_start, n, item);
+        const SlotDev &sd = tab->s[s];
+        if (sd.st->stop) continue;
+        const int local = item - tab->bwd_start[s];
+        const int tbx = local % sd.bgx, tby = (local / sd.bgx) % sd.bgy, tbz = local / (sd.bgx * sd.bgy);
+        const Epilogue epi{&sd.st->ba, &sd.st->bb, 0.0, 0.0, nullptr, nullptr, nullptr};
+        backward_tile<float, true, SRV_BX, SRV_BY, SRV_BZ, SRV_BR>(sd.g, sd.U, sd.V, epi, tbx, tby, tbz,
+                                                                    sd.pb + local, sacc, red);
+    }
+}
+
+// Scalar steps, one block per slot, same fixed-order reductions as the solvers.
+__global__ void __launch_bounds__(RED_THREADS) srv_after_forward(const SlotTable *tab) {
+    __shared__ double red[RED_THREADS / 32];
+    const int s = blockIdx.x;
+    if (s >= tab->n) return;
+    const SlotDev &sd = tab->s[s];
+    if (sd.st->stop) return;
+    const double ss = reduce_partials(sd.pf, tab->fwd_start[s + 1] - tab->fwd_start[s], red);
+    if (threadIdx.x == 0) gk_after_forward_step(sd.st, ss, nullptr);
+}
+
+__global__ void __launch_bounds__(RED_THREADS) srv_after_backward(const SlotTable *tab) {
+    __shared__ double red[RED_THREADS / 32];
+    const int s = blockIdx.x;
+    if (s >= tab->n) return;
+    const SlotDev &sd = tab->s[s];
+    if (sd.st->stop) return;
+    const double ss = reduce_partials(sd.pb, tab->bwd_start[s + 1] - tab->bwd_start[s], red);
+    if (threadIdx.x == 0)
+        gk_after_backward_step(sd.st, ss, sd.method, sd.hist_r, sd.hist_n, nullptr, nullptr, sd.cap);
+}
+
+// Vector recurrences of every slot (grid-stride over each slot's voxels).
+__global__ void __launch_bounds__(VEC_THREADS) srv_update(const SlotTable *tab) {
+    const int n = tab->n;
+    const int64_t stride = (int64_t)gridDim.x * VEC_THREADS;
+    for (int s = 0; s < n; ++s) {
+        const SlotDev &sd = tab->s[s];
+        const GkState *st = sd.st;
+        if (st->stop) continue;
+        const float k1 = (float)st->k1, k2 = (float)st->k2, k3 = (float)st->k3, k4 = (float)st->k4;
+        for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < sd.m; i += stride) {
+            if (sd.method == M_LSQR) lsqr_elem(sd.V[i], sd.x[i], sd.w[i], k1, k2, k3);
+            else lsmr_elem(sd.V[i], sd.x[i], sd.w[i], sd.h2[i], k1, k2, k3, k4);
+        }
+    }
+}
+
+__global__ void srv_status(const SlotTable *tab, SlotStatus *out) {
+    const int s = threadIdx.x;
+    if (s >= tab->n) return;
+    const GkState *st = tab->s[s].st;
+    out[s] = SlotStatus{st->iter, st->stop, st->status, 0};
+}
+
+// ====================================================================== host
+
+namespace {
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+struct Request {
+    uint64_t id = 0;
+    cbct_geometry_desc desc{};
+    std::vector<double> angles;
+    std::vector<float> b;
+    int method = M_LSQR;
+    int iters = 0;
+    double damp = 0.0;
+    size_t bytes = 0;
+    // results
+    bool admitted = false;
+    bool done = false;
+    cbct_status status = CBCT_OK;
+    std::string error;
+    std::vector<float> x;
+    std::vector<double> hist_r, hist_n;
+    int iters_done = 0;
+    double t_submit = 0, t_admit = 0, t_finish = 0;
+};
+
+struct Slot {
+    std::shared_ptr<Request> req;
+    cbct_geometry *geom = nullptr;
+    float *U = nullptr, *V = nullptr, *w = nullptr, *x = nullptr, *h2 = nullptr, *b = nullptr;
+    GkState *st = nullptr;
+    double *pf = nullptr, *pb = nullptr, *hist = nullptr;
+    int nf = 0, nb = 0, steps = 0;
+};
+
+// Forward tiles and bricks of a scan under the server's launch shapes.
+void grids(const cbct_geometry_desc &d, int &fgx, int &fgy, int &bgx, int &bgy, int &bgz) {
+    fgx = (d.nu + FWD_COLS - 1) / FWD_COLS;
+    fgy = (d.nv + 32 * SRV_FWD_ROWS - 1) / (32 * SRV_FWD_ROWS);
+    bgx = (d.nx + SRV_BX - 1) / SRV_BX;
+    bgy = (d.ny + SRV_BY - 1) / SRV_BY;
+    bgz = (d.nz + SRV_BZ - 1) / SRV_BZ;
+}
+
+// Device memory a request holds at its peak (ray tables, Krylov vectors,
+// staging of b, partial sums, state and histories), rounded up per buffer.
+size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
+    auto al = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
+    const size_t n = (size_t)d.nangles * d.nv * d.nu, m = (size_t)d.nx * d.ny * d.nz;
+    int fgx, fgy, bgx, bgy, bgz;
+    grids(d, fgx, fgy, bgx, bgy, bgz);
+    const size_t nf = (size_t)fgx * fgy * d.nangles, nb = (size_t)bgx * bgy * bgz;
+    size_t t = al((size_t)d.nangles * d.nu * 24) + al((size_t)d.nv * 16) + al(n / d.nangles * 4) + al(d.nangles * 8);
+    t += 2 * al(n * 4);                                     // U and the staged b
+    t += al(m * 4) * (method == M_LSMR ? 4 : 3);            // V, w, x (+ hbar)
+    t += al(nf * 8) + al(nb * 8) + al(sizeof(GkState)) + al((size_t)2 * iters * 8);
+    t += al(m * 4);                                         // re-layout of x when the result is read out
+    return t;
+}
+
+}  // namespace
+
+struct ServerImpl {
+    size_t budget = 0, in_use = 0;
+    int max_slots = 1, use_graph = 1, device = 0;
+    std::chrono::steady_clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::map<uint64_t, std::shared_ptr<Request>> requests;
+    uint64_t next_id = 1;
+    bool stopping = false;
+    std::thread worker;
+    // worker-owned
+    cudaStream_t s = nullptr;
+    SlotTable *tab_host = nullptr, *tab_dev = nullptr;
+    SlotStatus *stat_host = nullptr, *stat_dev = nullptr;
+    std::vector<Slot> slots;
+    bool table_dirty = true;
+    cudaGraphExec_t step_graph = nullptr;
+    int fwd_grid = 0, bwd_grid = 0, vec_grid = 0;
+    int64_t steps_run = 0, graph_replays = 0;
+
+    void run();
+    cbct_status setup_slot(Slot &sl);
+    void release_slot(Slot &sl);
+    cbct_status finish_slot(Slot &sl);
+    cbct_status enqueue_step();
+    void fail_all(cbct_status st, const std::string &msg);
+};
+
+// -------------------------------------------------------------- slot life
+
+cbct_status ServerImpl::setup_slot(Slot &sl) {
+    Request &r = *sl.req;
+    r.desc.angles_rad = r.angles.data();
+    cbct_status st = cbct_geometry_create(&r.desc, &sl.geom);
+    if (st != CBCT_OK) return st;
+    sl.geom->dev.fwd_rows = SRV_FWD_ROWS;
+    sl.geom->dev.bwd_config = 0;
+    const DevGeom &g = sl.geom->dev;
+    const int64_t n = cbct_geometry_num_rays(sl.geom), m = cbct_geometry_num_voxels(sl.geom);
+    sl.nf = forward_num_blocks(g);
+    sl.nb = backward_num_blocks(g);
+    auto A = [&](auto **p, size_t cnt) {
+        return cudaMallocAsync((void **)p, cnt * sizeof(**p) + 16, s);
+    };
+    cudaError_t e = A(&sl.U, (size_t)n);
+    if (e == cudaSuccess) e = A(&sl.b, (size_t)n);
+    if (e == cudaSuccess) e = A(&sl.V, (size_t)m);
+    if (e == cudaSuccess) e = A(&sl.w, (size_t)m);
+    if (e == cudaSuccess) e = A(&sl.x, (size_t)m);
+    if (e == cudaSuccess && r.method == M_LSMR) e = A(&sl.h2, (size_t)m);
+    if (e == cudaSuccess) e = A(&sl.pf, (size_t)std::max(sl.nf, VEC_BLOCKS));
+    if (e == cudaSuccess) e = A(&sl.pb, (size_t)sl.nb);
+    if (e == cudaSuccess) e = A(&sl.st, (size_t)1);
+    if (e == cudaSuccess) e = A(&sl.hist, (size_t)2 * r.iters);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.b, r.b.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl.x, 0, sizeof(float) * m, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl.hist, 0, sizeof(double) * 2 * r.iters, s);
+    GkState init;
+    std::memset(&init, 0, sizeof init);
+    init.damp = r.damp;
+    init.sqrt_n = std::sqrt((double)n);
+    init.sqrt_m = std::sqrt((double)m);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.st, &init, sizeof init, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "server: slot allocation");
+    // beta_1 u_1 = b, alpha_1 v_1 = A^T u_1: the same start as the single-request solver
+    k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.b, n, sl.pf);
+    gk_begin<<<1, RED_THREADS, 0, s>>>(sl.st, sl.pf, VEC_BLOCKS);
+    k_scale_to<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.b, sl.U, n, &sl.st->c0, &sl.st->stop);
+    Epilogue eb{&sl.st->ba, &sl.st->bb, 0.0, 0.0, sl.pb, &sl.st->stop, nullptr};
+    st = launch_backward(g, sl.U, sl.V, CBCT_F32, eb, s, true);
+    if (st != CBCT_OK) return st;
+    gk_begin2<<<1, RED_THREADS, 0, s>>>(sl.st, sl.pb, sl.nb, r.method);
+    k_start_dirs<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.V, sl.w, r.method == M_LSMR ? sl.h2 : nullptr, nullptr,
+                                                           m, sl.st);
+    CBCT_CUDA_TRY(cudaGetLastError());
+    CBCT_CUDA_TRY(cudaFreeAsync(sl.b, s));
+    sl.b = nullptr;
+    return CBCT_OK;
+}
+
+void ServerImpl::release_slot(Slot &sl) {
+    for (void *p : {(void *)sl.U, (void *)sl.b, (void *)sl.V, (void *)sl.w, (void *)sl.x, (void *)sl.h2,
+                    (void *)sl.pf, (void *)sl.pb, (void *)sl.st, (void *)sl.hist})
+        if (p) cudaFreeAsync(p, s);
+    sl.U = sl.b = sl.V = sl.w = sl.x = sl.h2 = nullptr;
+    sl.pf = sl.pb = sl.hist = nullptr;
+    sl.st = nullptr;
+    if (sl.geom) {
+        cudaStreamSynchronize(s);
+        cbct_geometry_destroy(sl.geom);
+        sl.geom = nullptr;
+    }
+}
+
+// Read out a finished slot: x (caller layout), histories and final state.
+cbct_status ServerImpl::finish_slot(Slot &sl) {
+    Request &r = *sl.req;
+    const int64_t m = cbct_geometry_num_voxels(sl.geom);
+    float *tmp = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(float) * m, s));
+    cbct_status st = launch_relayout(sl.geom->dev, sl.x, tmp, CBCT_F32, false, s);
+    r.x.assign((size_t)m, 0.0f);
+    r.hist_r.assign((size_t)r.iters, 0.0);
+    r.hist_n.assign((size_t)r.iters, 0.0);
+    GkState fin;
+    cudaError_t e = cudaSuccess;
+    if (st == CBCT_OK) e = cudaMemcpyAsync(r.x.data(), tmp, sizeof(float) * m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r.hist_r.data(), sl.hist, sizeof(double) * r.iters, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r.hist_n.data(), sl.hist + r.iters, sizeof(double) * r.iters, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&fin, sl.st, sizeof fin, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(tmp, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st != CBCT_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "server: read-out");
+    r.iters_done = fin.iter;
+    r.status = (cbct_status)fin.status;
+    if (r.status == CBCT_EBREAKDOWN) r.error = "Krylov breakdown: a norm became zero or non-finite";
+    return CBCT_OK;
+}
+
+// One Krylov iteration of every slot, then the per-slot status to the host.
+cbct_status ServerImpl::enqueue_step() {
+    auto launch_all = [&]() -> cudaError_t {
+        srv_forward<<<fwd_grid, FWD_THREADS, 0, s>>>(tab_dev);
+        srv_after_forward<<<SRV_MAX_SLOTS, RED_THREADS, 0, s>>>(tab_dev);
+        srv_backward<<<bwd_grid, BWD_THREADS, 0, s>>>(tab_dev);
+        srv_after_backward<<<SRV_MAX_SLOTS, RED_THREADS, 0, s>>>(tab_dev);
+        srv_update<<<vec_grid, VEC_THREADS, 0, s>>>(tab_dev);
+        srv_status<<<1, SRV_MAX_SLOTS, 0, s>>>(tab_dev, stat_dev);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(stat_host, stat_dev, sizeof(SlotStatus) * SRV_MAX_SLOTS, cudaMemcpyDeviceToHost, s);
+        return e;
+    };
+    if (use_graph && !step_graph) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = launch_all();
+            e = cudaStreamEndCapture(s, &graph);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&step_graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {             // fall back to plain launches
+            (void)cudaGetLastError();
+            step_graph = nullptr;
+            use_graph = 0;
+        }
+    }
+    if (use_graph && step_graph) {
+        CBCT_CUDA_TRY(cudaGraphLaunch(step_graph, s));
+        ++graph_replays;
+        return CBCT_OK;
+    }
+    CBCT_CUDA_TRY(launch_all());
+    return CBCT_OK;
+}
+
+void ServerImpl::fail_all(cbct_status st, const std::string &msg) {
+    std::vector<Slot> dead;
+    dead.swap(slots);
+    for (Slot &sl : dead) release_slot(sl);
+    std::lock_guard<std::mutex> lk(mu);
+    for (Slot &sl : dead) {
+        sl.req->status = st;
+        sl.req->error = msg;
+        sl.req->done = true;
+        sl.req->t_finish = now_s(t0);
+        in_use -= sl.req->bytes;
+    }
+    table_dirty = true;
+    cv_done.notify_all();
+}
+
+// ------------------------------------------------------------------ worker
+
+void ServerImpl::run() {
+    cudaSetDevice(device);
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> admit;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stopping) break;
+            while (!pending.empty() && (int)(slots.size() + admit.size()) < max_slots &&
+                   in_use + pending.front()->bytes <= budget) {
+                std::shared_ptr<Request> r = pending.front();
+                pending.pop_front();
+                in_use += r->bytes;
+                r->t_admit = now_s(t0);
+                r->admitted = true;
+                admit.push_back(r);
+            }
+            if (slots.empty() && admit.empty()) {
+                cv_work.wait_for(lk, std::chrono::milliseconds(50));
+                continue;
+            }
+        }
+        for (std::shared_ptr<Request> &r : admit) {
+            Slot sl;
+            sl.req = r;
+            cbct_status st = setup_slot(sl);
+            if (st != CBCT_OK) {
+                const std::string msg = cbct_last_error();
+                release_slot(sl);
+                std::lock_guard<std::mutex> lk(mu);
+                r->status = st;
+                r->error = msg;
+                r->done = true;
+                r->t_finish = now_s(t0);
+                in_use -= r->bytes;
+                cv_done.notify_all();
+                continue;
+            }
+            slots.push_back(sl);
+            table_dirty = true;
+        }
+        if (slots.empty()) continue;
+        if (table_dirty) {
+            SlotTable &t = *tab_host;
+            t.n = (int)slots.size();
+            t.fwd_start[0] = t.bwd_start[0] = 0;
+            for (int i = 0; i < t.n; ++i) {
+                const Slot &sl = slots[i];
+                SlotDev &d = t.s[i];
+                d.g = sl.geom->dev;
+                d.U = sl.U; d.V = sl.V; d.w = sl.w; d.x = sl.x; d.h2 = sl.h2;
+                d.st = sl.st;
+                d.pf = sl.pf; d.pb = sl.pb;
+                d.hist_r = sl.hist; d.hist_n = sl.hist + sl.req->iters;
+                d.method = sl.req->method;
+                d.cap = sl.req->iters;
+                const dim3 fg = forward_grid(d.g), bg = backward_grid(d.g);
+                d.fgx = fg.x; d.fgy = fg.y; d.bgx = bg.x; d.bgy = bg.y;
+                d.m = cbct_geometry_num_voxels(sl.geom);
+                t.fwd_start[i + 1] = t.fwd_start[i] + sl.nf;
+                t.bwd_start[i + 1] = t.bwd_start[i] + sl.nb;
+            }
+            if (cudaMemcpyAsync(tab_dev, tab_host, sizeof(SlotTable), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                fail_all(cuda_fail(cudaGetLastError(), "server: slot table"), cbct_last_error());
+                continue;
+            }
+            table_dirty = false;
+        }
+        cbct_status st = enqueue_step();
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (st != CBCT_OK || e != cudaSuccess) {
+            if (e != cudaSuccess) st = cuda_fail(e, "server: step");
+            fail_all(st, cbct_last_error());
+            continue;
+        }
+        ++steps_run;
+        for (int i = (int)slots.size() - 1; i >= 0; --i) {
+            Slot &sl = slots[i];
+            ++sl.steps;
+            if (!stat_host[i].stop && sl.steps < sl.req->iters) continue;
+            cbct_status fs = finish_slot(sl);
+            const std::string msg = fs == CBCT_OK ? sl.req->error : std::string(cbct_last_error());
+            std::shared_ptr<Request> r = sl.req;
+            release_slot(sl);
+            slots.erase(slots.begin() + i);
+            table_dirty = true;
+            std::lock_guard<std::mutex> lk(mu);
+            if (fs != CBCT_OK) r->status = fs;
+            r->error = msg;
+            r->done = true;
+            r->t_finish = now_s(t0);
+            in_use -= r->bytes;
+            cv_done.notify_all();
+        }
+    }
+    for (Slot &sl : slots) release_slot(sl);
+    slots.clear();
+    cudaStreamSynchronize(s);
+}
+
+}  // namespace cbct
+
+using namespace cbct;
+
+struct cbct_server {
+    ServerImpl impl;
+};
+
+extern "C" cbct_status cbct_server_create(const cbct_server_opts *o, cbct_server **out) {
+    if (!o || !out) { set_error("cbct_server_create: null argument"); return CBCT_EINVAL; }
+    *out = nullptr;
+    if (o->hbm_budget_bytes == 0 || o->max_slots < 1 || o->max_slots > SRV_MAX_SLOTS) {
+        set_error("cbct_server_create: need hbm_budget_bytes > 0 and 1 <= max_slots <= 64");
+        return CBCT_EINVAL;
+    }
+    cbct_server *srv = new (std::nothrow) cbct_server();
+    if (!srv) { set_error("cbct_server_create: out of host memory"); return CBCT_ENOMEM; }
+    ServerImpl &S = srv->impl;
+    S.budget = o->hbm_budget_bytes;
+    S.max_slots = o->max_slots;
+    S.use_graph = o->use_graph != 0;
+    S.t0 = std::chrono::steady_clock::now();
+    cudaError_t e = cudaGetDevice(&S.device);
+    int sms = 0, occ_f = 0, occ_b = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S.device);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, srv_forward, FWD_THREADS, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, srv_backward, BWD_THREADS, 0);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost(&S.tab_host, sizeof(SlotTable));
+    if (e == cudaSuccess) e = cudaMalloc(&S.tab_dev, sizeof(SlotTable));
+    if (e == cudaSuccess) e = cudaMallocHost(&S.stat_host, sizeof(SlotStatus) * SRV_MAX_SLOTS);
+    if (e == cudaSuccess) e = cudaMalloc(&S.stat_dev, sizeof(SlotStatus) * SRV_MAX_SLOTS);
+    if (e != cudaSuccess) {
+        cbct_status st = cuda_fail(e, "cbct_server_create");
+        if (S.tab_host) cudaFreeHost(S.tab_host);
+        if (S.tab_dev) cudaFree(S.tab_dev);
+        if (S.stat_host) cudaFreeHost(S.stat_host);
+        if (S.stat_dev) cudaFree(S.stat_dev);
+        if (S.s) cudaStreamDestroy(S.s);
+        delete srv;
+        return st;
+    }
+    std::memset(S.tab_host, 0, sizeof(SlotTable));
+    S.fwd_grid = sms * std::max(occ_f, 1);
+    S.bwd_grid = sms * std::max(occ_b, 1);
+    S.vec_grid = sms * 4;
+    try {
+        S.worker = std::thread([&S] { S.run(); });
+    } catch (...) {
+        set_error("cbct_server_create: cannot start the worker thread");
+        cudaFreeHost(S.tab_host);
+        cudaFree(S.tab_dev);
+        cudaFreeHost(S.stat_host);
+        cudaFree(S.stat_dev);
+        cudaStreamDestroy(S.s);
+        delete srv;
+        return CBCT_ENOMEM;
+    }
+    *out = srv;
+    return CBCT_OK;
+}
+
+extern "C" cbct_status cbct_server_submit(cbct_server *srv, const cbct_geometry_desc *desc, const float *b_host,
+                                          cbct_solver solver, const cbct_solve_opts *o, uint64_t *id) {
+    if (!srv || !desc || !b_host || !o || !id) { set_error("cbct_server_submit: null argument"); return CBCT_EINVAL; }
+    if (solver != CBCT_SOLVER_LSQR && solver != CBCT_SOLVER_LSMR) {
+        set_error("cbct_server_submit: solver must be LSQR or LSMR");
+        return CBCT_EINVAL;
+    }
+    if (o->iters < 1 || o->storage != CBCT_F32 || !(o->lambda >= 0.0) || !std::isfinite(o->lambda)) {
+        set_error("cbct_server_submit: need iters >= 1, FP32 storage and a finite lambda >= 0");
+        return CBCT_EINVAL;
+    }
+    cbct_status st = validate_geometry_desc(desc);
+    if (st != CBCT_OK) return st;
+    ServerImpl &S = srv->impl;
+    const int method = solver == CBCT_SOLVER_LSQR ? M_LSQR : M_LSMR;
+    const size_t bytes = request_bytes(*desc, method, o->iters);
+    if (bytes > S.budget) {
+        set_error("cbct_server_submit: the request needs more device memory than the server's budget");
+        return CBCT_EBUDGET;
+    }
+    std::shared_ptr<Request> r;
+    try {
+        r = std::make_shared<Request>();
+        r->desc = *desc;
+        r->angles.assign(desc->angles_rad, desc->angles_rad + desc->nangles);
+        const size_t n = (size_t)desc->nangles * desc->nv * desc->nu;
+        r->b.assign(b_host, b_host + n);
+    } catch (...) {
+        set_error("cbct_server_submit: out of host memory");
+        return CBCT_ENOMEM;
+    }
+    r->method = method;
+    r->iters = o->iters;
+    r->damp = o->lambda;
+    r->bytes = bytes;
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        r->t_submit = now_s(S.t0);
+        r->id = S.next_id++;
+        S.requests[r->id] = r;
+        S.pending.push_back(r);
+        *id = r->id;
+    }
+    S.cv_work.notify_one();
+    return CBCT_OK;
+}
+
+extern "C" cbct_status cbct_server_poll(cbct_server *srv, uint64_t id, int *done) {
+    if (!srv || !done) { set_error("cbct_server_poll: null argument"); return CBCT_EINVAL; }
+    std::lock_guard<std::mutex> lk(srv->impl.mu);
+    auto it = srv->impl.requests.find(id);
+    if (it == srv->impl.requests.end()) { set_error("cbct_server_poll: unknown request"); return CBCT_ENOTFOUND; }
+    *done = it->second->done ? 1 : 0;
+    return CBCT_OK;
+}
+
+extern "C" cbct_status cbct_server_wait(cbct_server *srv, uint64_t id, double timeout_s, float *x_host,
+                                        cbct_solve_report *rep, cbct_request_times *times) {
+    if (!srv) { set_error("cbct_server_wait: null server"); return CBCT_EINVAL; }
+    ServerImpl &S = srv->impl;
+    std::unique_lock<std::mutex> lk(S.mu);
+    auto it = S.requests.find(id);
+    if (it == S.requests.end()) { set_error("cbct_server_wait: unknown request"); return CBCT_ENOTFOUND; }
+    std::shared_ptr<Request> r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_s < 0.0) {
+        S.cv_done.wait(lk, ready);
+    } else if (!S.cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
+        set_error("cbct_server_wait: request not finished within the time-out");
+        return CBCT_ETIMEOUT;
+    }
+    if (x_host && !r->x.empty()) std::memcpy(x_host, r->x.data(), sizeof(float) * r->x.size());
+    if (rep) {
+        rep->iters_done = r->iters_done;
+        const int c = std::min(r->iters_done, r->iters);
+        if (rep->resid_norm && c > 0) std::memcpy(rep->resid_norm, r->hist_r.data(), sizeof(double) * c);
+        if (rep->normal_resid_norm && c > 0) std::memcpy(rep->normal_resid_norm, r->hist_n.data(), sizeof(double) * c);
+        rep->kernel_launches = rep->forward_launches = rep->backward_launches = 0;
+        rep->forward_ms = rep->backward_ms = 0.0;
+    }
+    if (times) *times = cbct_request_times{r->t_submit, r->t_admit, r->t_finish};
+    const cbct_status st = r->status;
+    if (st != CBCT_OK) set_error(r->error);
+    S.requests.erase(it);
+    return st;
+}
+
+extern "C" cbct_status cbct_server_get_stats(cbct_server *srv, cbct_server_stats *out) {
+    if (!srv || !out) { set_error("cbct_server_get_stats: null argument"); return CBCT_EINVAL; }
+    ServerImpl &S = srv->impl;
+    std::lock_guard<std::mutex> lk(S.mu);
+    out->steps = S.steps_run;
+    out->graph_replays = S.graph_replays;
+    out->bytes_in_use = S.in_use;
+    out->pending = (int)S.pending.size();
+    int active = 0;
+    for (auto &kv : S.requests)
+        if (!kv.second->done && kv.second->admitted) ++active;
+    out->active = active;
+    return CBCT_OK;
+}
+
+extern "C" void cbct_server_destroy(cbct_server *srv) {
+    if (!srv) return;
+    ServerImpl &S = srv->impl;
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.stopping = true;
+    }
+    S.cv_work.notify_all();
+    if (S.worker.joinable()) S.worker.join();
+    if (S.step_graph) cudaGraphExecDestroy(S.step_graph);
+    cudaStreamSynchronize(S.s);
+    cudaFreeHost(S.tab_host);
+    cudaFree(S.tab_dev);
+    cudaFreeHost(S.stat_host);
+    cudaFree(S.stat_dev);
+    cudaStreamDestroy(S.s);
+    delete srv;
+}

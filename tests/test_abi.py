@@ -77,3 +77,18 @@ def test_launch_shape_calls_reject_null(lib):
     assert lib.cbct_geometry_set_launch(None, 2, 0) == cbct.CBCT_EINVAL
     assert lib.cbct_geometry_get_launch(None, None, None) == cbct.CBCT_EINVAL
     assert lib.cbct_geometry_autotune(None, 8, None, None) == cbct.CBCT_EINVAL
+
+
+def test_server_argument_checks(lib):
+    from paper_2211_14212_gb300 import cbct
+    h = ctypes.c_void_p()
+    assert lib.cbct_server_create(None, ctypes.byref(h)) == cbct.CBCT_EINVAL
+    for budget, slots in ((0, 4), (1 << 30, 0), (1 << 30, 65)):
+        o = cbct._ServerOpts(budget, slots, 1)
+        assert lib.cbct_server_create(ctypes.byref(o), ctypes.byref(h)) == cbct.CBCT_EINVAL
+    rid = ctypes.c_uint64()
+    assert lib.cbct_server_submit(None, None, None, 0, None, ctypes.byref(rid)) == cbct.CBCT_EINVAL
+    done = ctypes.c_int()
+    assert lib.cbct_server_poll(None, 1, ctypes.byref(done)) == cbct.CBCT_EINVAL
+    assert lib.cbct_server_wait(None, 1, 0.0, None, None, None) == cbct.CBCT_EINVAL
+    lib.cbct_server_destroy(None)

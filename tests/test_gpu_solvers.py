@@ -80,8 +80,8 @@ SENS_FACTOR = 30.0
 def drift_check(cbct_fn, g, b, method, iters, ks, hist=None, **kw):
     """Compare GPU iterates x_k (k in ks) with the FP64 oracle's; the bar at k is
     max(1e-4, SENS_FACTOR x the oracle's own sensitivity to FP32 rounding of A).
-    The GPU residual history `hist` (if given) is held to the same bar,
-    relative to the oracle's residual at each iteration."""
+    The GPU residual history `hist` (if given) is held to 1e-4 relative where
+    that sensitivity is below 1e-5 and to a few per cent beyond."""
     h_exact = oracle_solve(g, b, method, iters, keep_iterates=True, **kw)[1]
     exact = h_exact["iterates"]
     key = (id(g), method, iters, "rounded", tuple(sorted(kw.items())))
@@ -101,8 +101,11 @@ def drift_check(cbct_fn, g, b, method, iters, ks, hist=None, **kw):
     # the 1e-4 bar itself applies wherever FP32 can meet it
     assert any(rel(rounded[k - 1], exact[k - 1]) < 1e-5 for k in ks)
     if hist is not None:
+        # residual estimates come out of longer recurrences than the iterates: 1e-4 where
+        # the problem is well conditioned for FP32 (sensitivity < 1e-5), a few per cent beyond
         for k in range(1, iters + 1):
-            bar = max(ITER_TOL, SENS_FACTOR * rel(rounded[k - 1], exact[k - 1]))
+            sens = rel(rounded[k - 1], exact[k - 1])
+            bar = ITER_TOL if sens < 1e-5 else max(0.05, SENS_FACTOR * sens)
             ref = h_exact["resid"][k - 1]
             assert abs(hist[k - 1] - ref) <= bar * ref, (k, hist[k - 1], ref, bar)
 
