@@ -106,9 +106,10 @@ cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream 
 /* Launch shapes of the projectors of one geometry (performance only: every
  * shape computes the same A and A^T).  fwd_rows: rays per lane of the forward
  * tile (1, 2 or 4; a warp follows 32 * fwd_rows rows of one detector column).
- * bwd_config: brick of the transpose tile, 0 = 16x16x32 voxels / 2 rays per
- * lane, 1 = 16x16x16 / 1, 2 = 8x8x64 / 2, 3 = 32x16x16 / 1.  Changing the shape
- * while another thread uses the geometry is a data race. */
+ * bwd_config: tile of the transpose (one warp per voxel column), 0 = 4 x 2
+ * columns x 32 voxels along z (1 per lane), 1 = 4 x 2 x 64 (2 per lane),
+ * 2 = 8 x 1 x 32, 3 = 2 x 4 x 64.  Changing the shape while another thread
+ * uses the geometry is a data race. */
 #define CBCT_TUNE_TIMES 7
 cbct_status cbct_geometry_set_launch(cbct_geometry *geom, int fwd_rows, int bwd_config);
 cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, int *bwd_config);

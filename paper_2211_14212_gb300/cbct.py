@@ -244,7 +244,7 @@ def count_nnz(geom: Geometry, stream=None) -> int:
 
 TUNE_TIMES = 7
 FWD_ROWS = (1, 2, 4)
-BWD_CONFIGS = ("16x16x32/2", "16x16x16/1", "8x8x64/2", "32x16x16/1")
+BWD_CONFIGS = ("4x2 columns x 32", "4x2 columns x 64", "8x1 columns x 32", "2x4 columns x 64")
 
 
 def set_launch(geom: Geometry, fwd_rows: int, bwd_config: int):

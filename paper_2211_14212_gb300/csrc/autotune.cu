@@ -1,5 +1,5 @@
 // Launch-shape autotuner: per geometry, the forward tile's rays per lane and
-// the transpose tile's brick shape are chosen by timing every candidate on a
+// the transpose tile's shape are chosen by timing every candidate on a
 // strided subset of the scan's angles (the work per angle is what the shape
 // changes; the angle count only scales it).
 #include <cfloat>
@@ -93,7 +93,7 @@ extern "C" cbct_status cbct_geometry_autotune(cbct_geometry *g, int max_angles, 
         const Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
         for (int c = 0; c < NUM_FWD_ROWS && st == CBCT_OK; ++c) {
             t->dev.fwd_rows = kFwdRows[c];
-            st = time_best([&] { return launch_forward(t->dev, x, y, CBCT_F32, epi, s); }, 2, s, e0, e1, &tf[c]);
+            st = time_best([&] { return launch_forward(t->dev, x, y, CBCT_F32, epi, s, true); }, 2, s, e0, e1, &tf[c]);
         }
         for (int c = 0; c < NUM_BWD_CONFIGS && st == CBCT_OK; ++c) {
             t->dev.bwd_config = c;

@@ -27,7 +27,7 @@ namespace cbct {
 // columns near the centre at 0/90/180/270 degrees) keep their crossings in
 // place.  I == 0 marks a ray exactly parallel to that axis' planes; pq then
 // holds its (fixed) voxel index.  The length of the ray/voxel segment
-// [alpha0, alpha1] is (alpha1 - alpha0) * ray_len[iv][iu].
+// [alpha0, alpha1] is (alpha1 - alpha0) * ray_len[iu][iv].
 //
 // Forward and transposed kernels derive every alpha from these tables with
 // the same two rounded operations (plane_alpha), so the segment lengths they
@@ -43,13 +43,14 @@ struct DevGeom {
     const float4 *ray_xy;    // [nangles][nu]: (fx, Ix, fy, Iy)
     const float2 *ray_xyq;   // [nangles][nu]: (pqx, pqy)
     const float4 *ray_z;     // [nv]: (fz, Iz, pqz, 0)
-    const float *ray_len;    // [nv][nu]
+    const float *ray_len;    // [nu][nv]
     const float2 *trig;      // [nangles] (cos t, sin t), for footprint windows only
     int fwd_rows;            // forward tile: rays per lane (1, 2 or 4)
     int bwd_config;          // transpose tile: brick shape / rays per lane (backward_shape)
 };
 
-// Brick of the transpose tile: bx x by x bz voxels, r rays per lane.
+// Tile of the transpose: a bx x by patch of voxel columns (one warp each),
+// bz = 32 r voxels along z (r per lane).
 struct BrickShape {
     int bx, by, bz, r;
 };
@@ -137,15 +138,19 @@ cbct_status cuda_fail(cudaError_t err, const char *what);
     } while (0)
 
 // Kernel launchers (projector.cu).  All return CBCT_OK or a CUDA failure.
-// launch_forward reads a z-fastest volume x[j][i][k].
-cbct_status launch_forward(const DevGeom &g, const void *x, void *y, cbct_dtype t,
-                           const Epilogue &epi, cudaStream_t s);
-// Volumes: the forward kernel reads, and the solvers keep, the z-fastest layout
-// x[j][i][k]; the ABI uses x[k][j][i].  launch_backward writes either.
-cbct_status launch_backward(const DevGeom &g, const void *y, void *x, cbct_dtype t,
+cbct_status launch_forward(const DevGeom &g, const void *x_zfast, void *y, cbct_dtype t,
+                           const Epilogue &epi, cudaStream_t s, bool vfast);
+// Layouts: the ABI uses x[k][j][i] and y[a][iv][iu].  The forward kernel reads
+// volumes z-fastest, x[j][i][k], and the transpose reads projections
+// v-fastest, y[a][iu][iv]; the solvers keep their vectors in those layouts.
+// launch_forward writes either projection layout, launch_backward either
+// volume layout.
+cbct_status launch_backward(const DevGeom &g, const void *y_vfast, void *x, cbct_dtype t,
                             const Epilogue &epi, cudaStream_t s, bool zfast);
 cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_zfast,
                             cudaStream_t s);
+cbct_status launch_proj_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_vfast,
+                                 cudaStream_t s);
 cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaStream_t s);
 int forward_num_blocks(const DevGeom &g);
 int backward_num_blocks(const DevGeom &g);

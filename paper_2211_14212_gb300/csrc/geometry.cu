@@ -120,7 +120,7 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
         zt[iv] = e;
         for (int iu = 0; iu < nu; ++iu) {
             const double u = (iu - 0.5 * (nu - 1)) * d->du;
-            len[(size_t)iv * nu + iu] = (float)std::sqrt(dsd * dsd + u * u + v * v);
+            len[(size_t)iu * nv + iv] = (float)std::sqrt(dsd * dsd + u * u + v * v);
         }
     }
 

@@ -1,11 +1,12 @@
 // Cone-beam projectors for sm_103a: the Siddon forward projection y = A x
 // (Sec. 1, Eq. 1: one ray per detector pixel) and its exact transpose
 // x = A^T y, as plain grids of the tiles defined in projector_device.cuh
-// (ray-column warps, shared x/y stepping, bricks of A^T in shared memory).
+// (ray-column warps sharing x/y stepping; the transpose gathers per voxel).
 //
-// Launch shapes are per geometry: DevGeom::fwd_rows (R rays per lane of the
-// forward tile) and DevGeom::bwd_config (brick shape and R of the transpose),
-// set to defaults at creation and chosen by cbct_geometry_autotune.
+// Launch shapes are per geometry: DevGeom::fwd_rows (rays per lane of the
+// forward tile) and DevGeom::bwd_config (column patch and voxels per lane of
+// the transpose tile), set to defaults at creation and chosen by
+// cbct_geometry_autotune.
 #include <cfloat>
 #include <cmath>
 
@@ -15,14 +16,14 @@ namespace cbct {
 
 // ------------------------------------------------------------- forward A x
 
-template <typename T, bool COMP, int R>
+template <typename T, bool COMP, int R, bool VF>
 __global__ void __launch_bounds__(FWD_THREADS)
 forward_kernel(DevGeom g, const T *__restrict__ vol, T *__restrict__ proj, Epilogue epi) {
     __shared__ double red[FWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    forward_tile<T, COMP, R>(g, vol, proj, epi, blockIdx.x, blockIdx.y, blockIdx.z,
-                             epi.partial ? epi.partial + b : nullptr, red);
+    forward_tile<T, COMP, R, VF>(g, vol, proj, epi, blockIdx.x, blockIdx.y, blockIdx.z,
+                                 epi.partial ? epi.partial + b : nullptr, red);
 }
 
 template <int R>
@@ -52,31 +53,40 @@ int forward_num_blocks(const DevGeom &g) {
     return (int)(gr.x * gr.y * gr.z);
 }
 
-template <int R>
+template <int R, bool VF>
 static void launch_forward_r(const DevGeom &g, const void *x, void *y, cbct_dtype t, const Epilogue &epi,
                              cudaStream_t s) {
     const dim3 grid = forward_grid(g);
     switch (t) {
     case CBCT_F32:
-        forward_kernel<float, false, R><<<grid, FWD_THREADS, 0, s>>>(g, (const float *)x, (float *)y, epi);
+        forward_kernel<float, false, R, VF><<<grid, FWD_THREADS, 0, s>>>(g, (const float *)x, (float *)y, epi);
         break;
     case CBCT_F16:
-        forward_kernel<__half, true, R><<<grid, FWD_THREADS, 0, s>>>(g, (const __half *)x, (__half *)y, epi);
+        forward_kernel<__half, true, R, VF><<<grid, FWD_THREADS, 0, s>>>(g, (const __half *)x, (__half *)y, epi);
         break;
     case CBCT_BF16:
-        forward_kernel<__nv_bfloat16, true, R><<<grid, FWD_THREADS, 0, s>>>(
+        forward_kernel<__nv_bfloat16, true, R, VF><<<grid, FWD_THREADS, 0, s>>>(
             g, (const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, epi);
         break;
     }
 }
 
-cbct_status launch_forward(const DevGeom &g, const void *x, void *y, cbct_dtype t,
-                           const Epilogue &epi, cudaStream_t s) {
+template <bool VF>
+static void launch_forward_v(const DevGeom &g, const void *x, void *y, cbct_dtype t, const Epilogue &epi,
+                             cudaStream_t s) {
     switch (g.fwd_rows) {
-    case 1: launch_forward_r<1>(g, x, y, t, epi, s); break;
-    case 4: launch_forward_r<4>(g, x, y, t, epi, s); break;
-    default: launch_forward_r<2>(g, x, y, t, epi, s); break;
+    case 1: launch_forward_r<1, VF>(g, x, y, t, epi, s); break;
+    case 4: launch_forward_r<4, VF>(g, x, y, t, epi, s); break;
+    default: launch_forward_r<2, VF>(g, x, y, t, epi, s); break;
     }
+}
+
+cbct_status launch_forward(const DevGeom &g, const void *x, void *y, cbct_dtype t,
+                           const Epilogue &epi, cudaStream_t s, bool vfast) {
+    if (vfast)
+        launch_forward_v<true>(g, x, y, t, epi, s);
+    else
+        launch_forward_v<false>(g, x, y, t, epi, s);
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }
@@ -94,23 +104,23 @@ cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaSt
 
 // ---------------------------------------------------------- transpose A^T y
 
-template <typename T, bool ZFAST, int BX, int BY, int BZ, int R>
+template <typename T, bool ZFAST, int CX, int K>
 __global__ void __launch_bounds__(BWD_THREADS)
 backward_kernel(DevGeom g, const T *__restrict__ proj, T *__restrict__ vol, Epilogue epi) {
-    __shared__ float sacc[BX * BY * BZ];
     __shared__ double red[BWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    backward_tile<T, ZFAST, BX, BY, BZ, R>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z,
-                                           epi.partial ? epi.partial + b : nullptr, sacc, red);
+    backward_tile<T, ZFAST, CX, K>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z,
+                                   epi.partial ? epi.partial + b : nullptr, red);
 }
 
+// Transpose tile shapes: column patch CX x (8 / CX), 32 K voxels along z.
 BrickShape backward_shape(int config) {
     switch (config) {
-    case 1: return BrickShape{16, 16, 16, 1};
-    case 2: return BrickShape{8, 8, 64, 2};
-    case 3: return BrickShape{32, 16, 16, 1};
-    default: return BrickShape{16, 16, 32, 2};
+    case 1: return BrickShape{4, 2, 64, 2};
+    case 2: return BrickShape{8, 1, 32, 1};
+    case 3: return BrickShape{2, 4, 64, 2};
+    default: return BrickShape{4, 2, 32, 1};
     }
 }
 
@@ -130,10 +140,10 @@ static void launch_backward_t(const DevGeom &g, const void *y, void *x, const Ep
     const T *yy = (const T *)y;
     T *xx = (T *)x;
     switch (g.bwd_config) {
-    case 1: backward_kernel<T, ZF, 16, 16, 16, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
-    case 2: backward_kernel<T, ZF, 8, 8, 64, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
-    case 3: backward_kernel<T, ZF, 32, 16, 16, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
-    default: backward_kernel<T, ZF, 16, 16, 32, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    case 1: backward_kernel<T, ZF, 4, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    case 2: backward_kernel<T, ZF, 8, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    case 3: backward_kernel<T, ZF, 2, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    default: backward_kernel<T, ZF, 4, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
     }
 }
 
@@ -153,6 +163,52 @@ cbct_status launch_backward(const DevGeom &g, const void *y, void *x, cbct_dtype
         launch_backward_z<true>(g, y, x, t, epi, s);
     else
         launch_backward_z<false>(g, y, x, t, epi, s);
+    CBCT_CUDA_TRY(cudaGetLastError());
+    return CBCT_OK;
+}
+
+// -------------------------------------------------- projection re-layout
+//
+// y[a][iv][iu] <-> y[a][iu][iv]: per angle a 2D transpose through a 32 x 33
+// shared tile (coalesced on both sides).
+
+template <typename T, bool TO_VFAST>
+__global__ void __launch_bounds__(256) proj_relayout_kernel(const T *__restrict__ src, T *__restrict__ dst, int nu,
+                                                            int nv) {
+    __shared__ T tile[32][33];
+    const size_t base = (size_t)blockIdx.z * nu * nv;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    // rows/cols of the source plane: TO_VFAST: src [iv][iu]; else src [iu][iv]
+    const int rows = TO_VFAST ? nv : nu, cols = TO_VFAST ? nu : nv;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int r = ty; r < 32; r += 8) {
+        const int rr = r0 + r, cc = c0 + tx;
+        if (rr < rows && cc < cols) tile[r][tx] = src[base + (size_t)rr * cols + cc];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int cc = c0 + r, rr = r0 + tx;
+        if (cc < cols && rr < rows) dst[base + (size_t)cc * rows + rr] = tile[tx][r];
+    }
+}
+
+template <typename T>
+static void launch_proj_relayout_t(const DevGeom &g, const void *src, void *dst, bool to_vfast, cudaStream_t s) {
+    const int rows = to_vfast ? g.nv : g.nu, cols = to_vfast ? g.nu : g.nv;
+    const dim3 grid((cols + 31) / 32, (rows + 31) / 32, g.nangles);
+    if (to_vfast)
+        proj_relayout_kernel<T, true><<<grid, 256, 0, s>>>((const T *)src, (T *)dst, g.nu, g.nv);
+    else
+        proj_relayout_kernel<T, false><<<grid, 256, 0, s>>>((const T *)src, (T *)dst, g.nu, g.nv);
+}
+
+cbct_status launch_proj_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_vfast,
+                                 cudaStream_t s) {
+    switch (t) {
+    case CBCT_F32: launch_proj_relayout_t<float>(g, src, dst, to_vfast, s); break;
+    case CBCT_F16: launch_proj_relayout_t<__half>(g, src, dst, to_vfast, s); break;
+    case CBCT_BF16: launch_proj_relayout_t<__nv_bfloat16>(g, src, dst, to_vfast, s); break;
+    }
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }
@@ -236,7 +292,7 @@ extern "C" cbct_status cbct_project(const cbct_geometry *g, const void *x, void 
     st = launch_relayout(g->dev, x, tmp, t, true, s);
     if (st == CBCT_OK) {
         Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
-        st = launch_forward(g->dev, tmp, y, t, epi, s);
+        st = launch_forward(g->dev, tmp, y, t, epi, s, false);
     }
     cudaFreeAsync(tmp, s);
     return st;
@@ -246,8 +302,17 @@ extern "C" cbct_status cbct_backproject(const cbct_geometry *g, const void *y, v
                                         cbct_stream stream) {
     cbct_status st = check_pair(g, y, x, t);
     if (st != CBCT_OK) return st;
-    Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
-    return launch_backward(g->dev, y, x, t, epi, (cudaStream_t)stream, false);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the transpose reads projections v-fastest: re-lay the caller's stack first
+    void *tmp = nullptr;
+    CBCT_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)cbct_geometry_num_rays(g) * dtype_size(t), s));
+    st = launch_proj_relayout(g->dev, y, tmp, t, true, s);
+    if (st == CBCT_OK) {
+        Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
+        st = launch_backward(g->dev, tmp, x, t, epi, s, false);
+    }
+    cudaFreeAsync(tmp, s);
+    return st;
 }
 
 extern "C" cbct_status cbct_count_nnz(const cbct_geometry *g, int64_t *nnz, cbct_stream stream) {

@@ -199,12 +199,12 @@ __device__ __forceinline__ void load_rays(const DevGeom &g, int a, int iu, int i
 //
 // One tile = 8 warps = 8 adjacent detector columns (iu) x 32 R detector rows
 // (iv) of one angle.  The volume is read z-fastest: vol[(j * nx + i) * nz + k].
-// Epilogue: proj = a * (A vol) + b * old, and one FP64 sum of squares of the
-// stored values into *partial (when non-null).
+// Epilogue: proj = a * (A vol) + b * old (either projection layout), and one
+// FP64 sum of squares of the stored values into *partial (when non-null).
 
 constexpr int FWD_COLS = 8, FWD_THREADS = 32 * FWD_COLS;
 
-template <typename T, bool COMP, int R>
+template <typename T, bool COMP, int R, bool VFAST>
 __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restrict__ vol, T *__restrict__ proj,
                                              const Epilogue &epi, int tx, int ty, int a, double *partial,
                                              double *red) {
@@ -238,9 +238,9 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
     for (int r = 0; r < R; ++r) {
         const int iv = iv0 + r * 32 + lane;
         if (col_ok && iv < g.nv) {
-            const size_t pix = (size_t)iv * g.nu + iu;
-            const size_t ray = (size_t)a * g.nv * g.nu + pix;
-            double out = acoef * (double)(acc[r] * g.ray_len[pix]);
+            // output y[a][iu][iv] (v fastest: one warp writes consecutive rows) or y[a][iv][iu]
+            const size_t ray = VFAST ? ((size_t)a * g.nu + iu) * g.nv + iv : ((size_t)a * g.nv + iv) * g.nu + iu;
+            double out = acoef * (double)(acc[r] * g.ray_len[(size_t)iu * g.nv + iv]);
             if (bcoef != 0.0) {
                 const T *oldp = epi.old ? (const T *)epi.old : (const T *)proj;
                 out += bcoef * (double)Storage<T>::ld_plain(oldp + ray);
@@ -258,101 +258,105 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
 
 // ---------------------------------------------------------- transpose A^T y
 //
-// One tile owns a brick of BX x BY x BZ voxels, accumulated in shared memory
-// (z fastest).  For every angle each warp finds the detector window onto which
-// the brick projects (its corners), cuts it into tasks of one detector column
-// x 32 R rows, and walks those rays through the brick with the forward
-// traversal, adding len * |d'| * y to the voxels they meet.  Warps move from
-// angle to angle independently.  After the last angle the brick is written
-// once (fused epilogue, either volume layout), so no global atomics are needed.
+// Gather form: each lane owns voxels (i, j, k) of one voxel column and sums
+// len * |d'| * y over every ray that meets them, in registers, angle by angle;
+// the volume is written once (fused epilogue), so there are no atomics and the
+// result does not depend on scheduling.  A warp owns one column (i, j) and
+// 32 K consecutive k (k = k0 + kk * 32 + lane); a tile is 8 warps on a
+// CX x (8 / CX) patch of columns.  For every angle the warp finds the detector
+// columns whose xy projection crosses cell (i, j) (the cell's four corners),
+// and for each of them the alpha interval [ain, aout] of that crossing (x and
+// y plane crossings, warp-uniform).  A lane then inverts z(alpha) =
+// v (dso/dsd + alpha) over [ain, aout] to get the detector rows that can meet
+// its voxel's z slab, and takes for each the segment
+//     [max(ain, z entry), min(aout, z exit)]
+// from the same plane_alpha values as the forward traversal, so every length
+// is bit-identical to the forward projector's: A^T is the exact transpose.
+// Projections are read v-fastest: y[a][iu][iv].
 
 constexpr int BWD_THREADS = 256;
 
-template <typename T, bool ZFAST, int BX, int BY, int BZ, int R>
+template <typename T, bool ZFAST, int CX, int K>
 __device__ __forceinline__ void backward_tile(const DevGeom &g, const T *__restrict__ proj, T *__restrict__ vol,
-                                              const Epilogue &epi, int tbx, int tby, int tbz, double *partial,
-                                              float *sacc, double *red) {
+                                              const Epilogue &epi, int tx, int ty, int tz, double *partial,
+                                              double *red) {
+    constexpr int CY = 8 / CX;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int bx = tbx * BX, by = tby * BY, bz = tbz * BZ;
-    const int ex = min(BX, g.nx - bx), ey = min(BY, g.ny - by), ez = min(BZ, g.nz - bz);
-    for (int q = threadIdx.x; q < BX * BY * BZ; q += BWD_THREADS) sacc[q] = 0.0f;
-    __syncthreads();
-
-    // brick corners (mm) for the footprint windows
-    const float x0 = g.bx0 + bx * g.dx, x1 = g.bx0 + (bx + ex) * g.dx;
-    const float y0 = g.by0 + by * g.dy, y1 = g.by0 + (by + ey) * g.dy;
-    const float z0 = g.bz0 + bz * g.dz, z1 = g.bz0 + (bz + ez) * g.dz;
-    const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
-    constexpr int ROWS = 32 * R;
-
-    for (int a = 0; a < g.nangles; ++a) {
-        const float2 cs = g.trig[a];
-        float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX;
+    const int i = tx * CX + (warp % CX), j = ty * CY + (warp / CX);
+    const int k0 = tz * 32 * K;
+    const bool col_ok = i < g.nx && j < g.ny;          // uniform across the warp
+    float acc[K];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float px = (c & 1) ? x1 : x0, py = (c & 2) ? y1 : y0;
-            const float along = g.dso - (px * cs.x + py * cs.y);   // > 0: source outside
-            const float across = -px * cs.y + py * cs.x;
-            const float mag = g.dsd / along;
-            umin = fminf(umin, across * mag);
-            umax = fmaxf(umax, across * mag);
-            vmin = fminf(vmin, fminf(z0 * mag, z1 * mag));
-            vmax = fmaxf(vmax, fmaxf(z0 * mag, z1 * mag));
-        }
-        const int iu0 = max(0, (int)ceilf(umin / g.du + cu - 0.01f));
-        const int iu1 = min(g.nu - 1, (int)floorf(umax / g.du + cu + 0.01f));
-        const int iv0 = max(0, (int)ceilf(vmin / g.dv + cv - 0.01f));
-        const int iv1 = min(g.nv - 1, (int)floorf(vmax / g.dv + cv + 0.01f));
-        if (iu0 > iu1 || iv0 > iv1) continue;
-        const int nblk = (iv1 - iv0 + ROWS) / ROWS;
-        const int ntask = (iu1 - iu0 + 1) * nblk;
-        const T *pa = proj + (size_t)a * g.nv * g.nu;
-        for (int task = warp; task < ntask; task += BWD_THREADS / 32) {
-            const int iu = iu0 + task / nblk;
-            const int ivb = iv0 + (task % nblk) * ROWS;
-            float w[R];
-            bool any = false;
+    for (int kk = 0; kk < K; ++kk) acc[kk] = 0.0f;
+    if (col_ok) {
+        const float x0 = g.bx0 + i * g.dx, x1 = x0 + g.dx;
+        const float y0 = g.by0 + j * g.dy, y1 = y0 + g.dy;
+        const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
+        const float m = g.dso / g.dsd;
+        float zlo_mm[K];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int iv = ivb + r * 32 + lane;
-                w[r] = 0.0f;
-                if (iv <= iv1) {                // rows outside the window never enter the brick
-                    const size_t pix = (size_t)iv * g.nu + iu;
-                    w[r] = Storage<T>::load(pa + pix) * g.ray_len[pix];
-                }
-                any |= w[r] != 0.0f;
+        for (int kk = 0; kk < K; ++kk) zlo_mm[kk] = g.bz0 + (k0 + kk * 32 + lane) * g.dz;
+        const size_t nuv = (size_t)g.nu * g.nv;
+        for (int a = 0; a < g.nangles; ++a) {
+            const float2 cs = g.trig[a];
+            float umin = FLT_MAX, umax = -FLT_MAX;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float px = (c & 1) ? x1 : x0, py = (c & 2) ? y1 : y0;
+                const float along = g.dso - (px * cs.x + py * cs.y);   // > 0: source outside
+                const float u = (-px * cs.y + py * cs.x) * (g.dsd / along);
+                umin = fminf(umin, u);
+                umax = fmaxf(umax, u);
             }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            RayAxis rx, ry, rz[R];
-            load_rays<R>(g, a, iu, ivb, iv1 + 1, rx, ry, rz);
-            auto seg = [&](int r, int idx, float len) {
-                if (w[r] != 0.0f && len > 0.0f) atomicAdd(&sacc[idx], len * w[r]);
-            };
-            // brick in shared memory, z fastest: ((j - by) * BX + (i - bx)) * BZ + (k - bz)
-            trace_columns<R>(g, rx, ry, rz, bx, bx + ex, by, by + ey, bz, bz + ez, -(by * BX + bx) * BZ - bz,
-                             BZ, BX * BZ, seg);
+            const int iu0 = max(0, (int)ceilf(umin / g.du + cu - 0.05f));
+            const int iu1 = min(g.nu - 1, (int)floorf(umax / g.du + cu + 0.05f));
+            const T *pa = proj + (size_t)a * nuv;
+            for (int iu = iu0; iu <= iu1; ++iu) {
+                const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
+                const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
+                float ain = -FLT_MAX, aout = FLT_MAX;
+                bool miss = false;
+                clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
+                clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
+                if (miss || !(ain < aout)) continue;
+                // rows whose ray can be inside z slab [z, z + dz] for some alpha in [ain, aout]
+                const float rlo = 1.0f / (m + ain), rhi = 1.0f / (m + aout);
+                const T *pcol = pa + (size_t)iu * g.nv;
+                const float *lcol = g.ray_len + (size_t)iu * g.nv;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const int k = k0 + kk * 32 + lane;
+                    if (k >= g.nz) continue;
+                    const float za = zlo_mm[kk], zb = za + g.dz;
+                    const float vmin = fminf(za * rlo, za * rhi), vmax = fmaxf(zb * rlo, zb * rhi);
+                    const int r0 = max(0, (int)ceilf(vmin / g.dv + cv - 0.05f));
+                    const int r1 = min(g.nv - 1, (int)floorf(vmax / g.dv + cv + 0.05f));
+                    for (int iv = r0; iv <= r1; ++iv) {
+                        const float4 z = g.ray_z[iv];
+                        float lo = ain, hi = aout;
+                        if (z.y == 0.0f) {              // ray in a z plane: half-open voxel index z.z
+                            if ((int)z.z != k) continue;
+                        } else {
+                            const RayAxis rz{z.x, z.y, z.z};
+                            const float e0 = plane_alpha((float)k - z.z, g.dz, rz);
+                            const float e1 = plane_alpha((float)(k + 1) - z.z, g.dz, rz);
+                            lo = fmaxf(lo, fminf(e0, e1));
+                            hi = fminf(hi, fmaxf(e0, e1));
+                        }
+                        if (hi > lo) acc[kk] += (hi - lo) * (lcol[iv] * Storage<T>::load(pcol + iv));
+                    }
+                }
+            }
         }
     }
-    __syncthreads();
-
     const double acoef = epi_a(epi), bcoef = epi_b(epi);
     double sq = 0.0;
-    for (int q = threadIdx.x; q < BX * BY * BZ; q += BWD_THREADS) {
-        int i, j, k;
-        if (ZFAST) {            // output x[j][i][k]: walk k fastest
-            k = q % BZ;
-            i = (q / BZ) % BX;
-            j = q / (BZ * BX);
-        } else {                // output x[k][j][i]: walk i fastest
-            i = q % BX;
-            j = (q / BX) % BY;
-            k = q / (BX * BY);
-        }
-        if (i >= ex || j >= ey || k >= ez) continue;
-        const int sidx = (j * BX + i) * BZ + k;
-        const size_t v = ZFAST ? ((size_t)(by + j) * g.nx + (bx + i)) * g.nz + (bz + k)
-                               : ((size_t)(bz + k) * g.ny + (by + j)) * g.nx + (bx + i);
-        double out = acoef * (double)sacc[sidx];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+        const int k = k0 + kk * 32 + lane;
+        if (!col_ok || k >= g.nz) continue;
+        const size_t v = ZFAST ? ((size_t)j * g.nx + i) * g.nz + k : ((size_t)k * g.ny + j) * g.nx + i;
+        double out = acoef * (double)acc[kk];
         if (bcoef != 0.0) {
             const T *oldp = epi.old ? (const T *)epi.old : (const T *)vol;
             out += bcoef * (double)Storage<T>::ld_plain(oldp + v);
@@ -364,8 +368,6 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const T *__restr
     if (partial) {
         const double s = block_sum<BWD_THREADS>(sq, red);
         if (threadIdx.x == 0) *partial = s;
-    } else {
-        __syncthreads();        // sacc may be reused by the caller's next tile
     }
 }
 

@@ -37,7 +37,7 @@ namespace cbct {
 
 constexpr int SRV_MAX_SLOTS = 64;
 constexpr int SRV_FWD_ROWS = 2;                       // forward tile: 2 rays per lane
-constexpr int SRV_BX = 16, SRV_BY = 16, SRV_BZ = 32, SRV_BR = 2;   // transpose brick (configuration 0)
+constexpr int SRV_CX = 4, SRV_BK = 1;                  // transpose tile: 4 x 2 columns, 1 voxel per lane (configuration 0)
 
 struct SlotDev {
     DevGeom g;
@@ -84,13 +84,12 @@ __global__ void __launch_bounds__(FWD_THREADS) srv_forward(const SlotTable *tab)
         const int local = item - tab->fwd_start[s];
         const int tx = local % sd.fgx, ty = (local / sd.fgx) % sd.fgy, a = local / (sd.fgx * sd.fgy);
         const Epilogue epi{&sd.st->fa, &sd.st->fb, 0.0, 0.0, nullptr, nullptr, nullptr};
-        forward_tile<float, false, SRV_FWD_ROWS>(sd.g, sd.V, sd.U, epi, tx, ty, a, sd.pf + local, red);
+        forward_tile<float, false, SRV_FWD_ROWS, true>(sd.g, sd.V, sd.U, epi, tx, ty, a, sd.pf + local, red);
     }
 }
 
-// V <- ba * A^T U + bb * V for every slot (bricks of all slots, z-fastest volumes).
+// V <- ba * A^T U + bb * V for every slot (transpose tiles of all slots, z-fastest volumes).
 __global__ void __launch_bounds__(BWD_THREADS) srv_backward(const SlotTable *tab) {
-    __shared__ float sacc[SRV_BX * SRV_BY * SRV_BZ];
     __shared__ double red[BWD_THREADS / 32];
     const int n = tab->n;
     const int total = tab->bwd_start[n];
@@ -101,8 +100,7 @@ __global__ void __launch_bounds__(BWD_THREADS) srv_backward(const SlotTable *tab
         const int local = item - tab->bwd_start[s];
         const int tbx = local % sd.bgx, tby = (local / sd.bgx) % sd.bgy, tbz = local / (sd.bgx * sd.bgy);
         const Epilogue epi{&sd.st->ba, &sd.st->bb, 0.0, 0.0, nullptr, nullptr, nullptr};
-        backward_tile<float, true, SRV_BX, SRV_BY, SRV_BZ, SRV_BR>(sd.g, sd.U, sd.V, epi, tbx, tby, tbz,
-                                                                    sd.pb + local, sacc, red);
+        backward_tile<float, true, SRV_CX, SRV_BK>(sd.g, sd.U, sd.V, epi, tbx, tby, tbz, sd.pb + local, red);
     }
 }
 
@@ -192,9 +190,9 @@ struct Slot {
 void grids(const cbct_geometry_desc &d, int &fgx, int &fgy, int &bgx, int &bgy, int &bgz) {
     fgx = (d.nu + FWD_COLS - 1) / FWD_COLS;
     fgy = (d.nv + 32 * SRV_FWD_ROWS - 1) / (32 * SRV_FWD_ROWS);
-    bgx = (d.nx + SRV_BX - 1) / SRV_BX;
-    bgy = (d.ny + SRV_BY - 1) / SRV_BY;
-    bgz = (d.nz + SRV_BZ - 1) / SRV_BZ;
+    bgx = (d.nx + SRV_CX - 1) / SRV_CX;
+    bgy = (d.ny + (8 / SRV_CX) - 1) / (8 / SRV_CX);
+    bgz = (d.nz + 32 * SRV_BK - 1) / (32 * SRV_BK);
 }
 
 // Device memory a request holds at its peak (ray tables, Krylov vectors,
@@ -283,7 +281,10 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     // beta_1 u_1 = b, alpha_1 v_1 = A^T u_1: the same start as the single-request solver
     k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.b, n, sl.pf);
     gk_begin<<<1, RED_THREADS, 0, s>>>(sl.st, sl.pf, VEC_BLOCKS);
-    k_scale_to<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.b, sl.U, n, &sl.st->c0, &sl.st->stop);
+    // U = su * b, v-fastest
+    st = launch_proj_relayout(g, sl.b, sl.U, CBCT_F32, true, s);
+    if (st != CBCT_OK) return st;
+    k_scale_inplace<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.U, n, &sl.st->c0, &sl.st->stop);
     Epilogue eb{&sl.st->ba, &sl.st->bb, 0.0, 0.0, sl.pb, &sl.st->stop, nullptr};
     st = launch_backward(g, sl.U, sl.V, CBCT_F32, eb, s, true);
     if (st != CBCT_OK) return st;

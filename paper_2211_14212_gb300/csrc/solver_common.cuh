@@ -67,6 +67,15 @@ k_scale_to(const float *__restrict__ src, T *__restrict__ dst, int64_t n, const 
         Storage<T>::store(dst + i, c * src[i]);
 }
 
+// v = coef * v in place.
+static __global__ void __launch_bounds__(VEC_THREADS)
+k_scale_inplace(float *v, int64_t n, const double *coef, const int *stop) {
+    if (stop && *stop) return;
+    const float c = (float)*coef;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS)
+        v[i] *= c;
+}
+
 // Combine a basis: x[m] = sum_j coef[j] * basis_j[m], basis_j = basis + j * n.
 template <typename T>
 __global__ void __launch_bounds__(VEC_THREADS)

@@ -163,7 +163,7 @@ k_cg_p(float *__restrict__ p, const float *__restrict__ s, int64_t n, double *pa
 // ====================================================================== drivers
 
 struct SolveIO {
-    const float *b_dev;
+    const float *b_dev;   // b re-laid v-fastest, y[a][iu][iv], like the projection-side vectors
     float *x_dev;         // caller layout x[k][j][i] (device; staging buffer for host x)
     float *xz;            // the iterate in the solvers' z-fastest layout x[j][i][k]
     bool x_is_host;
@@ -184,16 +184,21 @@ static cbct_status check_solve_args(const cbct_geometry *g, const float *b, floa
 // Stage host b / x through device memory when needed.
 static cbct_status setup_io(const cbct_geometry *g, const float *b, float *x, Workspace &ws, SolveIO &io) {
     const int64_t n = cbct_geometry_num_rays(g), m = cbct_geometry_num_voxels(g);
-    io.b_dev = b;
     io.x_dev = x;
     io.x_is_host = false;
     io.x_host = nullptr;
+    const float *bsrc = b;
     if (!is_device_pointer(b)) {
         float *bd = nullptr;
         CBCT_CUDA_TRY(ws.alloc(&bd, (size_t)n));
         CBCT_CUDA_TRY(cudaMemcpyAsync(bd, b, sizeof(float) * n, cudaMemcpyHostToDevice, ws.s));
-        io.b_dev = bd;
+        bsrc = bd;
     }
+    float *bv = nullptr;
+    CBCT_CUDA_TRY(ws.alloc(&bv, (size_t)n));
+    cbct_status st = launch_proj_relayout(g->dev, bsrc, bv, CBCT_F32, true, ws.s);
+    if (st != CBCT_OK) return st;
+    io.b_dev = bv;
     if (!is_device_pointer(x)) {
         float *xd = nullptr;
         CBCT_CUDA_TRY(ws.alloc(&xd, (size_t)m));
@@ -278,7 +283,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
 
     auto fwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(0);
-        if (r == CBCT_OK) r = launch_forward(g, in, out, t, e, s);
+        if (r == CBCT_OK) r = launch_forward(g, in, out, t, e, s, true);
         if (r == CBCT_OK) r = tr.mark(0);
         ++tr.launches;
         ++tr.fwd;
@@ -414,7 +419,7 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     tr.s = s;
     auto fwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(0);
-        if (r == CBCT_OK) r = launch_forward(g, in, out, CBCT_F32, e, s);
+        if (r == CBCT_OK) r = launch_forward(g, in, out, CBCT_F32, e, s, true);
         if (r == CBCT_OK) r = tr.mark(0);
         ++tr.launches;
         ++tr.fwd;
