@@ -119,6 +119,17 @@ cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, i
  * receives the forward times for fwd_rows 1, 2, 4 and the transpose times for
  * bwd_config 0..3.  Allocates scratch on `stream` and synchronises it. */
 cbct_status cbct_geometry_autotune(cbct_geometry *geom, int max_angles, double *times_ms, cbct_stream stream);
+/* Angles per pass of the transpose inside the solvers and cbct_backproject
+ * (performance only).  With a
+ * projection stack larger than L2 the transpose runs in passes over blocks of
+ * `angles` consecutive angles, keeping FP32 running sums in M values of
+ * scratch, so that each pass gathers from projections that stay in L2.
+ * angles >= nangles means one pass; angles == 0 restores the default (one
+ * pass); negative values are rejected (CBCT_EINVAL).  Every block size gives
+ * bit-identical sums (the running sums are kept in FP32 between passes, in
+ * the same order).  Not thread-safe, like set_launch. */
+cbct_status cbct_geometry_set_angle_block(cbct_geometry *geom, int angles);
+cbct_status cbct_geometry_get_angle_block(const cbct_geometry *geom, int *angles);
 
 /* ------------------------------------------------------------------ solvers
  * All solvers start from x_0 = 0 and run opts->iters iterations (fewer on

@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
     lib.cbct_geometry_set_launch.argtypes = [G, ctypes.c_int, ctypes.c_int]
     lib.cbct_geometry_get_launch.argtypes = [G, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.cbct_geometry_autotune.argtypes = [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+    lib.cbct_geometry_set_angle_block.argtypes = [G, ctypes.c_int]
+    lib.cbct_geometry_get_angle_block.argtypes = [G, ctypes.POINTER(ctypes.c_int)]
     for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Report), vp]
     lib.cbct_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(ctypes.c_void_p)]
@@ -257,6 +259,17 @@ def get_launch(geom: Geometry):
     f, b = ctypes.c_int(), ctypes.c_int()
     _check("cbct_geometry_get_launch", load().cbct_geometry_get_launch(geom.handle, ctypes.byref(f), ctypes.byref(b)))
     return int(f.value), int(b.value)
+
+
+def set_angle_block(geom: Geometry, angles: int):
+    """Angles per pass of the transpose (cbct_geometry_set_angle_block; 0 = default)."""
+    _check("cbct_geometry_set_angle_block", load().cbct_geometry_set_angle_block(geom.handle, int(angles)))
+
+
+def get_angle_block(geom: Geometry) -> int:
+    a = ctypes.c_int()
+    _check("cbct_geometry_get_angle_block", load().cbct_geometry_get_angle_block(geom.handle, ctypes.byref(a)))
+    return int(a.value)
 
 
 def autotune(geom: Geometry, max_angles: int = 32, stream=None) -> dict:

@@ -2,6 +2,7 @@
 // the transpose tile's shape are chosen by timing every candidate on a
 // strided subset of the scan's angles (the work per angle is what the shape
 // changes; the angle count only scales it).
+#include <algorithm>
 #include <cfloat>
 #include <vector>
 
@@ -62,6 +63,19 @@ extern "C" cbct_status cbct_geometry_get_launch(const cbct_geometry *g, int *fwd
     return CBCT_OK;
 }
 
+extern "C" cbct_status cbct_geometry_set_angle_block(cbct_geometry *g, int angles) {
+    if (!g) { set_error("cbct_geometry_set_angle_block: null geometry"); return CBCT_EINVAL; }
+    if (angles < 0) { set_error("cbct_geometry_set_angle_block: angles must be >= 0"); return CBCT_EINVAL; }
+    g->dev.angle_block = angles == 0 ? default_angle_block(g->dev) : std::min(angles, g->dev.nangles);
+    return CBCT_OK;
+}
+
+extern "C" cbct_status cbct_geometry_get_angle_block(const cbct_geometry *g, int *angles) {
+    if (!g || !angles) { set_error("cbct_geometry_get_angle_block: null argument"); return CBCT_EINVAL; }
+    *angles = g->dev.angle_block;
+    return CBCT_OK;
+}
+
 extern "C" cbct_status cbct_geometry_autotune(cbct_geometry *g, int max_angles, double *times_ms,
                                               cbct_stream stream) {
     if (!g) { set_error("cbct_geometry_autotune: null geometry"); return CBCT_EINVAL; }
@@ -97,7 +111,7 @@ extern "C" cbct_status cbct_geometry_autotune(cbct_geometry *g, int max_angles, 
         }
         for (int c = 0; c < NUM_BWD_CONFIGS && st == CBCT_OK; ++c) {
             t->dev.bwd_config = c;
-            st = time_best([&] { return launch_backward(t->dev, y, x, CBCT_F32, epi, s, true); }, 2, s, e0, e1,
+            st = time_best([&] { return launch_backward(t->dev, y, x, CBCT_F32, epi, s, true, nullptr); }, 2, s, e0, e1,
                            &tb[c]);
         }
     }

@@ -46,7 +46,8 @@ struct DevGeom {
     const float *ray_len;    // [nu][nv]
     const float2 *trig;      // [nangles] (cos t, sin t), for footprint windows only
     int fwd_rows;            // forward tile: rays per lane (1, 2 or 4)
-    int bwd_config;          // transpose tile: brick shape / rays per lane (backward_shape)
+    int bwd_config;          // transpose tile: column patch / voxels per lane (backward_shape)
+    int angle_block;         // transpose: angles per pass when summed in passes (launch_backward)
 };
 
 // Tile of the transpose: a bx x by patch of voxel columns (one warp each),
@@ -145,8 +146,12 @@ cbct_status launch_forward(const DevGeom &g, const void *x_zfast, void *y, cbct_
 // v-fastest, y[a][iu][iv]; the solvers keep their vectors in those layouts.
 // launch_forward writes either projection layout, launch_backward either
 // volume layout.
+// `accum` (optional, M FP32 values of scratch) lets the transpose run in passes
+// over blocks of DevGeom::angle_block angles; null means one pass.
 cbct_status launch_backward(const DevGeom &g, const void *y_vfast, void *x, cbct_dtype t,
-                            const Epilogue &epi, cudaStream_t s, bool zfast);
+                            const Epilogue &epi, cudaStream_t s, bool zfast, float *accum);
+int backward_passes(const DevGeom &g, const float *accum);
+int default_angle_block(const DevGeom &g);
 cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_zfast,
                             cudaStream_t s);
 cbct_status launch_proj_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_vfast,

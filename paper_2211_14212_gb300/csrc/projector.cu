@@ -106,12 +106,13 @@ cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaSt
 
 template <typename T, bool ZFAST, int CX, int K>
 __global__ void __launch_bounds__(BWD_THREADS)
-backward_kernel(DevGeom g, const T *__restrict__ proj, T *__restrict__ vol, Epilogue epi) {
+backward_kernel(DevGeom g, const T *__restrict__ proj, T *__restrict__ vol, Epilogue epi, int a_begin, int a_end,
+                const float *acc_in, float *acc_out) {
     __shared__ double red[BWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    backward_tile<T, ZFAST, CX, K>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z,
-                                   epi.partial ? epi.partial + b : nullptr, red);
+    backward_tile<T, ZFAST, CX, K>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z, a_begin, a_end, acc_in,
+                                   acc_out, epi.partial ? epi.partial + b : nullptr, red);
 }
 
 // Transpose tile shapes: column patch CX x (8 / CX), 32 K voxels along z.
@@ -135,34 +136,50 @@ int backward_num_blocks(const DevGeom &g) {
 }
 
 template <typename T, bool ZF>
-static void launch_backward_t(const DevGeom &g, const void *y, void *x, const Epilogue &epi, cudaStream_t s) {
+static void launch_backward_t(const DevGeom &g, const void *y, void *x, const Epilogue &epi, cudaStream_t s,
+                              int a0, int a1, const float *acc_in, float *acc_out) {
     const dim3 grid = backward_grid(g);
     const T *yy = (const T *)y;
     T *xx = (T *)x;
     switch (g.bwd_config) {
-    case 1: backward_kernel<T, ZF, 4, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
-    case 2: backward_kernel<T, ZF, 8, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
-    case 3: backward_kernel<T, ZF, 2, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
-    default: backward_kernel<T, ZF, 4, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi); break;
+    case 1: backward_kernel<T, ZF, 4, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 2: backward_kernel<T, ZF, 8, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 3: backward_kernel<T, ZF, 2, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    default: backward_kernel<T, ZF, 4, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     }
 }
 
 template <bool ZF>
 static void launch_backward_z(const DevGeom &g, const void *y, void *x, cbct_dtype t, const Epilogue &epi,
-                              cudaStream_t s) {
+                              cudaStream_t s, int a0, int a1, const float *acc_in, float *acc_out) {
     switch (t) {
-    case CBCT_F32: launch_backward_t<float, ZF>(g, y, x, epi, s); break;
-    case CBCT_F16: launch_backward_t<__half, ZF>(g, y, x, epi, s); break;
-    case CBCT_BF16: launch_backward_t<__nv_bfloat16, ZF>(g, y, x, epi, s); break;
+    case CBCT_F32: launch_backward_t<float, ZF>(g, y, x, epi, s, a0, a1, acc_in, acc_out); break;
+    case CBCT_F16: launch_backward_t<__half, ZF>(g, y, x, epi, s, a0, a1, acc_in, acc_out); break;
+    case CBCT_BF16: launch_backward_t<__nv_bfloat16, ZF>(g, y, x, epi, s, a0, a1, acc_in, acc_out); break;
     }
 }
 
+int backward_passes(const DevGeom &g, const float *accum) {
+    if (!accum || g.angle_block <= 0 || g.angle_block >= g.nangles) return 1;
+    return (g.nangles + g.angle_block - 1) / g.angle_block;
+}
+
+// One launch per block of angles (DevGeom::angle_block) when `accum` (M FP32
+// values) is given: each pass reads only its angles' projections, which then
+// stay in L2 while every voxel tile of the pass gathers from them.
 cbct_status launch_backward(const DevGeom &g, const void *y, void *x, cbct_dtype t, const Epilogue &epi,
-                            cudaStream_t s, bool zfast) {
-    if (zfast)
-        launch_backward_z<true>(g, y, x, t, epi, s);
-    else
-        launch_backward_z<false>(g, y, x, t, epi, s);
+                            cudaStream_t s, bool zfast, float *accum) {
+    const int passes = backward_passes(g, accum);
+    for (int p = 0; p < passes; ++p) {
+        const int a0 = passes == 1 ? 0 : p * g.angle_block;
+        const int a1 = passes == 1 ? g.nangles : min(g.nangles, a0 + g.angle_block);
+        const float *acc_in = p > 0 ? accum : nullptr;
+        float *acc_out = p + 1 < passes ? accum : nullptr;
+        if (zfast)
+            launch_backward_z<true>(g, y, x, t, epi, s, a0, a1, acc_in, acc_out);
+        else
+            launch_backward_z<false>(g, y, x, t, epi, s, a0, a1, acc_in, acc_out);
+    }
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }
@@ -305,13 +322,22 @@ extern "C" cbct_status cbct_backproject(const cbct_geometry *g, const void *y, v
     cudaStream_t s = (cudaStream_t)stream;
     // the transpose reads projections v-fastest: re-lay the caller's stack first
     void *tmp = nullptr;
+    float *accum = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)cbct_geometry_num_rays(g) * dtype_size(t), s));
+    cudaError_t err = cudaSuccess;
+    if (g->dev.angle_block < g->dev.nangles)     // summed in passes over blocks of angles
+        err = cudaMallocAsync(&accum, (size_t)cbct_geometry_num_voxels(g) * sizeof(float), s);
+    if (err != cudaSuccess) {
+        cudaFreeAsync(tmp, s);
+        return cuda_fail(err, "cbct_backproject");
+    }
     st = launch_proj_relayout(g->dev, y, tmp, t, true, s);
     if (st == CBCT_OK) {
         Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
-        st = launch_backward(g->dev, tmp, x, t, epi, s, false);
+        st = launch_backward(g->dev, tmp, x, t, epi, s, false, accum);
     }
     cudaFreeAsync(tmp, s);
+    if (accum) cudaFreeAsync(accum, s);
     return st;
 }
 

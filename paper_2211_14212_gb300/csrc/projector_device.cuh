@@ -276,9 +276,17 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
 
 constexpr int BWD_THREADS = 256;
 
+// Angles [a_begin, a_end) are summed in one call.  A scan whose projections
+// do not fit in L2 is summed in passes over blocks of angles (launch_backward):
+// `acc_in` (if not null) holds the FP32 sums of the earlier passes and
+// `acc_out` (if not null) receives the running sums instead of the volume, so
+// only the last pass applies the epilogue.  Both are z-fastest, indexed like
+// the internal volume; they may be the same buffer (each lane reads and writes
+// only its own voxels).
 template <typename T, bool ZFAST, int CX, int K>
 __device__ __forceinline__ void backward_tile(const DevGeom &g, const T *__restrict__ proj, T *__restrict__ vol,
-                                              const Epilogue &epi, int tx, int ty, int tz, double *partial,
+                                              const Epilogue &epi, int tx, int ty, int tz, int a_begin, int a_end,
+                                              const float *acc_in, float *acc_out, double *partial,
                                               double *red) {
     constexpr int CY = 8 / CX;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -287,29 +295,41 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const T *__restr
     const bool col_ok = i < g.nx && j < g.ny;          // uniform across the warp
     float acc[K];
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) acc[kk] = 0.0f;
+    for (int kk = 0; kk < K; ++kk) {
+        const int k = k0 + kk * 32 + lane;
+        acc[kk] = acc_in && col_ok && k < g.nz ? acc_in[((size_t)j * g.nx + i) * g.nz + k] : 0.0f;
+    }
     if (col_ok) {
         const float x0 = g.bx0 + i * g.dx, x1 = x0 + g.dx;
         const float y0 = g.by0 + j * g.dy, y1 = y0 + g.dy;
         const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
         const float m = g.dso / g.dsd;
-        float zlo_mm[K];
+        // The detector windows below only select candidates (every length is
+        // then computed exactly from plane_alpha), so they use fast
+        // approximate divisions: their relative error (~1e-6) stays far below
+        // the 0.05-pixel margins.
+        const float inv_du = 1.0f / g.du, inv_dv = 1.0f / g.dv;
+        float zr_lo[K], zr_hi[K];        // voxel slab bottom / top over dv
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) zlo_mm[kk] = g.bz0 + (k0 + kk * 32 + lane) * g.dz;
+        for (int kk = 0; kk < K; ++kk) {
+            const float za = g.bz0 + (k0 + kk * 32 + lane) * g.dz;
+            zr_lo[kk] = za * inv_dv;
+            zr_hi[kk] = (za + g.dz) * inv_dv;
+        }
         const size_t nuv = (size_t)g.nu * g.nv;
-        for (int a = 0; a < g.nangles; ++a) {
+        for (int a = a_begin; a < a_end; ++a) {
             const float2 cs = g.trig[a];
             float umin = FLT_MAX, umax = -FLT_MAX;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float px = (c & 1) ? x1 : x0, py = (c & 2) ? y1 : y0;
                 const float along = g.dso - (px * cs.x + py * cs.y);   // > 0: source outside
-                const float u = (-px * cs.y + py * cs.x) * (g.dsd / along);
+                const float u = (-px * cs.y + py * cs.x) * __fdividef(g.dsd, along);
                 umin = fminf(umin, u);
                 umax = fmaxf(umax, u);
             }
-            const int iu0 = max(0, (int)ceilf(umin / g.du + cu - 0.05f));
-            const int iu1 = min(g.nu - 1, (int)floorf(umax / g.du + cu + 0.05f));
+            const int iu0 = max(0, (int)ceilf(__fmaf_rn(umin, inv_du, cu - 0.05f)));
+            const int iu1 = min(g.nu - 1, (int)floorf(__fmaf_rn(umax, inv_du, cu + 0.05f)));
             const T *pa = proj + (size_t)a * nuv;
             for (int iu = iu0; iu <= iu1; ++iu) {
                 const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
@@ -320,34 +340,44 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const T *__restr
                 clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
                 if (miss || !(ain < aout)) continue;
                 // rows whose ray can be inside z slab [z, z + dz] for some alpha in [ain, aout]
-                const float rlo = 1.0f / (m + ain), rhi = 1.0f / (m + aout);
+                const float rlo = __fdividef(1.0f, m + ain), rhi = __fdividef(1.0f, m + aout);
                 const T *pcol = pa + (size_t)iu * g.nv;
                 const float *lcol = g.ray_len + (size_t)iu * g.nv;
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) {
                     const int k = k0 + kk * 32 + lane;
                     if (k >= g.nz) continue;
-                    const float za = zlo_mm[kk], zb = za + g.dz;
-                    const float vmin = fminf(za * rlo, za * rhi), vmax = fmaxf(zb * rlo, zb * rhi);
-                    const int r0 = max(0, (int)ceilf(vmin / g.dv + cv - 0.05f));
-                    const int r1 = min(g.nv - 1, (int)floorf(vmax / g.dv + cv + 0.05f));
+                    const float vmin = fminf(zr_lo[kk] * rlo, zr_lo[kk] * rhi);
+                    const float vmax = fmaxf(zr_hi[kk] * rlo, zr_hi[kk] * rhi);
+                    const int r0 = max(0, (int)ceilf(vmin + (cv - 0.05f)));
+                    const int r1 = min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f)));
+                    const float kf = (float)k;
                     for (int iv = r0; iv <= r1; ++iv) {
                         const float4 z = g.ray_z[iv];
                         float lo = ain, hi = aout;
                         if (z.y == 0.0f) {              // ray in a z plane: half-open voxel index z.z
-                            if ((int)z.z != k) continue;
+                            if (z.z != kf) hi = lo;
                         } else {
                             const RayAxis rz{z.x, z.y, z.z};
-                            const float e0 = plane_alpha((float)k - z.z, g.dz, rz);
-                            const float e1 = plane_alpha((float)(k + 1) - z.z, g.dz, rz);
+                            const float e0 = plane_alpha(kf - z.z, g.dz, rz);
+                            const float e1 = plane_alpha((kf + 1.0f) - z.z, g.dz, rz);
                             lo = fmaxf(lo, fminf(e0, e1));
                             hi = fminf(hi, fmaxf(e0, e1));
                         }
-                        if (hi > lo) acc[kk] += (hi - lo) * (lcol[iv] * Storage<T>::load(pcol + iv));
+                        // a miss adds exactly zero: the same sum as skipping it
+                        acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), lcol[iv] * Storage<T>::load(pcol + iv), acc[kk]);
                     }
                 }
             }
         }
+    }
+    if (acc_out) {                      // an earlier pass: keep the running sums
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int k = k0 + kk * 32 + lane;
+            if (col_ok && k < g.nz) acc_out[((size_t)j * g.nx + i) * g.nz + k] = acc[kk];
+        }
+        return;
     }
     const double acoef = epi_a(epi), bcoef = epi_b(epi);
     double sq = 0.0;

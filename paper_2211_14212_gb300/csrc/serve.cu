@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(BWD_THREADS) srv_backward(const SlotTable *tab
         const int local = item - tab->bwd_start[s];
         const int tbx = local % sd.bgx, tby = (local / sd.bgx) % sd.bgy, tbz = local / (sd.bgx * sd.bgy);
         const Epilogue epi{&sd.st->ba, &sd.st->bb, 0.0, 0.0, nullptr, nullptr, nullptr};
-        backward_tile<float, true, SRV_CX, SRV_BK>(sd.g, sd.U, sd.V, epi, tbx, tby, tbz, sd.pb + local, red);
+        backward_tile<float, true, SRV_CX, SRV_BK>(sd.g, sd.U, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
+                                                   nullptr, sd.pb + local, red);
     }
 }
 
@@ -286,7 +287,7 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     if (st != CBCT_OK) return st;
     k_scale_inplace<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.U, n, &sl.st->c0, &sl.st->stop);
     Epilogue eb{&sl.st->ba, &sl.st->bb, 0.0, 0.0, sl.pb, &sl.st->stop, nullptr};
-    st = launch_backward(g, sl.U, sl.V, CBCT_F32, eb, s, true);
+    st = launch_backward(g, sl.U, sl.V, CBCT_F32, eb, s, true, nullptr);
     if (st != CBCT_OK) return st;
     gk_begin2<<<1, RED_THREADS, 0, s>>>(sl.st, sl.pb, sl.nb, r.method);
     k_start_dirs<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.V, sl.w, r.method == M_LSMR ? sl.h2 : nullptr, nullptr,

@@ -266,6 +266,9 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     CBCT_CUDA_TRY(ws.alloc(&pv, (size_t)VEC_BLOCKS));
     CBCT_CUDA_TRY(ws.alloc(&hist, (size_t)3 * iters));
     CBCT_CUDA_TRY(ws.alloc(&dst, 1));
+    float *accum = nullptr;         // running sums of a transpose summed in passes
+    if (g.angle_block < g.nangles) CBCT_CUDA_TRY(ws.alloc(&accum, (size_t)m));
+    const int bwd_passes = backward_passes(g, accum);
     CBCT_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * 3 * iters, s));
 
     Tracker tr;
@@ -291,10 +294,10 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     };
     auto bwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(1);
-        if (r == CBCT_OK) r = launch_backward(g, in, out, t, e, s, true);
+        if (r == CBCT_OK) r = launch_backward(g, in, out, t, e, s, true, accum);
         if (r == CBCT_OK) r = tr.mark(1);
-        ++tr.launches;
-        ++tr.bwd;
+        tr.launches += bwd_passes;
+        tr.bwd += bwd_passes;
         return r;
     };
 
@@ -414,6 +417,9 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     CBCT_CUDA_TRY(ws.alloc(&hist, (size_t)3 * iters));
     CBCT_CUDA_TRY(ws.alloc(&dst, 1));
     CBCT_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * 3 * iters, s));
+    float *accum = nullptr;         // running sums of a transpose summed in passes
+    if (g.angle_block < g.nangles) CBCT_CUDA_TRY(ws.alloc(&accum, (size_t)m));
+    const int bwd_passes = backward_passes(g, accum);
     Tracker tr;
     tr.profile = o->profile != 0;
     tr.s = s;
@@ -427,10 +433,10 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     };
     auto bwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(1);
-        if (r == CBCT_OK) r = launch_backward(g, in, out, CBCT_F32, e, s, true);
+        if (r == CBCT_OK) r = launch_backward(g, in, out, CBCT_F32, e, s, true, accum);
         if (r == CBCT_OK) r = tr.mark(1);
-        ++tr.launches;
-        ++tr.bwd;
+        tr.launches += bwd_passes;
+        tr.bwd += bwd_passes;
         return r;
     };
     CgState init{};

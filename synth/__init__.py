@@ -123,7 +123,8 @@ def _cube(n, voxel, nu, nv, pix, nangles, dso, dsd, arc=360.0, nvox_z=None, pix_
 
 # Workload shapes.  "tiny"/"small" are test cases; c1..c5 are the five
 # benchmark configurations (medical CBCT at 32^3..512^3 and a high-magnification
-# micro-CT at 1024^3).  Unstated sizes follow the readings recorded in the design doc.
+# micro-CT at 1024^3).  Sizes the paper does not state (voxel and pixel pitch,
+# distances of the smaller cases) are chosen so the detector covers the volume.
 def config(name: str) -> Geometry:
     if name == "tiny":        # 8^3, 16x16 detector, 20 angles: dense A is 5120 x 512
         return _cube(8, 1.0, 16, 16, 1.2, 20, 100.0, 150.0)

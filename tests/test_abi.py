@@ -77,6 +77,8 @@ def test_launch_shape_calls_reject_null(lib):
     assert lib.cbct_geometry_set_launch(None, 2, 0) == cbct.CBCT_EINVAL
     assert lib.cbct_geometry_get_launch(None, None, None) == cbct.CBCT_EINVAL
     assert lib.cbct_geometry_autotune(None, 8, None, None) == cbct.CBCT_EINVAL
+    assert lib.cbct_geometry_set_angle_block(None, 4) == cbct.CBCT_EINVAL
+    assert lib.cbct_geometry_get_angle_block(None, None) == cbct.CBCT_EINVAL
 
 
 def test_server_argument_checks(lib):

@@ -120,6 +120,26 @@ def test_every_launch_shape_matches_oracle(cbct, name):
         cbct.set_launch(geom, 3, 0)
 
 
+@pytest.mark.parametrize("name", ["small", "short_scan"])
+def test_transpose_in_angle_passes_matches_oracle(cbct, name):
+    """The transpose summed in passes over blocks of angles (FP32 running sums
+    between passes) computes the same A^T y, for every block size."""
+    g = GEOMS[name]
+    geom = cbct.Geometry(g)
+    y = synth.random_projections(g, 31).astype(np.float32)
+    x_ref = oracle.backproject(g, y.astype(np.float64), 8)
+    for block in (1, 4, g.nangles - 1, g.nangles):
+        cbct.set_angle_block(geom, block)
+        assert cbct.get_angle_block(geom) == block
+        for bc in range(len(cbct.BWD_CONFIGS)):
+            cbct.set_launch(geom, 2, bc)
+            assert_close(cbct.backproject(geom, dev(y)).cpu().numpy(), x_ref)
+    cbct.set_angle_block(geom, 0)
+    assert cbct.get_angle_block(geom) == g.nangles        # small scans fit in one pass
+    with pytest.raises(cbct.CbctError):
+        cbct.set_angle_block(geom, -1)
+
+
 def test_autotune_picks_a_valid_shape(cbct):
     g = synth.config("c1")
     geom = cbct.Geometry(g)

@@ -243,6 +243,24 @@ def test_graph_replay_matches_plain_launches(cbct, c1_problem):
     np.testing.assert_allclose(rg.resid, rp.resid, rtol=1e-6)
 
 
+@pytest.mark.parametrize("method", ["cgls", "lsqr", "lsmr", "hybrid_lsqr"])
+def test_transpose_in_angle_passes(cbct, c1_problem, method):
+    """Solvers whose transpose is summed in passes over blocks of angles (and
+    graph-replayed) reach the same iterates: only the FP32 summation order of
+    A^T differs."""
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    x1, r1 = getattr(cbct, method)(geom, dev(b), 10)
+    cbct.set_angle_block(geom, 7)
+    x2, r2 = getattr(cbct, method)(geom, dev(b), 10)
+    x3, _ = getattr(cbct, method)(geom, dev(b), 10, use_graph=False)
+    assert r2.backward_launches > r1.backward_launches
+    assert rel(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-5
+    assert rel(x3.cpu().numpy(), x2.cpu().numpy()) <= 1e-6
+    x_ref, _ = oracle_solve(g, b, method, 10)
+    assert rel(x2.cpu().numpy(), x_ref) <= ITER_TOL
+
+
 def test_host_buffers(cbct, c1_problem):
     g, _, b = c1_problem
     geom = cbct.Geometry(g)
