@@ -99,6 +99,22 @@ cbct_status cbct_project(const cbct_geometry *geom, const void *x, void *y,
 cbct_status cbct_backproject(const cbct_geometry *geom, const void *y, void *x,
                              cbct_dtype dtype, cbct_stream stream);
 
+/* cbct_project without any device allocation, for callers that cannot call
+ * cudaMalloc (the paper has no counterpart: it is an interface variant, not a
+ * step of the method).  Same arguments, layouts and result as cbct_project;
+ * the z-fastest copy of the volume that cbct_project allocates per call lives
+ * here in a fixed 64 MiB array of the library's device memory, so the volume
+ * may hold at most 2^24 FP32 or 2^25 FP16/BF16 voxels (a 256^3 FP32 volume);
+ * larger volumes are rejected with CBCT_EINVAL before any work is queued.
+ * The geometry's device must be the current device (else CBCT_EINVAL).  The
+ * first call on a device looks the array up (cudaGetSymbolAddress); make it
+ * before capturing a stream.  Every call on a device shares the one array,
+ * which keeps the last call's contents (each call overwrites all it reads):
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and give wrong results, so serialise them on one stream. */
+cbct_status cbct_project_static(const cbct_geometry *geom, const void *x, void *y,
+                                cbct_dtype dtype, cbct_stream stream);
+
 /* Number of nonzeros of A (positive-length ray/voxel pairs in FP32), counted
  * by the forward traversal.  Synchronises `stream`. */
 cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream stream);

@@ -99,7 +99,7 @@ def load(path: str = LIB_PATH):
     lib.cbct_geometry_num_voxels.restype = i64
     lib.cbct_geometry_num_rays.argtypes = [G]
     lib.cbct_geometry_num_rays.restype = i64
-    for fn in ("cbct_project", "cbct_backproject"):
+    for fn in ("cbct_project", "cbct_backproject", "cbct_project_static"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.c_int, vp]
     lib.cbct_count_nnz.argtypes = [G, ctypes.POINTER(i64), vp]
     lib.cbct_geometry_set_launch.argtypes = [G, ctypes.c_int, ctypes.c_int]
@@ -220,6 +220,22 @@ def project(geom: Geometry, x, out=None, stream=None):
     _check("cbct_project", load().cbct_project(geom.handle, ctypes.c_void_p(x.data_ptr()),
                                                ctypes.c_void_p(out.data_ptr()), _dtype_code(x.dtype),
                                                _stream_handle(stream)))
+    return out
+
+
+def project_static(geom: Geometry, x, out=None, stream=None):
+    """y = A x like project(), through cbct_project_static, which allocates no
+    device memory (volume of at most 64 MiB; calls must not overlap on the GPU)."""
+    import torch
+    _require_cuda(x, "x", geom.num_voxels)
+    if out is None:
+        out = torch.empty(geom.proj_shape, dtype=x.dtype, device=x.device)
+    _require_cuda(out, "out", geom.num_rays)
+    if out.dtype != x.dtype:
+        raise TypeError("x and out must share a dtype")
+    _check("cbct_project_static", load().cbct_project_static(geom.handle, ctypes.c_void_p(x.data_ptr()),
+                                                             ctypes.c_void_p(out.data_ptr()), _dtype_code(x.dtype),
+                                                             _stream_handle(stream)))
     return out
 
 

@@ -1,0 +1,76 @@
+// cbct_project_static: the forward projection y = A x of cbct_project for
+// callers that cannot allocate device memory.  cbct_project re-lays the
+// caller's volume x[k][j][i] into a z-fastest temporary that it allocates on
+// the stream; here that temporary is a fixed array in the library's own
+// device memory, so the call allocates nothing.
+#include <mutex>
+
+#include "common.cuh"
+
+namespace cbct {
+
+// Largest re-laid volume the static scratch holds: 64 MiB, i.e. 2^24 FP32
+// voxels (a 256^3 volume) or 2^25 FP16/BF16 voxels.
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)64 << 20;
+
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+static std::mutex g_scratch_mutex;
+static void *g_scratch_ptr[MAX_DEVICES];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the first call on a device also loads the module there).
+static cbct_status scratch_for_current_device(void **out) {
+    int dev = 0;
+    CBCT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEVICES) {
+        set_error("cbct_project_static: device ordinal out of range");
+        return CBCT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t err = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (err != cudaSuccess) return cuda_fail(err, "cbct_project_static: cudaGetSymbolAddress");
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return CBCT_OK;
+}
+
+}  // namespace cbct
+
+using namespace cbct;
+
+extern "C" cbct_status cbct_project_static(const cbct_geometry *g, const void *x, void *y, cbct_dtype t,
+                                           cbct_stream stream) {
+    if (!g || !x || !y) { set_error("cbct_project_static: null geometry or buffer"); return CBCT_EINVAL; }
+    if (t != CBCT_F32 && t != CBCT_F16 && t != CBCT_BF16) {
+        set_error("cbct_project_static: unknown dtype");
+        return CBCT_EINVAL;
+    }
+    const size_t bytes = (size_t)cbct_geometry_num_voxels(g) * dtype_size(t);
+    if (bytes > STATIC_SCRATCH_BYTES) {
+        set_error("cbct_project_static: volume needs more than the 64 MiB of static scratch "
+                  "(at most 2^24 FP32 or 2^25 FP16/BF16 voxels)");
+        return CBCT_EINVAL;
+    }
+    int dev = 0;
+    CBCT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != g->device) {
+        set_error("cbct_project_static: the geometry's device is not the current device");
+        return CBCT_EINVAL;
+    }
+    void *scratch = nullptr;
+    cbct_status st = scratch_for_current_device(&scratch);
+    if (st != CBCT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // The re-layout writes every one of the M scratch values before the forward
+    // kernel reads any, so nothing left by an earlier call is used and nothing
+    // has to be cleared.
+    st = launch_relayout(g->dev, x, scratch, t, true, s);
+    if (st != CBCT_OK) return st;
+    const Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
+    return launch_forward(g->dev, scratch, y, t, epi, s, false);
+}
