@@ -124,16 +124,17 @@ cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream 
  * tile (1, 2 or 4; a warp follows 32 * fwd_rows rows of one detector column).
  * bwd_config: tile of the transpose (one warp per voxel column), 0 = 4 x 2
  * columns x 32 voxels along z (1 per lane), 1 = 4 x 2 x 64 (2 per lane),
- * 2 = 8 x 1 x 32, 3 = 2 x 4 x 64.  Changing the shape while another thread
- * uses the geometry is a data race. */
-#define CBCT_TUNE_TIMES 7
+ * 2 = 8 x 1 x 32, 3 = 2 x 4 x 64, 4 = 4 x 2 x 128 (4 per lane),
+ * 5 = 2 x 4 x 128.  Changing the shape while another thread uses the
+ * geometry is a data race. */
+#define CBCT_TUNE_TIMES 9
 cbct_status cbct_geometry_set_launch(cbct_geometry *geom, int fwd_rows, int bwd_config);
 cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, int *bwd_config);
 /* Times every launch shape (forward and transpose, FP32, on a strided subset
  * of at most max_angles angles; max_angles <= 0 = all) and keeps the fastest.
  * times_ms, if non-null, is a host array of CBCT_TUNE_TIMES doubles that
  * receives the forward times for fwd_rows 1, 2, 4 and the transpose times for
- * bwd_config 0..3.  Allocates scratch on `stream` and synchronises it. */
+ * bwd_config 0..5.  Allocates scratch on `stream` and synchronises it. */
 cbct_status cbct_geometry_autotune(cbct_geometry *geom, int max_angles, double *times_ms, cbct_stream stream);
 /* Angles per pass of the transpose inside the solvers and cbct_backproject
  * (performance only).  With a

@@ -260,9 +260,10 @@ def count_nnz(geom: Geometry, stream=None) -> int:
     return int(n.value)
 
 
-TUNE_TIMES = 7
+TUNE_TIMES = 9
 FWD_ROWS = (1, 2, 4)
-BWD_CONFIGS = ("4x2 columns x 32", "4x2 columns x 64", "8x1 columns x 32", "2x4 columns x 64")
+BWD_CONFIGS = ("4x2 columns x 32", "4x2 columns x 64", "8x1 columns x 32", "2x4 columns x 64",
+               "4x2 columns x 128", "2x4 columns x 128")
 
 
 def set_launch(geom: Geometry, fwd_rows: int, bwd_config: int):

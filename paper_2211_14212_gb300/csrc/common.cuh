@@ -45,6 +45,7 @@ struct DevGeom {
     const float4 *ray_z;     // [nv]: (fz, Iz, pqz, 0)
     const float *ray_len;    // [nu][nv]
     const float2 *trig;      // [nangles] (cos t, sin t), for footprint windows only
+    const float2 *zbox;      // [nz][nv]: alpha interval (entry, exit) of row iv's ray in z slab k
     int fwd_rows;            // forward tile: rays per lane (1, 2 or 4)
     int bwd_config;          // transpose tile: column patch / voxels per lane (backward_shape)
     int angle_block;         // transpose: angles per pass when summed in passes (launch_backward)
@@ -152,6 +153,9 @@ cbct_status launch_backward(const DevGeom &g, const void *y_vfast, void *x, cbct
                             const Epilogue &epi, cudaStream_t s, bool zfast, float *accum);
 int backward_passes(const DevGeom &g, const float *accum);
 int default_angle_block(const DevGeom &g);
+// Fills DevGeom::zbox (nz * nv entries) from the z tables; synchronous use at
+// geometry creation (legacy default stream).
+cudaError_t launch_zbox(const DevGeom &g, float2 *zbox);
 cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_zfast,
                             cudaStream_t s);
 cbct_status launch_proj_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_vfast,
@@ -162,6 +166,6 @@ int backward_num_blocks(const DevGeom &g);
 dim3 forward_grid(const DevGeom &g);
 dim3 backward_grid(const DevGeom &g);
 BrickShape backward_shape(int config);
-constexpr int NUM_FWD_ROWS = 3, NUM_BWD_CONFIGS = 4;
+constexpr int NUM_FWD_ROWS = 3, NUM_BWD_CONFIGS = 6;
 
 }  // namespace cbct

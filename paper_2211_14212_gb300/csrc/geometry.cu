@@ -146,21 +146,16 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
     const size_t s_xy = align(xy.size() * sizeof(float4)), s_q = align(xyq.size() * sizeof(float2));
     const size_t s_z = align(zt.size() * sizeof(float4));
     const size_t s_len = align(len.size() * sizeof(float)), s_tr = align(trig.size() * sizeof(float2));
-    const size_t o_q = s_xy, o_z = o_q + s_q, o_len = o_z + s_z, o_tr = o_len + s_len;
+    const size_t s_zb = align((size_t)nz * nv * sizeof(float2));
+    const size_t o_q = s_xy, o_z = o_q + s_q, o_len = o_z + s_z, o_tr = o_len + s_len, o_zb = o_tr + s_tr;
     cudaError_t err = cudaGetDevice(&g->device);
     char *mem = nullptr;
-    if (err == cudaSuccess) err = cudaMalloc(&mem, o_tr + s_tr);
+    if (err == cudaSuccess) err = cudaMalloc(&mem, o_zb + s_zb);
     if (err == cudaSuccess) err = cudaMemcpy(mem, xy.data(), xy.size() * sizeof(float4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(mem + o_q, xyq.data(), xyq.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(mem + o_z, zt.data(), zt.size() * sizeof(float4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(mem + o_len, len.data(), len.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(mem + o_tr, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (err != cudaSuccess) {
-        if (mem) cudaFree(mem);
-        delete[] g->angles;
-        delete g;
-        return cuda_fail(err, "cbct_geometry_create");
-    }
     g->table_mem = mem;
     DevGeom &dg = g->dev;
     dg.nx = nx; dg.ny = ny; dg.nz = nz; dg.nu = nu; dg.nv = nv; dg.nangles = na;
@@ -172,6 +167,17 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
     dg.ray_z = reinterpret_cast<const float4 *>(mem + o_z);
     dg.ray_len = reinterpret_cast<const float *>(mem + o_len);
     dg.trig = reinterpret_cast<const float2 *>(mem + o_tr);
+    dg.zbox = reinterpret_cast<const float2 *>(mem + o_zb);
+    // the z slab crossings are computed on the device by the projectors' own
+    // plane_alpha, so that they are bit-identical to the forward traversal's
+    if (err == cudaSuccess) err = launch_zbox(dg, reinterpret_cast<float2 *>(mem + o_zb));
+    if (err == cudaSuccess) err = cudaStreamSynchronize(0);
+    if (err != cudaSuccess) {
+        if (mem) cudaFree(mem);
+        delete[] g->angles;
+        delete g;
+        return cuda_fail(err, "cbct_geometry_create");
+    }
     dg.fwd_rows = 2;
     dg.bwd_config = nz >= 64 ? 1 : 0;       // 2 voxels per lane once the column is deep enough
     dg.angle_block = default_angle_block(dg);

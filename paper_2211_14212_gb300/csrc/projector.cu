@@ -7,6 +7,7 @@
 // forward tile) and DevGeom::bwd_config (column patch and voxels per lane of
 // the transpose tile), set to defaults at creation and chosen by
 // cbct_geometry_autotune.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -121,6 +122,8 @@ BrickShape backward_shape(int config) {
     case 1: return BrickShape{4, 2, 64, 2};
     case 2: return BrickShape{8, 1, 32, 1};
     case 3: return BrickShape{2, 4, 64, 2};
+    case 4: return BrickShape{4, 2, 128, 4};
+    case 5: return BrickShape{2, 4, 128, 4};
     default: return BrickShape{4, 2, 32, 1};
     }
 }
@@ -145,6 +148,8 @@ static void launch_backward_t(const DevGeom &g, const void *y, void *x, const Ep
     case 1: backward_kernel<T, ZF, 4, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     case 2: backward_kernel<T, ZF, 8, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     case 3: backward_kernel<T, ZF, 2, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 4: backward_kernel<T, ZF, 4, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 5: backward_kernel<T, ZF, 2, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     default: backward_kernel<T, ZF, 4, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     }
 }
@@ -182,6 +187,37 @@ cbct_status launch_backward(const DevGeom &g, const void *y, void *x, cbct_dtype
     }
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
+}
+
+// ------------------------------------------------------ z slab crossings
+// zbox[k][iv] = (entry, exit) alpha of row iv's ray in z slab k, i.e. the two
+// z plane crossings ordered; a ray in a z plane (I == 0) is inside slab pq
+// for every alpha and outside every other slab.  The rows' z tables do not
+// depend on the angle (circular orbit), so one table serves all angles.
+__global__ void zbox_kernel(DevGeom g, float2 *__restrict__ zbox) {
+    const size_t n = (size_t)g.nz * g.nv;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx / g.nv), iv = (int)(idx % g.nv);
+        const float4 z = g.ray_z[iv];
+        const float kf = (float)k;
+        float2 r;
+        if (z.y == 0.0f) {
+            r = z.z == kf ? make_float2(-FLT_MAX, FLT_MAX) : make_float2(FLT_MAX, FLT_MAX);
+        } else {
+            const RayAxis rz{z.x, z.y, z.z};
+            const float e0 = plane_alpha(kf - z.z, g.dz, rz);
+            const float e1 = plane_alpha((kf + 1.0f) - z.z, g.dz, rz);
+            r = make_float2(fminf(e0, e1), fmaxf(e0, e1));
+        }
+        zbox[idx] = r;
+    }
+}
+
+cudaError_t launch_zbox(const DevGeom &g, float2 *zbox) {
+    const size_t n = (size_t)g.nz * g.nv;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    zbox_kernel<<<blocks, 256, 0, 0>>>(g, zbox);
+    return cudaGetLastError();
 }
 
 // -------------------------------------------------- projection re-layout

@@ -269,9 +269,11 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
 // y plane crossings, warp-uniform).  A lane then inverts z(alpha) =
 // v (dso/dsd + alpha) over [ain, aout] to get the detector rows that can meet
 // its voxel's z slab, and takes for each the segment
-//     [max(ain, z entry), min(aout, z exit)]
-// from the same plane_alpha values as the forward traversal, so every length
-// is bit-identical to the forward projector's: A^T is the exact transpose.
+//     [max(ain, z entry), min(aout, z exit)].
+// The z entry/exit of a row's ray in slab k does not depend on the angle
+// (circular orbit), so it is read from the table DevGeom::zbox, which
+// plane_alpha filled at geometry creation: every length is bit-identical to
+// the forward projector's, and A^T is the exact transpose.
 // Projections are read v-fastest: y[a][iu][iv].
 
 constexpr int BWD_THREADS = 256;
@@ -351,19 +353,10 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const T *__restr
                     const float vmax = fmaxf(zr_hi[kk] * rlo, zr_hi[kk] * rhi);
                     const int r0 = max(0, (int)ceilf(vmin + (cv - 0.05f)));
                     const int r1 = min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f)));
-                    const float kf = (float)k;
+                    const float2 *zb = g.zbox + (size_t)k * g.nv;
                     for (int iv = r0; iv <= r1; ++iv) {
-                        const float4 z = g.ray_z[iv];
-                        float lo = ain, hi = aout;
-                        if (z.y == 0.0f) {              // ray in a z plane: half-open voxel index z.z
-                            if (z.z != kf) hi = lo;
-                        } else {
-                            const RayAxis rz{z.x, z.y, z.z};
-                            const float e0 = plane_alpha(kf - z.z, g.dz, rz);
-                            const float e1 = plane_alpha((kf + 1.0f) - z.z, g.dz, rz);
-                            lo = fmaxf(lo, fminf(e0, e1));
-                            hi = fminf(hi, fmaxf(e0, e1));
-                        }
+                        const float2 e = zb[iv];         // row iv's alpha interval in slab k
+                        const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
                         // a miss adds exactly zero: the same sum as skipping it
                         acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), lcol[iv] * Storage<T>::load(pcol + iv), acc[kk]);
                     }
