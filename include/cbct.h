@@ -122,11 +122,11 @@ cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream 
 /* Launch shapes of the projectors of one geometry (performance only: every
  * shape computes the same A and A^T).  fwd_rows: rays per lane of the forward
  * tile (1, 2 or 4; a warp follows 32 * fwd_rows rows of one detector column).
- * bwd_config: tile of the transpose (one warp per voxel column), 0 = 4 x 2
- * columns x 32 voxels along z (1 per lane), 1 = 4 x 2 x 64 (2 per lane),
- * 2 = 8 x 1 x 32, 3 = 2 x 4 x 64, 4 = 4 x 2 x 128 (4 per lane),
- * 5 = 2 x 4 x 128.  Changing the shape while another thread uses the
- * geometry is a data race. */
+ * bwd_config: tile of the transpose (one lane per voxel column, 32 columns
+ * along x per warp), as (columns along x) x (rows along y) x (slabs along z):
+ * 0 = 32 x 8 x 4 (4 slabs per lane), 1 = 32 x 4 x 8 (4), 2 = 32 x 8 x 8 (8),
+ * 3 = 32 x 4 x 16 (8), 4 = 32 x 2 x 32 (8), 5 = 32 x 8 x 16 (16).  Changing
+ * the shape while another thread uses the geometry is a data race. */
 #define CBCT_TUNE_TIMES 9
 cbct_status cbct_geometry_set_launch(cbct_geometry *geom, int fwd_rows, int bwd_config);
 cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, int *bwd_config);
@@ -157,17 +157,22 @@ cbct_status cbct_geometry_get_angle_block(const cbct_geometry *geom, int *angles
  * allocates its workspace per call with stream-ordered allocation and frees
  * it before returning. */
 
-typedef enum { CBCT_LAMBDA_FIXED = 0, CBCT_LAMBDA_GCV = 1 } cbct_lambda_rule;
+typedef enum { CBCT_LAMBDA_FIXED = 0, CBCT_LAMBDA_GCV = 1, CBCT_LAMBDA_DP = 2 } cbct_lambda_rule;
 
 typedef struct {
     int iters;               /* iterations (>= 1) */
     double lambda;           /* Tikhonov lambda (Sec. 2.2, Eq. 6): damping of CGLS/LSQR/LSMR,
                                 or the fixed lambda of hybrid LSQR with CBCT_LAMBDA_FIXED */
-    cbct_lambda_rule rule;   /* hybrid LSQR only: fixed lambda or GCV (Sec. 2.2.2) */
+    cbct_lambda_rule rule;   /* hybrid LSQR only: fixed lambda, GCV or the discrepancy
+                                principle (Sec. 2.2.2) */
     cbct_dtype storage;      /* storage type of the Krylov vectors (u, v, basis V_k) */
     int use_graph;           /* nonzero: capture one iteration as a CUDA graph and replay it */
     int profile;             /* nonzero: time every projector launch with CUDA events (disables
                                 the graph) and fill the report's *_ms fields */
+    double noise_level;      /* CBCT_LAMBDA_DP: nl = ||e|| / ||b||; lambda_k is the root of
+                                ||b - A x_lambda|| = nl ||b|| on the projected problem, found by
+                                bisection in log lambda over sigma_max [1e-8, 1e8]; 0 while even
+                                the smallest lambda leaves the residual above the target */
 } cbct_solve_opts;
 
 /* Per-iteration histories, written to caller-allocated HOST arrays of length
@@ -211,22 +216,31 @@ cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *geom, const float *b, fl
  * ("continuous batching"; no counterpart in the paper, which solves one scan at
  * a time).  Submitted requests wait in FIFO order and are admitted as slots
  * while the device memory they need fits the budget; a library-owned worker
- * thread then advances every admitted request by one Krylov iteration per step
- * (one multi-instance launch per kernel for all of them), reads out finished
- * results, frees their memory and admits waiting requests between steps.
- * Each result equals the single-request solver's (same kernels, same
- * reduction order) up to the FP32 rounding of the transpose's shared-memory
- * accumulation.  Requests use FP32 storage and LSQR or LSMR.  All calls are
- * thread-safe except cbct_server_destroy, which must not overlap any other
- * call on the same server. */
+ * thread then runs steps: one Krylov iteration of a set of admitted requests
+ * (one multi-instance launch per kernel for all of them), after which it reads
+ * out finished results, frees their memory and admits waiting requests.  Which
+ * admitted requests a step advances is the schedule: CBCT_SCHED_SRPT (default)
+ * takes them in order of least remaining work (iterations left x rays x
+ * (nx + ny)) while the step's forward tiles (8 detector columns x 64 rows of
+ * one angle each) stay within 4096, about five waves of the GPU, so small
+ * requests are batched and large ones run one at a time, shortest first;
+ * CBCT_SCHED_SHARE advances every admitted request every step.  Each result
+ * equals the single-request solver's (same kernels and per-voxel / per-ray
+ * summation order) up to the rounding of the blockwise norm reductions.
+ * Requests use FP32 storage and LSQR or LSMR.  All calls are thread-safe
+ * except cbct_server_destroy, which must not overlap any other call on the
+ * same server. */
 
 typedef struct cbct_server cbct_server;   /* opaque, library-owned */
 typedef enum { CBCT_SOLVER_LSQR = 0, CBCT_SOLVER_LSMR = 1 } cbct_solver;
+
+typedef enum { CBCT_SCHED_SRPT = 0, CBCT_SCHED_SHARE = 1 } cbct_schedule;
 
 typedef struct {
     size_t hbm_budget_bytes;   /* device memory the server may hold for requests (> 0) */
     int max_slots;             /* most requests in flight at once (1..64) */
     int use_graph;             /* nonzero: replay each step as one captured CUDA graph */
+    int schedule;              /* cbct_schedule: which admitted requests a step advances */
 } cbct_server_opts;
 
 typedef struct {

@@ -308,6 +308,52 @@ def gcv_lambda(sigma, p1, beta1):
     return math.exp(t)
 
 
+def projected_residual(sigma, p1, beta1, lam):
+    """||beta1 e1 - H_k y_lam|| of the projected Tikhonov solution (Eq. 8), from
+    H_k = P Sigma Q^T: the component of beta1 e1 outside range(H_k) plus the
+    filtered part inside it (the numerator of the GCV function, square-rooted)."""
+    k = sigma.shape[0]
+    s2 = sigma * sigma
+    l2 = lam * lam
+    f = l2 / (s2 + l2)
+    return math.sqrt(float(np.sum((f * beta1 * p1[:k]) ** 2) + (beta1 * p1[k]) ** 2))
+
+
+DP_DECADES = 8.0
+DP_REL_TOL = 1e-10
+
+
+def dp_lambda(sigma, p1, beta1, target):
+    """Discrepancy principle (Sec. 2.2.2): lam with ||b - A x_lam|| = target
+    (= nl ||b||), on the projected problem, where ||b - A V_k y|| equals
+    ||beta1 e1 - H_k y||.
+
+    The paper prints an argmin of ||A x_lam - b||^2 - nl^2 ||b||^2, unbounded
+    below as written; the reading here is the root of the equality.  The
+    projected residual grows monotonically with lam, so the root is bracketed
+    in log lam over [sigma_max 1e-8, sigma_max 1e8] and found by bisection to a
+    bracket narrower than 1e-10 (relative); if even the smallest lam leaves a
+    residual above the target (too few iterations yet), lam = 0, and if the
+    largest one stays below it, lam = the upper end.
+    """
+    smax = float(np.max(sigma))
+    if smax == 0.0:
+        return 0.0
+    lo = math.log(smax) - DP_DECADES * math.log(10.0)
+    hi = math.log(smax) + DP_DECADES * math.log(10.0)
+    if projected_residual(sigma, p1, beta1, math.exp(lo)) >= target:
+        return 0.0
+    if projected_residual(sigma, p1, beta1, math.exp(hi)) <= target:
+        return math.exp(hi)
+    while hi - lo > DP_REL_TOL:
+        mid = 0.5 * (lo + hi)
+        if projected_residual(sigma, p1, beta1, math.exp(mid)) < target:
+            lo = mid
+        else:
+            hi = mid
+    return math.exp(0.5 * (lo + hi))
+
+
 def projected_tikhonov(h, beta1, lam, svd=None):
     """y = argmin ||beta1 e1 - H y||^2 + lam^2 ||y||^2 (Eq. 8) via the SVD H = P Sigma Q^T."""
     p, sigma, qt = np.linalg.svd(h, full_matrices=True) if svd is None else svd
@@ -317,8 +363,9 @@ def projected_tikhonov(h, beta1, lam, svd=None):
     return qt.T @ coef
 
 
-def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False):
-    """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lam_k fixed or chosen by GCV (Sec. 2.2.2).
+def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False, noise_level=0.0):
+    """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lam_k fixed, chosen by GCV or by the
+    discrepancy principle with relative noise level nl = noise_level (Sec. 2.2.2).
 
     Stores the basis V_k; at every iteration k solves the projected Tikhonov
     problem for y_k and forms x_k = V_k y_k.  History: ``resid`` = projected
@@ -354,6 +401,8 @@ def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False):
         svd = np.linalg.svd(h, full_matrices=True)
         if rule == "gcv":
             lam_k = gcv_lambda(svd[1], svd[0][0, :], beta1)
+        elif rule == "dp":
+            lam_k = dp_lambda(svd[1], svd[0][0, :], beta1, noise_level * beta1)
         elif rule == "fixed":
             lam_k = float(lam)
         else:

@@ -22,7 +22,7 @@ CBCT_OK, CBCT_EINVAL, CBCT_ENOMEM, CBCT_ECUDA, CBCT_EBREAKDOWN, CBCT_ETIMEOUT, C
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBREAKDOWN", 5: "ETIMEOUT",
                 6: "EBUDGET", 7: "ENOTFOUND"}
 F32, F16, BF16 = 0, 1, 2
-LAMBDA_FIXED, LAMBDA_GCV = 0, 1
+LAMBDA_FIXED, LAMBDA_GCV, LAMBDA_DP = 0, 1, 2
 
 
 class CbctError(RuntimeError):
@@ -44,7 +44,8 @@ class _Desc(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("lam", ctypes.c_double), ("rule", ctypes.c_int),
-                ("storage", ctypes.c_int), ("use_graph", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("storage", ctypes.c_int), ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
+                ("noise_level", ctypes.c_double)]
 
 
 class _Report(ctypes.Structure):
@@ -60,7 +61,8 @@ class _Report(ctypes.Structure):
 
 
 class _ServerOpts(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("use_graph", ctypes.c_int)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("schedule", ctypes.c_int)]
 
 
 class _Times(ctypes.Structure):
@@ -262,8 +264,8 @@ def count_nnz(geom: Geometry, stream=None) -> int:
 
 TUNE_TIMES = 9
 FWD_ROWS = (1, 2, 4)
-BWD_CONFIGS = ("4x2 columns x 32", "4x2 columns x 64", "8x1 columns x 32", "2x4 columns x 64",
-               "4x2 columns x 128", "2x4 columns x 128")
+BWD_CONFIGS = ("32x8 columns x 4", "32x4 columns x 8", "32x8 columns x 8", "32x4 columns x 16",
+               "32x2 columns x 32", "32x8 columns x 16")
 
 
 def set_launch(geom: Geometry, fwd_rows: int, bwd_config: int):
@@ -315,7 +317,7 @@ class SolveReport:
 
 
 def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=True, x=None, stream=None,
-           profile=False):
+           profile=False, noise_level=0.0):
     """Run one of the C-ABI solvers.  b/x may be CUDA tensors or host (numpy or
     CPU torch, FP32) buffers; host buffers are staged by the library."""
     import torch
@@ -339,8 +341,10 @@ def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=Tru
         if xh.dtype != np.float32 or not xh.flags.c_contiguous or xh.size != geom.num_voxels:
             raise TypeError("host x must be a contiguous float32 array of %d elements" % geom.num_voxels)
         bptr, xptr = bh.ctypes.data, xh.ctypes.data
-    rule_code = {"fixed": LAMBDA_FIXED, "gcv": LAMBDA_GCV}[rule] if isinstance(rule, str) else int(rule)
-    opts = _Opts(int(iters), float(lam), rule_code, STORAGE[storage], 1 if use_graph else 0, 1 if profile else 0)
+    rule_code = ({"fixed": LAMBDA_FIXED, "gcv": LAMBDA_GCV, "dp": LAMBDA_DP}[rule] if isinstance(rule, str)
+                 else int(rule))
+    opts = _Opts(int(iters), float(lam), rule_code, STORAGE[storage], 1 if use_graph else 0, 1 if profile else 0,
+                 float(noise_level))
     hr = np.zeros(iters, dtype=np.float64)
     hn = np.zeros(iters, dtype=np.float64)
     hl = np.zeros(iters, dtype=np.float64)
@@ -370,9 +374,10 @@ def lsmr(geom, b, iters, lam=0.0, **kw):
     return _solve("cbct_lsmr_solve", geom, b, iters, lam=lam, **kw)
 
 
-def hybrid_lsqr(geom, b, iters, rule="gcv", lam=0.0, **kw):
-    """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lambda_k fixed or by GCV (Sec. 2.2.2)."""
-    return _solve("cbct_hybrid_lsqr_solve", geom, b, iters, lam=lam, rule=rule, **kw)
+def hybrid_lsqr(geom, b, iters, rule="gcv", lam=0.0, noise_level=0.0, **kw):
+    """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lambda_k fixed, by GCV or by the
+    discrepancy principle with relative noise level `noise_level` (Sec. 2.2.2)."""
+    return _solve("cbct_hybrid_lsqr_solve", geom, b, iters, lam=lam, rule=rule, noise_level=noise_level, **kw)
 
 
 # ------------------------------------------------------------------ serving
@@ -387,14 +392,16 @@ class ServedResult:
 
 class Server:
     """Continuous-batching server (cbct_server_*): requests of different scans
-    are admitted by device-memory budget and advanced together, one Krylov
-    iteration of every admitted request per step."""
+    are admitted by device-memory budget and advanced in steps of one Krylov
+    iteration; schedule "srpt" (default) advances the requests with the least
+    remaining work until a step fills the GPU, "share" advances all of them."""
 
     SOLVERS = {"lsqr": 0, "lsmr": 1}
+    SCHEDULES = {"srpt": 0, "share": 1}
 
-    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, use_graph: bool = True):
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, use_graph: bool = True, schedule: str = "srpt"):
         lib = load()
-        o = _ServerOpts(int(hbm_budget_bytes), int(max_slots), 1 if use_graph else 0)
+        o = _ServerOpts(int(hbm_budget_bytes), int(max_slots), 1 if use_graph else 0, self.SCHEDULES[schedule])
         h = ctypes.c_void_p()
         _check("cbct_server_create", lib.cbct_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -179,7 +179,7 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
         return cuda_fail(err, "cbct_geometry_create");
     }
     dg.fwd_rows = 2;
-    dg.bwd_config = nz >= 64 ? 1 : 0;       // 2 voxels per lane once the column is deep enough
+    dg.bwd_config = nz >= 8 ? 2 : 0;        // 8 slabs per lane once the volume is deep enough
     dg.angle_block = default_angle_block(dg);
     *out = g;
     return CBCT_OK;

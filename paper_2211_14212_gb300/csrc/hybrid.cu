@@ -9,12 +9,17 @@
 //   2. obtains the first row of P: P[0][i] = (H Q)[0][i] / sigma_i for the k
 //      singular vectors and, for the (k+1)-th, 1/||z|| with z the null vector
 //      of H_k^T (z_0 = 1, z_{i+1} = -alpha_{i+1} z_i / beta_{i+2});
-//   3. picks lambda_k: fixed, or the minimiser of
+//   3. picks lambda_k: fixed; or the minimiser of
 //         G(lam) = ||(I - H H^+_lam) beta_1 e_1||^2 / (trace(I - H H^+_lam))^2,
 //      H^+_lam = (H^T H + lam^2 I)^{-1} H^T, evaluated from the SVD; the
 //      minimiser is taken on a 200-point log grid over [sigma_max 1e-8,
 //      sigma_max] (ties to the larger lambda) and refined by golden-section
-//      search in log lambda on the neighbouring bracket to 1e-10;
+//      search in log lambda on the neighbouring bracket to 1e-10; or (the
+//      discrepancy principle) the root of ||beta_1 e_1 - H y_lam|| = nl beta_1,
+//      the projected form of ||b - A x_lam|| = nl ||b||, by bisection in
+//      log lambda over sigma_max [1e-8, 1e8] to 1e-10 (0 if even the
+//      smallest lambda leaves the residual above the target, the upper end if
+//      the largest stays below it);
 //   4. forms y_k = sum_i q_i beta_1 (H Q)[0][i] / (sigma_i^2 + lam^2) and the
 //      coefficients of the stored basis vectors, x_k = sum_j coef_j V_j.
 #include <cfloat>
@@ -45,6 +50,22 @@ __device__ double gcv_value(const double *sig, const double *p1, int k, double b
     return num / (den * den);
 }
 
+// ||beta_1 e_1 - H y_lam|| from the SVD (the GCV numerator, square-rooted).
+__device__ double projected_residual(const double *sig, const double *p1, int k, double beta1, double lam) {
+    const double l2 = lam * lam;
+    double num = 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double s2 = sig[i] * sig[i];
+        const double f = (s2 + l2) > 0.0 ? l2 / (s2 + l2) : 1.0;
+        const double t = f * beta1 * p1[i];
+        num += t * t;
+    }
+    num += (beta1 * p1[k]) * (beta1 * p1[k]);
+    return sqrt(num);
+}
+
+constexpr double DP_DECADES = 8.0, DP_TOL = 1e-10;
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -53,8 +74,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(PS_THREADS)
 projected_solve_kernel(const double *__restrict__ alphas, const double *__restrict__ betas,
                        const double *__restrict__ scales, const int *iter_ptr, const int *stop, int rule,
-                       double lambda_fixed, double *work, int kmax, double *coef, double *hist_lambda,
-                       double *hist_resid) {
+                       double lambda_fixed, double noise_level, double *work, int kmax, double *coef,
+                       double *hist_lambda, double *hist_resid) {
     __shared__ int rotated;
     __shared__ double gvals[GCV_POINTS];
     __shared__ double lam_sh;
@@ -148,6 +169,29 @@ projected_solve_kernel(const double *__restrict__ alphas, const double *__restri
     // lambda_k
     if (rule == CBCT_LAMBDA_FIXED) {
         if (tid == 0) lam_sh = lambda_fixed;
+    } else if (rule == CBCT_LAMBDA_DP) {
+        if (tid == 0) {
+            double smax = 0.0;
+            for (int i = 0; i < k; ++i) smax = fmax(smax, sig[i]);
+            const double target = noise_level * beta1;
+            double lam = 0.0;
+            if (smax > 0.0) {
+                double lo = log(smax) - DP_DECADES * log(10.0), hi = log(smax) + DP_DECADES * log(10.0);
+                if (projected_residual(sig, p1, k, beta1, exp(lo)) >= target) {
+                    lam = 0.0;
+                } else if (projected_residual(sig, p1, k, beta1, exp(hi)) <= target) {
+                    lam = exp(hi);
+                } else {
+                    while (hi - lo > DP_TOL) {
+                        const double mid = 0.5 * (lo + hi);
+                        if (projected_residual(sig, p1, k, beta1, exp(mid)) < target) lo = mid;
+                        else hi = mid;
+                    }
+                    lam = exp(0.5 * (lo + hi));
+                }
+            }
+            lam_sh = lam;
+        }
     } else {
         double smax = 0.0;
         for (int i = 0; i < k; ++i) smax = fmax(smax, sig[i]);
@@ -194,25 +238,17 @@ projected_solve_kernel(const double *__restrict__ alphas, const double *__restri
         coef[j] = y / (scales[j] * alphas[j]);
     }
     if (tid == 0) {
-        double num = 0.0;
-        for (int i = 0; i < k; ++i) {
-            const double s2 = sig[i] * sig[i];
-            const double f = (s2 + l2) > 0.0 ? l2 / (s2 + l2) : 1.0;
-            const double t = f * beta1 * p1[i];
-            num += t * t;
-        }
-        num += (beta1 * p1[k]) * (beta1 * p1[k]);
         hist_lambda[k - 1] = lam;
-        hist_resid[k - 1] = sqrt(num);
+        hist_resid[k - 1] = projected_residual(sig, p1, k, beta1, lam);
     }
 }
 
 cbct_status launch_projected_solve(const double *alphas, const double *betas, const double *scales,
                                    const int *iter, const int *stop, int rule, double lambda_fixed,
-                                   double *work, int kmax, double *coef, double *hist_lambda,
-                                   double *hist_resid, cudaStream_t s) {
-    projected_solve_kernel<<<1, PS_THREADS, 0, s>>>(alphas, betas, scales, iter, stop, rule, lambda_fixed, work,
-                                                     kmax, coef, hist_lambda, hist_resid);
+                                   double noise_level, double *work, int kmax, double *coef,
+                                   double *hist_lambda, double *hist_resid, cudaStream_t s) {
+    projected_solve_kernel<<<1, PS_THREADS, 0, s>>>(alphas, betas, scales, iter, stop, rule, lambda_fixed,
+                                                     noise_level, work, kmax, coef, hist_lambda, hist_resid);
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }

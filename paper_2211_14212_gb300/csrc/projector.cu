@@ -37,8 +37,9 @@ count_kernel(DevGeom g, unsigned long long *count) {
     if (iu < g.nu) {
         RayAxis rx, ry, rz[R];
         load_rays<R>(g, blockIdx.z, iu, blockIdx.y * 32 * R, g.nv, rx, ry, rz);
-        auto seg = [&](int, int, float len) { c += len > 0.0f; };
-        trace_columns<R>(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, 0, g.nz, g.nx * g.nz, seg);
+        auto fetch = [](int) { return 0.0f; };
+        auto seg = [&](int, float len, float) { c += len > 0.0f; };
+        trace_columns<R>(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, 0, g.nz, g.nx * g.nz, fetch, seg);
     }
     const double s = block_sum<FWD_THREADS>((double)c, red);
     if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)s);
@@ -105,26 +106,27 @@ cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaSt
 
 // ---------------------------------------------------------- transpose A^T y
 
-template <typename T, bool ZFAST, int CX, int K>
-__global__ void __launch_bounds__(BWD_THREADS)
-backward_kernel(DevGeom g, const T *__restrict__ proj, T *__restrict__ vol, Epilogue epi, int a_begin, int a_end,
+template <typename T, bool ZFAST, int CY, int K>
+__global__ void __launch_bounds__(BWD_THREADS, K >= 8 ? 3 : 4)
+backward_kernel(DevGeom g, const float *__restrict__ proj, T *__restrict__ vol, Epilogue epi, int a_begin, int a_end,
                 const float *acc_in, float *acc_out) {
     __shared__ double red[BWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    backward_tile<T, ZFAST, CX, K>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z, a_begin, a_end, acc_in,
+    backward_tile<T, ZFAST, CY, K>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z, a_begin, a_end, acc_in,
                                    acc_out, epi.partial ? epi.partial + b : nullptr, red);
 }
 
-// Transpose tile shapes: column patch CX x (8 / CX), 32 K voxels along z.
+// Transpose tile shapes: 32 voxel columns along x (one per lane) x CY rows j,
+// (8 / CY) blocks of K slabs along z.
 BrickShape backward_shape(int config) {
     switch (config) {
-    case 1: return BrickShape{4, 2, 64, 2};
-    case 2: return BrickShape{8, 1, 32, 1};
-    case 3: return BrickShape{2, 4, 64, 2};
-    case 4: return BrickShape{4, 2, 128, 4};
-    case 5: return BrickShape{2, 4, 128, 4};
-    default: return BrickShape{4, 2, 32, 1};
+    case 1: return BrickShape{32, 4, 8, 4};
+    case 2: return BrickShape{32, 8, 8, 8};
+    case 3: return BrickShape{32, 4, 16, 8};
+    case 4: return BrickShape{32, 2, 32, 8};
+    case 5: return BrickShape{32, 8, 16, 16};
+    default: return BrickShape{32, 8, 4, 4};
     }
 }
 
@@ -139,23 +141,23 @@ int backward_num_blocks(const DevGeom &g) {
 }
 
 template <typename T, bool ZF>
-static void launch_backward_t(const DevGeom &g, const void *y, void *x, const Epilogue &epi, cudaStream_t s,
+static void launch_backward_t(const DevGeom &g, const float *y, void *x, const Epilogue &epi, cudaStream_t s,
                               int a0, int a1, const float *acc_in, float *acc_out) {
     const dim3 grid = backward_grid(g);
-    const T *yy = (const T *)y;
+    const float *yy = y;
     T *xx = (T *)x;
     switch (g.bwd_config) {
-    case 1: backward_kernel<T, ZF, 4, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 2: backward_kernel<T, ZF, 8, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 3: backward_kernel<T, ZF, 2, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 4: backward_kernel<T, ZF, 4, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 5: backward_kernel<T, ZF, 2, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    default: backward_kernel<T, ZF, 4, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 1: backward_kernel<T, ZF, 4, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 2: backward_kernel<T, ZF, 8, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 3: backward_kernel<T, ZF, 4, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 4: backward_kernel<T, ZF, 2, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 5: backward_kernel<T, ZF, 8, 16><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    default: backward_kernel<T, ZF, 8, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     }
 }
 
 template <bool ZF>
-static void launch_backward_z(const DevGeom &g, const void *y, void *x, cbct_dtype t, const Epilogue &epi,
+static void launch_backward_z(const DevGeom &g, const float *y, void *x, cbct_dtype t, const Epilogue &epi,
                               cudaStream_t s, int a0, int a1, const float *acc_in, float *acc_out) {
     switch (t) {
     case CBCT_F32: launch_backward_t<float, ZF>(g, y, x, epi, s, a0, a1, acc_in, acc_out); break;
@@ -172,7 +174,7 @@ int backward_passes(const DevGeom &g, const float *accum) {
 // One launch per block of angles (DevGeom::angle_block) when `accum` (M FP32
 // values) is given: each pass reads only its angles' projections, which then
 // stay in L2 while every voxel tile of the pass gathers from them.
-cbct_status launch_backward(const DevGeom &g, const void *y, void *x, cbct_dtype t, const Epilogue &epi,
+cbct_status launch_backward(const DevGeom &g, const float *y, void *x, cbct_dtype t, const Epilogue &epi,
                             cudaStream_t s, bool zfast, float *accum) {
     const int passes = backward_passes(g, accum);
     for (int p = 0; p < passes; ++p) {
@@ -218,6 +220,84 @@ cudaError_t launch_zbox(const DevGeom &g, float2 *zbox) {
     const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
     zbox_kernel<<<blocks, 256, 0, 0>>>(g, zbox);
     return cudaGetLastError();
+}
+
+// ------------------------------------------- ray-length weighted inputs
+// The transpose sums len * |d'| * y; its input w = |d'| * y (u-fastest) is
+// formed once per product (here, or in the forward epilogue).
+
+// v-fastest y[a][iu][iv] -> w[a][iv][iu], through a 32 x 32 shared-memory
+// tile so that reads and writes are both coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) weight_kernel(const T *__restrict__ y, const float *__restrict__ len,
+                                                     float *__restrict__ w, int nu, int nv) {
+    __shared__ float tile[32][33];
+    const size_t base = (size_t)blockIdx.z * nu * nv;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int v0 = blockIdx.x * 32, u0 = blockIdx.y * 32;
+    for (int r = ty; r < 32; r += 8) {
+        const int iu = u0 + r, iv = v0 + tx;
+        if (iu < nu && iv < nv) {
+            const size_t o = (size_t)iu * nv + iv;
+            tile[r][tx] = len[o] * Storage<T>::load(y + base + o);
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int iv = v0 + r, iu = u0 + tx;
+        if (iu < nu && iv < nv) w[base + (size_t)iv * nu + iu] = tile[tx][r];
+    }
+}
+
+cbct_status launch_weight(const DevGeom &g, const void *y, cbct_dtype t, float *w, cudaStream_t s) {
+    const dim3 grid((g.nv + 31) / 32, (g.nu + 31) / 32, g.nangles);
+    switch (t) {
+    case CBCT_F32: weight_kernel<float><<<grid, 256, 0, s>>>((const float *)y, g.ray_len, w, g.nu, g.nv); break;
+    case CBCT_F16: weight_kernel<__half><<<grid, 256, 0, s>>>((const __half *)y, g.ray_len, w, g.nu, g.nv); break;
+    case CBCT_BF16:
+        weight_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)y, g.ray_len, w, g.nu, g.nv);
+        break;
+    }
+    CBCT_CUDA_TRY(cudaGetLastError());
+    return CBCT_OK;
+}
+
+// ABI y[a][iv][iu] -> w[a][iv][iu] = |d'| * y (same layout; the length table
+// ray_len[iu][iv] is read through a transposed shared-memory tile).
+template <typename T>
+__global__ void __launch_bounds__(256) weight_abi_kernel(const T *__restrict__ y, const float *__restrict__ len,
+                                                         float *__restrict__ w, int nu, int nv) {
+    __shared__ float ltile[32][33];
+    const size_t base = (size_t)blockIdx.z * nu * nv;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int u0 = blockIdx.x * 32, v0 = blockIdx.y * 32;
+    for (int r = ty; r < 32; r += 8) {
+        const int iu = u0 + r, iv = v0 + tx;
+        if (iu < nu && iv < nv) ltile[r][tx] = len[(size_t)iu * nv + iv];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int iv = v0 + r, iu = u0 + tx;
+        if (iu < nu && iv < nv) {
+            const size_t o = base + (size_t)iv * nu + iu;
+            w[o] = ltile[tx][r] * Storage<T>::load(y + o);
+        }
+    }
+}
+
+cbct_status launch_weight_abi(const DevGeom &g, const void *y, cbct_dtype t, float *w, cudaStream_t s) {
+    const dim3 grid((g.nu + 31) / 32, (g.nv + 31) / 32, g.nangles);
+    switch (t) {
+    case CBCT_F32: weight_abi_kernel<float><<<grid, 256, 0, s>>>((const float *)y, g.ray_len, w, g.nu, g.nv); break;
+    case CBCT_F16:
+        weight_abi_kernel<__half><<<grid, 256, 0, s>>>((const __half *)y, g.ray_len, w, g.nu, g.nv);
+        break;
+    case CBCT_BF16:
+        weight_abi_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)y, g.ray_len, w, g.nu, g.nv);
+        break;
+    }
+    CBCT_CUDA_TRY(cudaGetLastError());
+    return CBCT_OK;
 }
 
 // -------------------------------------------------- projection re-layout
@@ -356,10 +436,10 @@ extern "C" cbct_status cbct_backproject(const cbct_geometry *g, const void *y, v
     cbct_status st = check_pair(g, y, x, t);
     if (st != CBCT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // the transpose reads projections v-fastest: re-lay the caller's stack first
-    void *tmp = nullptr;
+    // the transpose reads |d'| * y: weight the caller's stack first
+    float *tmp = nullptr;
     float *accum = nullptr;
-    CBCT_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)cbct_geometry_num_rays(g) * dtype_size(t), s));
+    CBCT_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)cbct_geometry_num_rays(g) * sizeof(float), s));
     cudaError_t err = cudaSuccess;
     if (g->dev.angle_block < g->dev.nangles)     // summed in passes over blocks of angles
         err = cudaMallocAsync(&accum, (size_t)cbct_geometry_num_voxels(g) * sizeof(float), s);
@@ -367,7 +447,7 @@ extern "C" cbct_status cbct_backproject(const cbct_geometry *g, const void *y, v
         cudaFreeAsync(tmp, s);
         return cuda_fail(err, "cbct_backproject");
     }
-    st = launch_proj_relayout(g->dev, y, tmp, t, true, s);
+    st = launch_weight_abi(g->dev, y, t, tmp, s);
     if (st == CBCT_OK) {
         Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
         st = launch_backward(g->dev, tmp, x, t, epi, s, false, accum);

@@ -2,21 +2,22 @@
 //
 // Requests (a scan, its measured projections b, LSQR or LSMR, an iteration
 // count, optional Tikhonov damping) are admitted into slots while the device
-// memory they need fits a budget.  Every step of the server advances every
-// active slot by one Krylov iteration with persistent multi-instance kernels:
-// one forward launch walks the forward tiles of all slots, one transpose
-// launch walks all their bricks, one launch per scalar step handles all slots
-// (one block each) and one launch updates all their vectors.  A slot finishes,
-// its result is copied out and its memory is freed while the others continue;
-// waiting requests are admitted between steps.  The launch topology of a step
-// does not depend on the mix (fixed persistent grids, a device slot table), so
-// one captured CUDA graph is replayed for every step.
+// memory they need fits a budget.  A step of the server advances a set of
+// slots by one Krylov iteration with persistent multi-instance kernels: one
+// forward launch walks the forward tiles of all slots in the step, one
+// transpose launch walks all their tiles, one launch per scalar step handles
+// all of them (one block each) and one launch updates all their vectors.  The
+// schedule picks the set: shortest remaining work first until the step's
+// forward tiles fill the GPU (SRPT, the default), or every slot (SHARE).  A
+// slot finishes, its result is copied out and its memory is freed while the
+// others continue; waiting requests are admitted between steps.  The launch
+// topology of a step does not depend on the set (fixed persistent grids, a
+// device slot table), so one captured CUDA graph is replayed for every step.
 //
-// Each slot computes exactly what the single-request solver computes: the same
-// tiles, the same per-tile partial sums in the same order, the same scalar
-// steps (gk.cuh).  Only the order of the shared-memory accumulation in the
-// transpose tiles can differ between runs, so a result is the same alone and
-// in a mix up to FP32 rounding.
+// Each slot computes what the single-request solver computes: the same tiles,
+// the same per-ray and per-voxel summation order, the same scalar steps
+// (gk.cuh); only the blockwise norm partials can be grouped differently when
+// the single-request solver runs other launch shapes.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -37,11 +38,13 @@ namespace cbct {
 
 constexpr int SRV_MAX_SLOTS = 64;
 constexpr int SRV_FWD_ROWS = 2;                       // forward tile: 2 rays per lane
-constexpr int SRV_CX = 4, SRV_BK = 1;                  // transpose tile: 4 x 2 columns, 1 voxel per lane (configuration 0)
+constexpr int64_t SRV_SAT_TILES = 4096;                // SRPT: forward tiles that fill a step (~5 waves)
+constexpr int SRV_CY = 8, SRV_BK = 8;                  // transpose tile: 32 x 8 columns x 8 slabs (configuration 2)
+constexpr int SRV_BWD_CONFIG = 2;
 
 struct SlotDev {
     DevGeom g;
-    float *U, *V, *w, *x, *h2;
+    float *U, *Uw, *V, *w, *x, *h2;     // Uw = |d'| U, the transpose's input
     GkState *st;
     double *pf, *pb, *hist_r, *hist_n;
     int method, cap;
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(FWD_THREADS) srv_forward(const SlotTable *tab)
         if (sd.st->stop) continue;
         const int local = item - tab->fwd_start[s];
         const int tx = local % sd.fgx, ty = (local / sd.fgx) % sd.fgy, a = local / (sd.fgx * sd.fgy);
-        const Epilogue epi{&sd.st->fa, &sd.st->fb, 0.0, 0.0, nullptr, nullptr, nullptr};
+        const Epilogue epi{&sd.st->fa, &sd.st->fb, 0.0, 0.0, nullptr, nullptr, nullptr, sd.Uw};
         forward_tile<float, false, SRV_FWD_ROWS, true>(sd.g, sd.V, sd.U, epi, tx, ty, a, sd.pf + local, red);
     }
 }
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(BWD_THREADS) srv_backward(const SlotTable *tab
         const int local = item - tab->bwd_start[s];
         const int tbx = local % sd.bgx, tby = (local / sd.bgx) % sd.bgy, tbz = local / (sd.bgx * sd.bgy);
         const Epilogue epi{&sd.st->ba, &sd.st->bb, 0.0, 0.0, nullptr, nullptr, nullptr};
-        backward_tile<float, true, SRV_CX, SRV_BK>(sd.g, sd.U, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
+        backward_tile<float, true, SRV_CY, SRV_BK>(sd.g, sd.Uw, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
                                                    nullptr, sd.pb + local, red);
     }
 }
@@ -181,19 +184,20 @@ struct Request {
 struct Slot {
     std::shared_ptr<Request> req;
     cbct_geometry *geom = nullptr;
-    float *U = nullptr, *V = nullptr, *w = nullptr, *x = nullptr, *h2 = nullptr, *b = nullptr;
+    float *U = nullptr, *Uw = nullptr, *V = nullptr, *w = nullptr, *x = nullptr, *h2 = nullptr, *b = nullptr;
     GkState *st = nullptr;
     double *pf = nullptr, *pb = nullptr, *hist = nullptr;
     int nf = 0, nb = 0, steps = 0;
+    double work_iter = 0.0;           // cost model of one iteration: rays x (nx + ny)
 };
 
 // Forward tiles and bricks of a scan under the server's launch shapes.
 void grids(const cbct_geometry_desc &d, int &fgx, int &fgy, int &bgx, int &bgy, int &bgz) {
     fgx = (d.nu + FWD_COLS - 1) / FWD_COLS;
     fgy = (d.nv + 32 * SRV_FWD_ROWS - 1) / (32 * SRV_FWD_ROWS);
-    bgx = (d.nx + SRV_CX - 1) / SRV_CX;
-    bgy = (d.ny + (8 / SRV_CX) - 1) / (8 / SRV_CX);
-    bgz = (d.nz + 32 * SRV_BK - 1) / (32 * SRV_BK);
+    bgx = (d.nx + 31) / 32;
+    bgy = (d.ny + SRV_CY - 1) / SRV_CY;
+    bgz = (d.nz + SRV_BK * (8 / SRV_CY) - 1) / (SRV_BK * (8 / SRV_CY));
 }
 
 // Device memory a request holds at its peak (ray tables, Krylov vectors,
@@ -205,7 +209,8 @@ size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
     grids(d, fgx, fgy, bgx, bgy, bgz);
     const size_t nf = (size_t)fgx * fgy * d.nangles, nb = (size_t)bgx * bgy * bgz;
     size_t t = al((size_t)d.nangles * d.nu * 24) + al((size_t)d.nv * 16) + al(n / d.nangles * 4) + al(d.nangles * 8);
-    t += 2 * al(n * 4);                                     // U and the staged b
+    t += al((size_t)d.nz * d.nv * 8);                       // z slab table
+    t += 3 * al(n * 4);                                     // U, |d'| U and the staged b
     t += al(m * 4) * (method == M_LSMR ? 4 : 3);            // V, w, x (+ hbar)
     t += al(nf * 8) + al(nb * 8) + al(sizeof(GkState)) + al((size_t)2 * iters * 8);
     t += al(m * 4);                                         // re-layout of x when the result is read out
@@ -216,7 +221,7 @@ size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
 
 struct ServerImpl {
     size_t budget = 0, in_use = 0;
-    int max_slots = 1, use_graph = 1, device = 0;
+    int max_slots = 1, use_graph = 1, device = 0, schedule = CBCT_SCHED_SRPT;
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -230,12 +235,14 @@ struct ServerImpl {
     SlotTable *tab_host = nullptr, *tab_dev = nullptr;
     SlotStatus *stat_host = nullptr, *stat_dev = nullptr;
     std::vector<Slot> slots;
+    std::vector<int> step_slots;      // slots advanced by the current step, in slot-table order
     bool table_dirty = true;
     cudaGraphExec_t step_graph = nullptr;
     int fwd_grid = 0, bwd_grid = 0, vec_grid = 0;
     int64_t steps_run = 0, graph_replays = 0;
 
     void run();
+    std::vector<int> pick_step_slots() const;
     cbct_status setup_slot(Slot &sl);
     void release_slot(Slot &sl);
     cbct_status finish_slot(Slot &sl);
@@ -251,15 +258,17 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     cbct_status st = cbct_geometry_create(&r.desc, &sl.geom);
     if (st != CBCT_OK) return st;
     sl.geom->dev.fwd_rows = SRV_FWD_ROWS;
-    sl.geom->dev.bwd_config = 0;
+    sl.geom->dev.bwd_config = SRV_BWD_CONFIG;
     const DevGeom &g = sl.geom->dev;
     const int64_t n = cbct_geometry_num_rays(sl.geom), m = cbct_geometry_num_voxels(sl.geom);
     sl.nf = forward_num_blocks(g);
     sl.nb = backward_num_blocks(g);
+    sl.work_iter = (double)n * (g.nx + g.ny);
     auto A = [&](auto **p, size_t cnt) {
         return cudaMallocAsync((void **)p, cnt * sizeof(**p) + 16, s);
     };
     cudaError_t e = A(&sl.U, (size_t)n);
+    if (e == cudaSuccess) e = A(&sl.Uw, (size_t)n);
     if (e == cudaSuccess) e = A(&sl.b, (size_t)n);
     if (e == cudaSuccess) e = A(&sl.V, (size_t)m);
     if (e == cudaSuccess) e = A(&sl.w, (size_t)m);
@@ -286,8 +295,10 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     st = launch_proj_relayout(g, sl.b, sl.U, CBCT_F32, true, s);
     if (st != CBCT_OK) return st;
     k_scale_inplace<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.U, n, &sl.st->c0, &sl.st->stop);
+    st = launch_weight(g, sl.U, CBCT_F32, sl.Uw, s);
+    if (st != CBCT_OK) return st;
     Epilogue eb{&sl.st->ba, &sl.st->bb, 0.0, 0.0, sl.pb, &sl.st->stop, nullptr};
-    st = launch_backward(g, sl.U, sl.V, CBCT_F32, eb, s, true, nullptr);
+    st = launch_backward(g, sl.Uw, sl.V, CBCT_F32, eb, s, true, nullptr);
     if (st != CBCT_OK) return st;
     gk_begin2<<<1, RED_THREADS, 0, s>>>(sl.st, sl.pb, sl.nb, r.method);
     k_start_dirs<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.V, sl.w, r.method == M_LSMR ? sl.h2 : nullptr, nullptr,
@@ -299,10 +310,10 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
 }
 
 void ServerImpl::release_slot(Slot &sl) {
-    for (void *p : {(void *)sl.U, (void *)sl.b, (void *)sl.V, (void *)sl.w, (void *)sl.x, (void *)sl.h2,
+    for (void *p : {(void *)sl.U, (void *)sl.Uw, (void *)sl.b, (void *)sl.V, (void *)sl.w, (void *)sl.x, (void *)sl.h2,
                     (void *)sl.pf, (void *)sl.pb, (void *)sl.st, (void *)sl.hist})
         if (p) cudaFreeAsync(p, s);
-    sl.U = sl.b = sl.V = sl.w = sl.x = sl.h2 = nullptr;
+    sl.U = sl.Uw = sl.b = sl.V = sl.w = sl.x = sl.h2 = nullptr;
     sl.pf = sl.pb = sl.hist = nullptr;
     sl.st = nullptr;
     if (sl.geom) {
@@ -382,6 +393,7 @@ cbct_status ServerImpl::enqueue_step() {
 void ServerImpl::fail_all(cbct_status st, const std::string &msg) {
     std::vector<Slot> dead;
     dead.swap(slots);
+    step_slots.clear();
     for (Slot &sl : dead) release_slot(sl);
     std::lock_guard<std::mutex> lk(mu);
     for (Slot &sl : dead) {
@@ -396,6 +408,32 @@ void ServerImpl::fail_all(cbct_status st, const std::string &msg) {
 }
 
 // ------------------------------------------------------------------ worker
+
+// SRPT: the slots with the least remaining work (iterations left x cost of
+// one), ties by request id, as long as the step's forward tiles stay within
+// SRV_SAT_TILES (the first slot always runs); SHARE: every slot.  Returned in
+// increasing slot index.
+std::vector<int> ServerImpl::pick_step_slots() const {
+    std::vector<int> all(slots.size());
+    for (size_t i = 0; i < slots.size(); ++i) all[i] = (int)i;
+    if (schedule == CBCT_SCHED_SHARE) return all;
+    auto remaining = [&](int i) { return (slots[i].req->iters - slots[i].steps) * slots[i].work_iter; };
+    std::sort(all.begin(), all.end(), [&](int a, int b) {
+        const double ra = remaining(a), rb = remaining(b);
+        return ra != rb ? ra < rb : slots[a].req->id < slots[b].req->id;
+    });
+    std::vector<int> pick;
+    int64_t tiles = 0;
+    for (int i : all) {
+        // a step's duration is its total work: never let a larger request join
+        // (and slow down) a step that smaller ones already fill
+        if (!pick.empty() && tiles + slots[i].nf > SRV_SAT_TILES) break;
+        pick.push_back(i);
+        tiles += slots[i].nf;
+    }
+    std::sort(pick.begin(), pick.end());
+    return pick;
+}
 
 void ServerImpl::run() {
     cudaSetDevice(device);
@@ -438,15 +476,22 @@ void ServerImpl::run() {
             table_dirty = true;
         }
         if (slots.empty()) continue;
+        {
+            std::vector<int> pick = pick_step_slots();
+            if (pick != step_slots) {
+                step_slots.swap(pick);
+                table_dirty = true;
+            }
+        }
         if (table_dirty) {
             SlotTable &t = *tab_host;
-            t.n = (int)slots.size();
+            t.n = (int)step_slots.size();
             t.fwd_start[0] = t.bwd_start[0] = 0;
             for (int i = 0; i < t.n; ++i) {
-                const Slot &sl = slots[i];
+                const Slot &sl = slots[step_slots[i]];
                 SlotDev &d = t.s[i];
                 d.g = sl.geom->dev;
-                d.U = sl.U; d.V = sl.V; d.w = sl.w; d.x = sl.x; d.h2 = sl.h2;
+                d.U = sl.U; d.Uw = sl.Uw; d.V = sl.V; d.w = sl.w; d.x = sl.x; d.h2 = sl.h2;
                 d.st = sl.st;
                 d.pf = sl.pf; d.pb = sl.pb;
                 d.hist_r = sl.hist; d.hist_n = sl.hist + sl.req->iters;
@@ -472,15 +517,20 @@ void ServerImpl::run() {
             continue;
         }
         ++steps_run;
-        for (int i = (int)slots.size() - 1; i >= 0; --i) {
+        // table entries are in increasing slot index: walk them backwards so that
+        // erasing a finished slot leaves the remaining indices valid
+        bool erased = false;
+        for (int ti = (int)step_slots.size() - 1; ti >= 0; --ti) {
+            const int i = step_slots[ti];
             Slot &sl = slots[i];
             ++sl.steps;
-            if (!stat_host[i].stop && sl.steps < sl.req->iters) continue;
+            if (!stat_host[ti].stop && sl.steps < sl.req->iters) continue;
             cbct_status fs = finish_slot(sl);
             const std::string msg = fs == CBCT_OK ? sl.req->error : std::string(cbct_last_error());
             std::shared_ptr<Request> r = sl.req;
             release_slot(sl);
             slots.erase(slots.begin() + i);
+            erased = true;
             table_dirty = true;
             std::lock_guard<std::mutex> lk(mu);
             if (fs != CBCT_OK) r->status = fs;
@@ -490,6 +540,7 @@ void ServerImpl::run() {
             in_use -= r->bytes;
             cv_done.notify_all();
         }
+        if (erased) step_slots.clear();     // slot indices shifted: the next step re-picks
     }
     for (Slot &sl : slots) release_slot(sl);
     slots.clear();
@@ -511,12 +562,17 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *o, cbct_server
         set_error("cbct_server_create: need hbm_budget_bytes > 0 and 1 <= max_slots <= 64");
         return CBCT_EINVAL;
     }
+    if (o->schedule != CBCT_SCHED_SRPT && o->schedule != CBCT_SCHED_SHARE) {
+        set_error("cbct_server_create: unknown schedule");
+        return CBCT_EINVAL;
+    }
     cbct_server *srv = new (std::nothrow) cbct_server();
     if (!srv) { set_error("cbct_server_create: out of host memory"); return CBCT_ENOMEM; }
     ServerImpl &S = srv->impl;
     S.budget = o->hbm_budget_bytes;
     S.max_slots = o->max_slots;
     S.use_graph = o->use_graph != 0;
+    S.schedule = o->schedule;
     S.t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaGetDevice(&S.device);
     int sms = 0, occ_f = 0, occ_b = 0;

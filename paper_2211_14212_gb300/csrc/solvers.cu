@@ -24,8 +24,8 @@ namespace cbct {
 
 cbct_status launch_projected_solve(const double *alphas, const double *betas, const double *scales,
                                    const int *iter, const int *stop, int rule, double lambda_fixed,
-                                   double *work, int kmax, double *coef, double *hist_lambda,
-                                   double *hist_resid, cudaStream_t s);
+                                   double noise_level, double *work, int kmax, double *coef,
+                                   double *hist_lambda, double *hist_resid, cudaStream_t s);
 
 // ===================================================================== CGLS
 //
@@ -243,11 +243,12 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     if (st != CBCT_OK) return st;
 
     T *U = nullptr, *V = nullptr, *basis = nullptr;
-    float *w = nullptr, *h2 = nullptr;
+    float *w = nullptr, *h2 = nullptr, *W = nullptr;
     double *pf = nullptr, *pb = nullptr, *pv = nullptr, *hist = nullptr;
     double *alpha_arr = nullptr, *beta_arr = nullptr, *scale_arr = nullptr, *coef = nullptr, *work = nullptr;
     GkState *dst = nullptr;
     CBCT_CUDA_TRY(ws.alloc(&U, (size_t)n));
+    CBCT_CUDA_TRY(ws.alloc(&W, (size_t)n));          // |d'| U, the transpose's input
     if (method == M_HYBRID) {
         CBCT_CUDA_TRY(ws.alloc(&basis, (size_t)m * (iters + 1)));
         CBCT_CUDA_TRY(ws.alloc(&alpha_arr, (size_t)iters + 2));
@@ -292,7 +293,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
         ++tr.fwd;
         return r;
     };
-    auto bwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
+    auto bwd = [&](const float *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(1);
         if (r == CBCT_OK) r = launch_backward(g, in, out, t, e, s, true, accum);
         if (r == CBCT_OK) r = tr.mark(1);
@@ -305,8 +306,10 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, n, pv);
     gk_begin<<<1, RED_THREADS, 0, s>>>(dst, pv, VEC_BLOCKS);
     k_scale_to<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, U, n, &dst->c0, stop);
-    tr.launches += 3;
+    tr.launches += 4;
     CBCT_CUDA_TRY(cudaGetLastError());
+    st = launch_weight(g, U, t, W, s);
+    if (st != CBCT_OK) return st;
     if (method == M_HYBRID) {
         double one = 1.0;
         CBCT_CUDA_TRY(cudaMemcpyAsync(scale_arr, &one, sizeof one, cudaMemcpyHostToDevice, s));
@@ -314,7 +317,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     // alpha_1 v_1 = A^T u_1
     {
         Epilogue e{&dst->ba, &dst->bb, 0, 0, pb, stop, nullptr};
-        st = bwd(U, V, e);
+        st = bwd(W, V, e);
         if (st != CBCT_OK) return st;
     }
     gk_begin2<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method);
@@ -336,12 +339,12 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     auto one_iteration = [&]() -> cbct_status {
         T *Vin = method == M_HYBRID ? basis + (size_t)k * m : V;
         T *Vout = method == M_HYBRID ? basis + (size_t)(k + 1) * m : V;
-        Epilogue ef{&dst->fa, &dst->fb, 0, 0, pf, stop, nullptr};
+        Epilogue ef{&dst->fa, &dst->fb, 0, 0, pf, stop, nullptr, W};
         cbct_status r = fwd(Vin, U, ef);
         if (r != CBCT_OK) return r;
         gk_after_forward<<<1, RED_THREADS, 0, s>>>(dst, pf, nf, beta_arr);
         Epilogue eb{&dst->ba, &dst->bb, 0, 0, pb, stop, method == M_HYBRID ? (const void *)Vin : nullptr};
-        r = bwd(U, Vout, eb);
+        r = bwd(W, Vout, eb);
         if (r != CBCT_OK) return r;
         gk_after_backward<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method, hist_r, hist_n, alpha_arr,
                                                      scale_arr, iters);
@@ -352,7 +355,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
             k_lsmr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.xz, w, h2, m, dst);
         } else {
             r = launch_projected_solve(alpha_arr, beta_arr, scale_arr, &dst->iter, stop, (int)o->rule, o->lambda,
-                                       work, iters, coef, hist_l, hist_r, s);
+                                       o->noise_level, work, iters, coef, hist_l, hist_r, s);
             if (r != CBCT_OK) return r;
         }
         CBCT_CUDA_TRY(cudaGetLastError());
@@ -403,11 +406,12 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     SolveIO io;
     cbct_status st = setup_io(geom, b, x, ws, io);
     if (st != CBCT_OK) return st;
-    float *r = nullptr, *q = nullptr, *sv = nullptr, *p = nullptr;
+    float *r = nullptr, *q = nullptr, *sv = nullptr, *p = nullptr, *wr = nullptr;
     double *pq = nullptr, *pp = nullptr, *pr = nullptr, *ps = nullptr, *hist = nullptr;
     CgState *dst = nullptr;
     CBCT_CUDA_TRY(ws.alloc(&r, (size_t)n));
     CBCT_CUDA_TRY(ws.alloc(&q, (size_t)n));
+    CBCT_CUDA_TRY(ws.alloc(&wr, (size_t)n));
     CBCT_CUDA_TRY(ws.alloc(&sv, (size_t)m));
     CBCT_CUDA_TRY(ws.alloc(&p, (size_t)m));
     CBCT_CUDA_TRY(ws.alloc(&pq, (size_t)nf));
@@ -431,7 +435,7 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
         ++tr.fwd;
         return r;
     };
-    auto bwd = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
+    auto bwd = [&](const float *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(1);
         if (r == CBCT_OK) r = launch_backward(g, in, out, CBCT_F32, e, s, true, accum);
         if (r == CBCT_OK) r = tr.mark(1);
@@ -446,10 +450,12 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
 
     // r = b; s = A^T r; gamma = ||s||^2; p = s
     k_copy_sumsq<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, r, nullptr, n, nullptr, nullptr);
-    ++tr.launches;
+    st = launch_weight(g, r, CBCT_F32, wr, s);
+    if (st != CBCT_OK) return st;
+    tr.launches += 2;
     {
         Epilogue e{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
-        st = bwd(r, sv, e);
+        st = bwd(wr, sv, e);
         if (st != CBCT_OK) return st;
     }
     k_copy_sumsq<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sv, p, nullptr, m, pp, nullptr);
@@ -464,13 +470,15 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
         if (rr != CBCT_OK) return rr;
         cg_after_forward<<<1, RED_THREADS, 0, s>>>(dst, pq, nf, pp, VEC_BLOCKS);
         k_cg_r<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(r, q, n, pr, dst);
+        rr = launch_weight(g, r, CBCT_F32, wr, s);        // the transpose's input |d'| r
+        if (rr != CBCT_OK) return rr;
         Epilogue eb{nullptr, nullptr, 1.0, 0.0, nullptr, stop, nullptr};
-        rr = bwd(r, sv, eb);
+        rr = bwd(wr, sv, eb);
         if (rr != CBCT_OK) return rr;
         k_cg_xs<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.xz, sv, p, m, ps, dst);
         cg_after_backward<<<1, RED_THREADS, 0, s>>>(dst, ps, VEC_BLOCKS, pr, VEC_BLOCKS, hist_r, hist_n, iters);
         k_cg_p<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(p, sv, m, pp, dst);
-        tr.launches += 5;
+        tr.launches += 6;
         CBCT_CUDA_TRY(cudaGetLastError());
         return CBCT_OK;
     };
@@ -497,8 +505,13 @@ static cbct_status dispatch_gk(const cbct_geometry *g, const float *b, float *x,
                                cbct_solve_report *rep, cbct_stream stream, Method method) {
     cbct_status st = check_solve_args(g, b, x, o);
     if (st != CBCT_OK) return st;
-    if (method == M_HYBRID && o->rule != CBCT_LAMBDA_FIXED && o->rule != CBCT_LAMBDA_GCV) {
+    if (method == M_HYBRID && o->rule != CBCT_LAMBDA_FIXED && o->rule != CBCT_LAMBDA_GCV &&
+        o->rule != CBCT_LAMBDA_DP) {
         set_error("hybrid LSQR: unknown lambda rule");
+        return CBCT_EINVAL;
+    }
+    if (method == M_HYBRID && o->rule == CBCT_LAMBDA_DP && !(o->noise_level >= 0.0 && o->noise_level < 1.0)) {
+        set_error("hybrid LSQR: the discrepancy principle needs 0 <= noise_level < 1");
         return CBCT_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;

@@ -125,3 +125,29 @@ def test_many_requests_continuous(cbct):
         st = srv.stats()
     assert all(np.isfinite(r.x).all() and r.x.shape == s for r, s in zip(res, shapes))
     assert st["bytes_in_use"] == 0 and st["active"] == 0 and st["pending"] == 0
+
+
+@pytest.mark.parametrize("schedule", ["srpt", "share"])
+def test_schedule(cbct, schedule):
+    """A large request (more forward tiles than one step needs to fill the GPU)
+    and a short one submitted right after it: SRPT runs the short one alone,
+    so the steps add up; SHARE advances both in the same steps."""
+    big = synth.Geometry(128, 128, 128, 2.0, 2.0, 2.0, 256, 256, 1.6, 1.6, 1000.0, 1536.0,
+                         synth.circular_angles(180))
+    small = synth.config("c1")
+    rng = np.random.default_rng(4)
+    b_big = np.abs(rng.standard_normal(big.num_rays)).astype(np.float32)
+    b_small = np.abs(rng.standard_normal(small.num_rays)).astype(np.float32)
+    with cbct.Server(8 << 30, max_slots=4, schedule=schedule) as srv:
+        i_big = srv.submit(big, b_big, "lsqr", 30)
+        i_small = srv.submit(small, b_small, "lsqr", 4)
+        r_big, r_small = srv.wait(i_big, timeout=300), srv.wait(i_small, timeout=300)
+        st = srv.stats()
+    assert r_big.report.iters_done == 30 and r_small.report.iters_done == 4
+    if schedule == "srpt":
+        assert st["steps"] == 34
+        assert r_small.finish_s <= r_big.finish_s
+    else:
+        assert st["steps"] < 34
+    alone, _ = cbct.lsqr(cbct.Geometry(small), b_small, 4)
+    assert rel(r_small.x, alone) <= MIX_TOL

@@ -208,6 +208,28 @@ def test_hybrid_lsqr(cbct, medium_problem, rule, lam):
     assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
 
 
+def test_hybrid_lsqr_discrepancy_principle(cbct, medium_problem):
+    """DP (Sec. 2.2.2) with twice the true relative noise level ||b - b_clean|| /
+    ||b|| (0.0053 here; LSQR's residual reaches 2 nl at k = 16 of 20): lambda_k
+    and iterates as the oracle's, lambda_k = 0 until the projected problem can
+    reach the discrepancy."""
+    g, x_true, b = medium_problem
+    b_clean = oracle.project(g, x_true.astype(np.float64)).ravel()
+    nl = 2.0 * float(np.linalg.norm(b - b_clean) / np.linalg.norm(b))
+    geom = cbct.Geometry(g)
+    k = 20
+    x, rep = cbct.hybrid_lsqr(geom, dev(b), k, rule="dp", noise_level=nl)
+    x_ref, h = oracle_solve(g, b, "hybrid_lsqr", k, rule="dp", noise_level=nl)
+    assert rep.iters_done == k
+    lam_ref = np.asarray(h["lambda"])
+    zero = lam_ref == 0.0
+    assert np.all(rep.lam[zero] == 0.0)
+    assert zero.any() and (~zero).any()
+    np.testing.assert_allclose(rep.lam[~zero], lam_ref[~zero], rtol=1e-3)
+    np.testing.assert_allclose(rep.resid, h["resid"], rtol=1e-4)
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+
+
 def test_hybrid_fixed_equals_damped_lsqr_on_gpu(cbct, c1_problem):
     g, _, b = c1_problem
     geom = cbct.Geometry(g)

@@ -178,3 +178,62 @@ def test_hybrid_gcv_runs_and_lambda_positive(tiny_system):
     assert all(l > 0 for l in h["lambda"])
     # projected residual equals the explicit one (A V_k = U_{k+1} H_k)
     assert abs(h["resid"][-1] - np.linalg.norm(b - a @ x)) <= 1e-8 * np.linalg.norm(b)
+
+
+# ------------------------------------------------- discrepancy principle (Sec. 2.2.2)
+def test_dp_residual_meets_noise_level_explicitly(tiny_system):
+    """Where the projected problem can reach it, the DP lam_k makes the explicit
+    residual ||b - A x_k|| (dense product, not the projected formula) equal
+    nl ||b||; before that (residual of the unregularised iterate still above
+    the target) lam_k = 0 and x_k is the LSQR iterate."""
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    nb = np.linalg.norm(b)
+    _, h_lsqr = krylov.lsqr(op, b, 12, keep_iterates=True)
+    nl = 0.999 * h_lsqr["resid"][5] / nb            # reachable once r_k of LSQR drops below r_6
+    _, h = krylov.hybrid_lsqr(op, b, 12, rule="dp", noise_level=nl, keep_iterates=True)
+    reached = 0
+    for k in range(1, 13):
+        xk = h["iterates"][k - 1]
+        explicit = np.linalg.norm(b - a @ xk)
+        if h["lambda"][k - 1] == 0.0:
+            assert rel(xk, h_lsqr["iterates"][k - 1]) <= 1e-8
+            assert explicit >= nl * nb * (1 - 1e-9)
+        else:
+            reached += 1
+            assert abs(explicit - nl * nb) <= 1e-8 * nb
+    assert reached >= 3
+
+
+def test_dp_lambda_grows_with_noise_level(tiny_system):
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    nb = np.linalg.norm(b)
+    _, h_lsqr = krylov.lsqr(op, b, 10)
+    lams = []
+    for f in (0.1, 0.3, 0.6, 0.9):
+        nl = h_lsqr["resid"][-1] / nb + f * (1 - h_lsqr["resid"][-1] / nb)
+        _, h = krylov.hybrid_lsqr(op, b, 10, rule="dp", noise_level=nl)
+        lams.append(h["lambda"][-1])
+    assert all(l1 < l2 for l1, l2 in zip(lams, lams[1:]))
+    assert lams[0] > 0
+
+
+def test_dp_bisection_brackets_the_root():
+    """dp_lambda against a brute-force scan of the projected residual on a
+    random bidiagonal H (the root lies between neighbouring scan points)."""
+    rng = np.random.default_rng(31)
+    k = 8
+    h = np.zeros((k + 1, k))
+    for i in range(k):
+        h[i, i] = rng.uniform(0.05, 2)
+        h[i + 1, i] = rng.uniform(0.05, 1)
+    beta1 = 1.7
+    p, sigma, _ = np.linalg.svd(h, full_matrices=True)
+    r0 = krylov.projected_residual(sigma, p[0], beta1, 0.0)
+    target = 0.5 * (r0 + beta1)
+    lam = krylov.dp_lambda(sigma, p[0], beta1, target)
+    # independent check of the residual at lam: solve the regularised problem directly
+    y = np.linalg.solve(h.T @ h + lam * lam * np.eye(k), h.T @ (beta1 * np.eye(k + 1)[0]))
+    assert abs(np.linalg.norm(beta1 * np.eye(k + 1)[0] - h @ y) - target) <= 1e-8 * beta1
+    assert krylov.dp_lambda(sigma, p[0], beta1, 0.5 * r0) == 0.0
