@@ -122,11 +122,11 @@ cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream 
 /* Launch shapes of the projectors of one geometry (performance only: every
  * shape computes the same A and A^T).  fwd_rows: rays per lane of the forward
  * tile (1, 2 or 4; a warp follows 32 * fwd_rows rows of one detector column).
- * bwd_config: tile of the transpose (one lane per voxel column, 32 columns
- * along x per warp), as (columns along x) x (rows along y) x (slabs along z):
- * 0 = 32 x 8 x 4 (4 slabs per lane), 1 = 32 x 4 x 8 (4), 2 = 32 x 8 x 8 (8),
- * 3 = 32 x 4 x 16 (8), 4 = 32 x 2 x 32 (8), 5 = 32 x 8 x 16 (16).  Changing
- * the shape while another thread uses the geometry is a data race. */
+ * bwd_config: tile of the transpose (one warp per voxel column), 0 = 4 x 2
+ * columns x 32 voxels along z (1 per lane), 1 = 4 x 2 x 64 (2 per lane),
+ * 2 = 8 x 1 x 32, 3 = 2 x 4 x 64, 4 = 4 x 2 x 128 (4 per lane),
+ * 5 = 2 x 4 x 128.  Changing the shape while another thread uses the
+ * geometry is a data race. */
 #define CBCT_TUNE_TIMES 9
 cbct_status cbct_geometry_set_launch(cbct_geometry *geom, int fwd_rows, int bwd_config);
 cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, int *bwd_config);

@@ -264,8 +264,8 @@ def count_nnz(geom: Geometry, stream=None) -> int:
 
 TUNE_TIMES = 9
 FWD_ROWS = (1, 2, 4)
-BWD_CONFIGS = ("32x8 columns x 4", "32x4 columns x 8", "32x8 columns x 8", "32x4 columns x 16",
-               "32x2 columns x 32", "32x8 columns x 16")
+BWD_CONFIGS = ("4x2 columns x 32", "4x2 columns x 64", "8x1 columns x 32", "2x4 columns x 64",
+               "4x2 columns x 128", "2x4 columns x 128")
 
 
 def set_launch(geom: Geometry, fwd_rows: int, bwd_config: int):

@@ -51,8 +51,8 @@ struct DevGeom {
     int angle_block;         // transpose: angles per pass when summed in passes (launch_backward)
 };
 
-// Tile of the transpose: bx (= 32, one per lane) x by voxel columns, bz slabs
-// along z in blocks of r (one block per warp row).
+// Tile of the transpose: a bx x by patch of voxel columns (one warp each),
+// bz = 32 r voxels along z (r per lane).
 struct BrickShape {
     int bx, by, bz, r;
 };
@@ -108,8 +108,8 @@ struct Epilogue {
     double *partial;
     const int *stop;         // when non-null and *stop != 0, the launch does nothing
     const void *old;         // where out_old is read (same storage type); null = the output itself
-    float *weighted;         // forward only: when non-null, also receives |d'| * (stored output),
-                             // u-fastest w[a][iv][iu], the transpose's input (launch_backward)
+    float *weighted;         // forward, v-fastest output only: when non-null, also receives
+                             // |d'| * (stored output), the transpose's input (launch_backward)
 };
 
 __device__ __forceinline__ double epi_a(const Epilogue &e) { return e.a_ptr ? *e.a_ptr : e.a_val; }
@@ -150,15 +150,15 @@ cbct_status launch_forward(const DevGeom &g, const void *x_zfast, void *y, cbct_
 // launch_forward writes either projection layout, launch_backward either
 // volume layout.
 // The transpose reads its projections pre-weighted by the ray lengths |d'|,
-// FP32, u-fastest: w[a][iv][iu] = |d'| * y (what the forward epilogue writes
+// FP32, v-fastest: w[a][iu][iv] = |d'| * y (what the forward epilogue writes
 // to Epilogue::weighted, or launch_weight / launch_weight_abi make).
 // `accum` (optional, M FP32 values of scratch) lets the transpose run in passes
 // over blocks of DevGeom::angle_block angles; null means one pass.
-cbct_status launch_backward(const DevGeom &g, const float *w_ufast, void *x, cbct_dtype t,
+cbct_status launch_backward(const DevGeom &g, const float *w_vfast, void *x, cbct_dtype t,
                             const Epilogue &epi, cudaStream_t s, bool zfast, float *accum);
-// w[a][iv][iu] = |d'| * y for a v-fastest projection vector y[a][iu][iv] of type t.
+// w[a][iu][iv] = |d'| * y for a v-fastest projection vector y[a][iu][iv] of type t.
 cbct_status launch_weight(const DevGeom &g, const void *y_vfast, cbct_dtype t, float *w, cudaStream_t s);
-// w[a][iv][iu] = |d'| * y for y in the ABI layout y[a][iv][iu].
+// w[a][iu][iv] = |d'| * y for y in the ABI layout y[a][iv][iu].
 cbct_status launch_weight_abi(const DevGeom &g, const void *y_abi, cbct_dtype t, float *w, cudaStream_t s);
 int backward_passes(const DevGeom &g, const float *accum);
 int default_angle_block(const DevGeom &g);

@@ -179,7 +179,7 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
         return cuda_fail(err, "cbct_geometry_create");
     }
     dg.fwd_rows = 2;
-    dg.bwd_config = nz >= 8 ? 2 : 0;        // 8 slabs per lane once the volume is deep enough
+    dg.bwd_config = nz >= 128 ? 5 : nz >= 64 ? 3 : 0;   // 4 / 2 / 1 voxels per lane by column depth
     dg.angle_block = default_angle_block(dg);
     *out = g;
     return CBCT_OK;

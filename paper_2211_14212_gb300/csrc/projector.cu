@@ -18,7 +18,7 @@ namespace cbct {
 // ------------------------------------------------------------- forward A x
 
 template <typename T, bool COMP, int R, bool VF>
-__global__ void __launch_bounds__(FWD_THREADS)
+__global__ void __launch_bounds__(FWD_THREADS, 4)
 forward_kernel(DevGeom g, const T *__restrict__ vol, T *__restrict__ proj, Epilogue epi) {
     __shared__ double red[FWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
@@ -106,27 +106,26 @@ cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaSt
 
 // ---------------------------------------------------------- transpose A^T y
 
-template <typename T, bool ZFAST, int CY, int K>
-__global__ void __launch_bounds__(BWD_THREADS, K >= 8 ? 3 : 4)
+template <typename T, bool ZFAST, int CX, int K>
+__global__ void __launch_bounds__(BWD_THREADS, 4)
 backward_kernel(DevGeom g, const float *__restrict__ proj, T *__restrict__ vol, Epilogue epi, int a_begin, int a_end,
                 const float *acc_in, float *acc_out) {
     __shared__ double red[BWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    backward_tile<T, ZFAST, CY, K>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z, a_begin, a_end, acc_in,
+    backward_tile<T, ZFAST, CX, K>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z, a_begin, a_end, acc_in,
                                    acc_out, epi.partial ? epi.partial + b : nullptr, red);
 }
 
-// Transpose tile shapes: 32 voxel columns along x (one per lane) x CY rows j,
-// (8 / CY) blocks of K slabs along z.
+// Transpose tile shapes: column patch CX x (8 / CX), 32 K voxels along z.
 BrickShape backward_shape(int config) {
     switch (config) {
-    case 1: return BrickShape{32, 4, 8, 4};
-    case 2: return BrickShape{32, 8, 8, 8};
-    case 3: return BrickShape{32, 4, 16, 8};
-    case 4: return BrickShape{32, 2, 32, 8};
-    case 5: return BrickShape{32, 8, 16, 16};
-    default: return BrickShape{32, 8, 4, 4};
+    case 1: return BrickShape{4, 2, 64, 2};
+    case 2: return BrickShape{8, 1, 32, 1};
+    case 3: return BrickShape{2, 4, 64, 2};
+    case 4: return BrickShape{4, 2, 128, 4};
+    case 5: return BrickShape{2, 4, 128, 4};
+    default: return BrickShape{4, 2, 32, 1};
     }
 }
 
@@ -147,12 +146,12 @@ static void launch_backward_t(const DevGeom &g, const float *y, void *x, const E
     const float *yy = y;
     T *xx = (T *)x;
     switch (g.bwd_config) {
-    case 1: backward_kernel<T, ZF, 4, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 2: backward_kernel<T, ZF, 8, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 3: backward_kernel<T, ZF, 4, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 4: backward_kernel<T, ZF, 2, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 5: backward_kernel<T, ZF, 8, 16><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    default: backward_kernel<T, ZF, 8, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 1: backward_kernel<T, ZF, 4, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 2: backward_kernel<T, ZF, 8, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 3: backward_kernel<T, ZF, 2, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 4: backward_kernel<T, ZF, 4, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 5: backward_kernel<T, ZF, 2, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    default: backward_kernel<T, ZF, 4, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     }
 }
 
@@ -223,64 +222,54 @@ cudaError_t launch_zbox(const DevGeom &g, float2 *zbox) {
 }
 
 // ------------------------------------------- ray-length weighted inputs
-// The transpose sums len * |d'| * y; its input w = |d'| * y (u-fastest) is
+// The transpose sums len * |d'| * y; its input w = |d'| * y (v-fastest) is
 // formed once per product (here, or in the forward epilogue).
 
-// v-fastest y[a][iu][iv] -> w[a][iv][iu], through a 32 x 32 shared-memory
-// tile so that reads and writes are both coalesced.
+// v-fastest y[a][iu][iv] -> w[a][iu][iv]: one thread per detector pixel,
+// looping over the angles (the length is loaded once).
 template <typename T>
 __global__ void __launch_bounds__(256) weight_kernel(const T *__restrict__ y, const float *__restrict__ len,
-                                                     float *__restrict__ w, int nu, int nv) {
-    __shared__ float tile[32][33];
-    const size_t base = (size_t)blockIdx.z * nu * nv;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int v0 = blockIdx.x * 32, u0 = blockIdx.y * 32;
-    for (int r = ty; r < 32; r += 8) {
-        const int iu = u0 + r, iv = v0 + tx;
-        if (iu < nu && iv < nv) {
-            const size_t o = (size_t)iu * nv + iv;
-            tile[r][tx] = len[o] * Storage<T>::load(y + base + o);
-        }
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int iv = v0 + r, iu = u0 + tx;
-        if (iu < nu && iv < nv) w[base + (size_t)iv * nu + iu] = tile[tx][r];
+                                                     float *__restrict__ w, size_t nuv, int nangles) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nuv; i += (size_t)gridDim.x * blockDim.x) {
+        const float l = len[i];
+        for (int a = 0; a < nangles; ++a) w[(size_t)a * nuv + i] = l * Storage<T>::load(y + (size_t)a * nuv + i);
     }
 }
 
 cbct_status launch_weight(const DevGeom &g, const void *y, cbct_dtype t, float *w, cudaStream_t s) {
-    const dim3 grid((g.nv + 31) / 32, (g.nu + 31) / 32, g.nangles);
+    const size_t nuv = (size_t)g.nu * g.nv;
+    const int blocks = (int)std::min<size_t>((nuv + 255) / 256, 4096);
+    const int na = g.nangles;
     switch (t) {
-    case CBCT_F32: weight_kernel<float><<<grid, 256, 0, s>>>((const float *)y, g.ray_len, w, g.nu, g.nv); break;
-    case CBCT_F16: weight_kernel<__half><<<grid, 256, 0, s>>>((const __half *)y, g.ray_len, w, g.nu, g.nv); break;
+    case CBCT_F32: weight_kernel<float><<<blocks, 256, 0, s>>>((const float *)y, g.ray_len, w, nuv, na); break;
+    case CBCT_F16: weight_kernel<__half><<<blocks, 256, 0, s>>>((const __half *)y, g.ray_len, w, nuv, na); break;
     case CBCT_BF16:
-        weight_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)y, g.ray_len, w, g.nu, g.nv);
+        weight_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16 *)y, g.ray_len, w, nuv, na);
         break;
     }
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }
 
-// ABI y[a][iv][iu] -> w[a][iv][iu] = |d'| * y (same layout; the length table
-// ray_len[iu][iv] is read through a transposed shared-memory tile).
+// ABI y[a][iv][iu] (type T) -> w[a][iu][iv] = |d'| * y (FP32), through a
+// 32 x 32 shared-memory tile so that both sides are coalesced.
 template <typename T>
-__global__ void __launch_bounds__(256) weight_abi_kernel(const T *__restrict__ y, const float *__restrict__ len,
-                                                         float *__restrict__ w, int nu, int nv) {
-    __shared__ float ltile[32][33];
+__global__ void __launch_bounds__(256) weighted_relayout_kernel(const T *__restrict__ src, const float *__restrict__ len,
+                                                                float *__restrict__ dst, int nu, int nv) {
+    __shared__ float tile[32][33];
     const size_t base = (size_t)blockIdx.z * nu * nv;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int u0 = blockIdx.x * 32, v0 = blockIdx.y * 32;
     for (int r = ty; r < 32; r += 8) {
-        const int iu = u0 + r, iv = v0 + tx;
-        if (iu < nu && iv < nv) ltile[r][tx] = len[(size_t)iu * nv + iv];
+        const int iv = v0 + r, iu = u0 + tx;
+        if (iv < nv && iu < nu) tile[r][tx] = Storage<T>::load(src + base + (size_t)iv * nu + iu);
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
-        const int iv = v0 + r, iu = u0 + tx;
+        const int iu = u0 + r, iv = v0 + tx;
         if (iu < nu && iv < nv) {
-            const size_t o = base + (size_t)iv * nu + iu;
-            w[o] = ltile[tx][r] * Storage<T>::load(y + o);
+            const size_t o = (size_t)iu * nv + iv;
+            dst[base + o] = len[o] * tile[tx][r];
         }
     }
 }
@@ -288,12 +277,15 @@ __global__ void __launch_bounds__(256) weight_abi_kernel(const T *__restrict__ y
 cbct_status launch_weight_abi(const DevGeom &g, const void *y, cbct_dtype t, float *w, cudaStream_t s) {
     const dim3 grid((g.nu + 31) / 32, (g.nv + 31) / 32, g.nangles);
     switch (t) {
-    case CBCT_F32: weight_abi_kernel<float><<<grid, 256, 0, s>>>((const float *)y, g.ray_len, w, g.nu, g.nv); break;
+    case CBCT_F32:
+        weighted_relayout_kernel<float><<<grid, 256, 0, s>>>((const float *)y, g.ray_len, w, g.nu, g.nv);
+        break;
     case CBCT_F16:
-        weight_abi_kernel<__half><<<grid, 256, 0, s>>>((const __half *)y, g.ray_len, w, g.nu, g.nv);
+        weighted_relayout_kernel<__half><<<grid, 256, 0, s>>>((const __half *)y, g.ray_len, w, g.nu, g.nv);
         break;
     case CBCT_BF16:
-        weight_abi_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)y, g.ray_len, w, g.nu, g.nv);
+        weighted_relayout_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)y, g.ray_len, w, g.nu,
+                                                                      g.nv);
         break;
     }
     CBCT_CUDA_TRY(cudaGetLastError());
@@ -436,7 +428,7 @@ extern "C" cbct_status cbct_backproject(const cbct_geometry *g, const void *y, v
     cbct_status st = check_pair(g, y, x, t);
     if (st != CBCT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // the transpose reads |d'| * y: weight the caller's stack first
+    // the transpose reads |d'| * y, v-fastest: re-lay and weight the caller's stack first
     float *tmp = nullptr;
     float *accum = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)cbct_geometry_num_rays(g) * sizeof(float), s));

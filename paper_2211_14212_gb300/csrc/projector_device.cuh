@@ -262,8 +262,6 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
     }
     double sq = 0.0;
     const double acoef = epi_a(epi), bcoef = epi_b(epi);
-    // |d'| * stored for the transpose, staged so that it is written u-fastest
-    __shared__ float wtile[32 * 4][FWD_COLS + 1];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int iv = iv0 + r * 32 + lane;
@@ -278,19 +276,9 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
             }
             const float stored = Storage<T>::round((float)out);
             Storage<T>::store(proj + ray, stored);
-            if (epi.weighted) wtile[r * 32 + lane][warp] = len * stored;
+            if (VFAST && epi.weighted) epi.weighted[ray] = len * stored;
             sq += (double)stored * (double)stored;
         }
-    }
-    if (epi.weighted) {                 // uniform across the block
-        __syncthreads();
-        // w[a][iv][iu]: FWD_COLS consecutive iu of one row per group of threads
-        for (int t = threadIdx.x; t < 32 * R * FWD_COLS; t += FWD_THREADS) {
-            const int row = t / FWD_COLS, col = t % FWD_COLS;
-            const int iv = iv0 + row, iuw = tx * FWD_COLS + col;
-            if (iv < g.nv && iuw < g.nu) epi.weighted[((size_t)a * g.nv + iv) * g.nu + iuw] = wtile[row][col];
-        }
-        __syncthreads();                // wtile is reused by the next tile of a persistent kernel
     }
     if (partial) {
         const double s = block_sum<FWD_THREADS>(sq, red);
@@ -300,27 +288,24 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
 
 // ---------------------------------------------------------- transpose A^T y
 //
-// Gather form: each lane owns voxels (i, j, k) and sums len * w over every ray
-// that meets them, in registers, angle by angle; the volume is written once
-// (fused epilogue), so there are no atomics and the result does not depend on
-// scheduling.  Lanes take 32 consecutive voxel columns i of one row j and K
-// consecutive slabs k0..k0+K-1 (the same k in every lane); a tile is 8 warps
-// covering CY rows j x (8 / CY) blocks of K slabs.  For every angle a lane
-// finds the detector columns iu whose xy projection crosses its cell (i, j)
-// (the cell's four corners), and for each of them the alpha interval
-// [ain, aout] of that crossing (its x and y plane crossings).  It then inverts
-// z(alpha) = v (dso/dsd + alpha) over [ain, aout] to get the detector rows
-// that can meet slab k, and takes for each the segment
+// Gather form: each lane owns voxels (i, j, k) of one voxel column and sums
+// len * w over every ray that meets them, in registers, angle by angle;
+// the volume is written once (fused epilogue), so there are no atomics and the
+// result does not depend on scheduling.  A warp owns one column (i, j) and
+// 32 K consecutive k (k = k0 + kk * 32 + lane); a tile is 8 warps on a
+// CX x (8 / CX) patch of columns.  For every angle the warp finds the detector
+// columns whose xy projection crosses cell (i, j) (the cell's four corners),
+// and for each of them the alpha interval [ain, aout] of that crossing (x and
+// y plane crossings, warp-uniform).  A lane then inverts z(alpha) =
+// v (dso/dsd + alpha) over [ain, aout] to get the detector rows that can meet
+// its voxel's z slab, and takes for each the segment
 //     [max(ain, z entry), min(aout, z exit)].
 // The z entry/exit of a row's ray in slab k does not depend on the angle
 // (circular orbit), so it is read from the table DevGeom::zbox, which
 // plane_alpha filled at geometry creation: every length is bit-identical to
 // the forward projector's, and A^T is the exact transpose.
-// With every lane on the same slab k and on neighbouring cells, the lanes'
-// table entries zbox[k][iv] and projection values fall within a few detector
-// rows and columns: the warp's loads touch a few sectors instead of 32.
-// Projections are read u-fastest and pre-weighted by the ray length:
-// w[a][iv][iu] = |d'| * y.
+// Projections are read v-fastest and pre-weighted by the ray length:
+// w[a][iu][iv] = |d'| * y.
 
 constexpr int BWD_THREADS = 256;
 
@@ -331,35 +316,39 @@ constexpr int BWD_THREADS = 256;
 // only the last pass applies the epilogue.  Both are z-fastest, indexed like
 // the internal volume; they may be the same buffer (each lane reads and writes
 // only its own voxels).
-template <typename T, bool ZFAST, int CY, int K>
+template <typename T, bool ZFAST, int CX, int K>
 __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__restrict__ wproj, T *__restrict__ vol,
                                               const Epilogue &epi, int tx, int ty, int tz, int a_begin, int a_end,
                                               const float *acc_in, float *acc_out, double *partial,
                                               double *red) {
-    constexpr int KB = 8 / CY;                    // slab blocks per tile
+    constexpr int CY = 8 / CX;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = tx * 32 + lane;
-    const int j = ty * CY + (warp % CY);
-    const int k0 = (tz * KB + warp / CY) * K;
-    const bool ok = i < g.nx && j < g.ny && k0 < g.nz;
+    const int i = tx * CX + (warp % CX), j = ty * CY + (warp / CX);
+    const int k0 = tz * 32 * K;
+    const bool col_ok = i < g.nx && j < g.ny;          // uniform across the warp
     float acc[K];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
-        const int k = k0 + kk;
-        acc[kk] = acc_in && ok && k < g.nz ? acc_in[((size_t)j * g.nx + i) * g.nz + k] : 0.0f;
+        const int k = k0 + kk * 32 + lane;
+        acc[kk] = acc_in && col_ok && k < g.nz ? acc_in[((size_t)j * g.nx + i) * g.nz + k] : 0.0f;
     }
-    if (ok) {
+    if (col_ok) {
         const float x0 = g.bx0 + i * g.dx, x1 = x0 + g.dx;
         const float y0 = g.by0 + j * g.dy, y1 = y0 + g.dy;
         const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
         const float m = g.dso / g.dsd;
         // The detector windows below only select candidates (every length is
-        // then computed exactly from the zbox table), so they use fast
+        // then computed exactly from plane_alpha), so they use fast
         // approximate divisions: their relative error (~1e-6) stays far below
         // the 0.05-pixel margins.
         const float inv_du = 1.0f / g.du, inv_dv = 1.0f / g.dv;
-        const float zr0 = (g.bz0 + k0 * g.dz) * inv_dv, dzr = g.dz * inv_dv;   // slab k0's bottom, height, over dv
-        const int kn = min(K, g.nz - k0);
+        float zr_lo[K], zr_hi[K];        // voxel slab bottom / top over dv
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const float za = g.bz0 + (k0 + kk * 32 + lane) * g.dz;
+            zr_lo[kk] = za * inv_dv;
+            zr_hi[kk] = (za + g.dz) * inv_dv;
+        }
         const size_t nuv = (size_t)g.nu * g.nv;
         for (int a = a_begin; a < a_end; ++a) {
             const float2 cs = g.trig[a];
@@ -374,7 +363,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
             }
             const int iu0 = max(0, (int)ceilf(__fmaf_rn(umin, inv_du, cu - 0.05f)));
             const int iu1 = min(g.nu - 1, (int)floorf(__fmaf_rn(umax, inv_du, cu + 0.05f)));
-            const float *wa = wproj + (size_t)a * nuv;
+            const float *pa = wproj + (size_t)a * nuv;
             for (int iu = iu0; iu <= iu1; ++iu) {
                 const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
                 const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
@@ -383,23 +372,23 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                 clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
                 clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
                 if (miss || !(ain < aout)) continue;
-                // rows whose ray can be inside slab [z, z + dz] for some alpha in [ain, aout]
+                // rows whose ray can be inside z slab [z, z + dz] for some alpha in [ain, aout]
                 const float rlo = __fdividef(1.0f, m + ain), rhi = __fdividef(1.0f, m + aout);
-                const float *wc = wa + iu;               // row iv at wc[iv * nu]
+                const float *wcol = pa + (size_t)iu * g.nv;
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) {
-                    if (kk >= kn) break;
-                    const float zlo = __fmaf_rn((float)kk, dzr, zr0), zhi = zlo + dzr;
-                    const float vmin = fminf(zlo * rlo, zlo * rhi);
-                    const float vmax = fmaxf(zhi * rlo, zhi * rhi);
+                    const int k = k0 + kk * 32 + lane;
+                    if (k >= g.nz) continue;
+                    const float vmin = fminf(zr_lo[kk] * rlo, zr_lo[kk] * rhi);
+                    const float vmax = fmaxf(zr_hi[kk] * rlo, zr_hi[kk] * rhi);
                     const int r0 = max(0, (int)ceilf(vmin + (cv - 0.05f)));
                     const int r1 = min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f)));
-                    const float2 *zb = g.zbox + (size_t)(k0 + kk) * g.nv;
+                    const float2 *zb = g.zbox + (size_t)k * g.nv;
                     for (int iv = r0; iv <= r1; ++iv) {
-                        const float2 e = __ldg(zb + iv);  // row iv's alpha interval in slab k
+                        const float2 e = zb[iv];         // row iv's alpha interval in slab k
                         const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
                         // a miss adds exactly zero: the same sum as skipping it
-                        acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wc + (size_t)iv * g.nu), acc[kk]);
+                        acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
                     }
                 }
             }
@@ -408,8 +397,8 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
     if (acc_out) {                      // an earlier pass: keep the running sums
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) {
-            const int k = k0 + kk;
-            if (ok && k < g.nz) acc_out[((size_t)j * g.nx + i) * g.nz + k] = acc[kk];
+            const int k = k0 + kk * 32 + lane;
+            if (col_ok && k < g.nz) acc_out[((size_t)j * g.nx + i) * g.nz + k] = acc[kk];
         }
         return;
     }
@@ -417,8 +406,8 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
     double sq = 0.0;
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
-        const int k = k0 + kk;
-        if (!ok || k >= g.nz) continue;
+        const int k = k0 + kk * 32 + lane;
+        if (!col_ok || k >= g.nz) continue;
         const size_t v = ZFAST ? ((size_t)j * g.nx + i) * g.nz + k : ((size_t)k * g.ny + j) * g.nx + i;
         double out = acoef * (double)acc[kk];
         if (bcoef != 0.0) {

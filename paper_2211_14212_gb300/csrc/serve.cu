@@ -39,8 +39,8 @@ namespace cbct {
 constexpr int SRV_MAX_SLOTS = 64;
 constexpr int SRV_FWD_ROWS = 2;                       // forward tile: 2 rays per lane
 constexpr int64_t SRV_SAT_TILES = 4096;                // SRPT: forward tiles that fill a step (~5 waves)
-constexpr int SRV_CY = 8, SRV_BK = 8;                  // transpose tile: 32 x 8 columns x 8 slabs (configuration 2)
-constexpr int SRV_BWD_CONFIG = 2;
+constexpr int SRV_CX = 2, SRV_BK = 4;                  // transpose tile: 2 x 4 columns x 128 (configuration 5)
+constexpr int SRV_BWD_CONFIG = 5;
 
 struct SlotDev {
     DevGeom g;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(BWD_THREADS) srv_backward(const SlotTable *tab
         const int local = item - tab->bwd_start[s];
         const int tbx = local % sd.bgx, tby = (local / sd.bgx) % sd.bgy, tbz = local / (sd.bgx * sd.bgy);
         const Epilogue epi{&sd.st->ba, &sd.st->bb, 0.0, 0.0, nullptr, nullptr, nullptr};
-        backward_tile<float, true, SRV_CY, SRV_BK>(sd.g, sd.Uw, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
+        backward_tile<float, true, SRV_CX, SRV_BK>(sd.g, sd.Uw, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
                                                    nullptr, sd.pb + local, red);
     }
 }
@@ -195,9 +195,9 @@ struct Slot {
 void grids(const cbct_geometry_desc &d, int &fgx, int &fgy, int &bgx, int &bgy, int &bgz) {
     fgx = (d.nu + FWD_COLS - 1) / FWD_COLS;
     fgy = (d.nv + 32 * SRV_FWD_ROWS - 1) / (32 * SRV_FWD_ROWS);
-    bgx = (d.nx + 31) / 32;
-    bgy = (d.ny + SRV_CY - 1) / SRV_CY;
-    bgz = (d.nz + SRV_BK * (8 / SRV_CY) - 1) / (SRV_BK * (8 / SRV_CY));
+    bgx = (d.nx + SRV_CX - 1) / SRV_CX;
+    bgy = (d.ny + (8 / SRV_CX) - 1) / (8 / SRV_CX);
+    bgz = (d.nz + 32 * SRV_BK - 1) / (32 * SRV_BK);
 }
 
 // Device memory a request holds at its peak (ray tables, Krylov vectors,
