@@ -43,7 +43,10 @@ CPU_SAMPLE_ANGLES = 24          # about 20 s of FP64 oracle work on 16 host core
 # keyed by the projector sources it was measured on (projector_hash()); the
 # bench reports null once those sources changed.
 NCU_TRAFFIC = {
-    # "backward": (bytes_per_launch, projector_hash()),
+    # one launch of the 2x4x128 transpose tile at 256^3 / 512^2 / 360 (ncu --set full,
+    # the cbct_backproject launch of the projectors mode; the solver's launch of the
+    # same tile differs only in the output layout): 7.071 GB read + 0.121 GB written
+    "backward": (7192121000, "6bf8558d2cfed6ce"),
 }
 
 
