@@ -359,6 +359,54 @@ def run_projectors(args):
     return 0
 
 
+def run_precision(args):
+    """Storage-precision study on the 512^3 scan (768 x 512 detector, 720 angles,
+    noisy): hybrid LSQR 50 iterations with GCV, Krylov vectors and basis stored
+    in FP32, FP16 or BF16 (FP32 ray sums, FP64 scalars); time per iteration,
+    throughput, and the difference of each result from the FP32 one."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2211_14212_gb300 import cbct
+    g = synth.config("c3")
+    dev = torch.device("cuda", 0)
+    geom = cbct.Geometry(g)
+    tune = cbct.autotune(geom, max_angles=32)
+    x_true = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=2, scale=0.02)).to(dev)
+    b = cbct.project(geom, x_true).cpu().numpy()
+    b = torch.from_numpy(synth.poisson_log_noise(b, 1e5, seed=25).astype(np.float32)).to(dev)
+    nnz = cbct.count_nnz(geom)
+    iters = 50
+    out = {"mode": "precision", "config": {"workload": "512^3 CBCT precision study: hybrid LSQR 50 (GCV)",
+                                           "volume": [g.nx, g.ny, g.nz], "voxel_mm": g.dx,
+                                           "detector": [g.nu, g.nv], "pixel_mm": g.du, "angles": g.nangles,
+                                           "dso_mm": g.dso, "dsd_mm": g.dsd, "noise": "Poisson I0=1e5"},
+           "nnz": nnz, "launch_shapes": {"fwd_rows": tune["fwd_rows"], "bwd": tune["bwd_shape"]}, "storage": {}}
+    ref = None
+    xt = x_true.double()
+    for storage in ("f32", "f16", "bf16"):
+        cbct.hybrid_lsqr(geom, b, 2, storage=storage)                    # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, rep = cbct.hybrid_lsqr(geom, b, iters, storage=storage)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        xd = x.double()
+        if ref is None:
+            ref = xd.clone()
+        out["storage"][storage] = {
+            "s_per_solve": dt, "ms_per_iter": 1000 * dt / iters,
+            "gupdates_per_s": 2 * nnz * iters / dt / 1e9,
+            "rel_diff_vs_f32": float((xd - ref).norm() / ref.norm()),
+            "rel_err_vs_phantom": float((xd - xt).norm() / xt.norm()),
+            "lambda_last": float(rep.lam[-1]), "resid_last": float(rep.resid[-1])}
+        del x, xd
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def serving_requests(count, scale, seed=3):
     """The serving stream: volumes in {128, 192, 256, 384}^3 over a 256 mm field
     of view, square detectors of 256..768 pixels (409.6 mm wide), 90..720 angles
@@ -466,6 +514,7 @@ def run_serving(args):
            "scale": args.serving_scale, "unit": "recon/s",
            "plain_one_at_a_time": plain,
            "server_srpt": serve("srpt"),
+           "server_ratio": serve("ratio"),
            "server_share": serve("share"),
            "request_mix": [r["desc"] + [r["solver"], r["iters"]] for r in reqs]}
     print(json.dumps(out), flush=True)
@@ -479,9 +528,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "projectors", "serving"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "projectors", "serving", "precision"], default="solve",
                     help="solve: the benchmark step (default); projectors: standalone A / A^T timing; "
-                         "serving: continuous-batching server vs one request at a time")
+                         "serving: continuous-batching server vs one request at a time; "
+                         "precision: FP32 / FP16 / BF16 storage study at 512^3")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--serving-scale", type=float, default=1.0)
     ap.add_argument("--serving-slots", type=int, default=16)
@@ -493,6 +543,8 @@ def main():
         sys.exit(run_projectors(args))
     if args.mode == "serving":
         sys.exit(run_serving(args))
+    if args.mode == "precision":
+        sys.exit(run_precision(args))
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
 
 

@@ -125,16 +125,16 @@ cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream 
  * bwd_config: tile of the transpose (one warp per voxel column), 0 = 4 x 2
  * columns x 32 voxels along z (1 per lane), 1 = 4 x 2 x 64 (2 per lane),
  * 2 = 8 x 1 x 32, 3 = 2 x 4 x 64, 4 = 4 x 2 x 128 (4 per lane),
- * 5 = 2 x 4 x 128.  Changing the shape while another thread uses the
- * geometry is a data race. */
-#define CBCT_TUNE_TIMES 9
+ * 5 = 2 x 4 x 128, 6 = 4 x 2 x 256 (8 per lane), 7 = 2 x 4 x 256.  Changing
+ * the shape while another thread uses the geometry is a data race. */
+#define CBCT_TUNE_TIMES 11
 cbct_status cbct_geometry_set_launch(cbct_geometry *geom, int fwd_rows, int bwd_config);
 cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, int *bwd_config);
 /* Times every launch shape (forward and transpose, FP32, on a strided subset
  * of at most max_angles angles; max_angles <= 0 = all) and keeps the fastest.
  * times_ms, if non-null, is a host array of CBCT_TUNE_TIMES doubles that
  * receives the forward times for fwd_rows 1, 2, 4 and the transpose times for
- * bwd_config 0..5.  Allocates scratch on `stream` and synchronises it. */
+ * bwd_config 0..7.  Allocates scratch on `stream` and synchronises it. */
 cbct_status cbct_geometry_autotune(cbct_geometry *geom, int max_angles, double *times_ms, cbct_stream stream);
 /* Angles per pass of the transpose inside the solvers and cbct_backproject
  * (performance only).  With a
@@ -173,6 +173,12 @@ typedef struct {
                                 ||b - A x_lambda|| = nl ||b|| on the projected problem, found by
                                 bisection in log lambda over sigma_max [1e-8, 1e8]; 0 while even
                                 the smallest lambda leaves the residual above the target */
+    int explicit_residual;   /* nonzero: after every iteration compute ||b - A x_k|| with one more
+                                forward projection and stop at the first k where it exceeds
+                                (1 - stop_tol) times the previous one, returning x_{k-1} (the
+                                paper's toolbox stops once the explicit residual increases,
+                                Sec. 3.1.1); costs one product with A per iteration */
+    double stop_tol;         /* 0 <= stop_tol < 1; 0 = stop on increase */
 } cbct_solve_opts;
 
 /* Per-iteration histories, written to caller-allocated HOST arrays of length
@@ -190,6 +196,11 @@ typedef struct {
     int64_t backward_launches;   /* out: backprojector launches */
     double forward_ms;           /* out, profile != 0: summed device time of the forward launches */
     double backward_ms;          /* out, profile != 0: summed device time of the backprojector launches */
+    double *explicit_resid_norm; /* explicit_residual: ||b - A x_k|| per completed iteration, plus the
+                                    one that triggered the stop (host array of length >= iters) */
+    int explicit_count;          /* out: entries written to explicit_resid_norm */
+    int stopped_on_residual;     /* out: 1 if the explicit-residual rule ended the solve; the
+                                    returned x is then x_{iters_done}, iters_done = count - 1 */
 } cbct_solve_report;
 
 /* CGLS (Sec. 2.1.1, Eq. 3). */
@@ -224,7 +235,10 @@ cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *geom, const float *b, fl
  * (nx + ny)) while the step's forward tiles (8 detector columns x 64 rows of
  * one angle each) stay within 4096, about five waves of the GPU, so small
  * requests are batched and large ones run one at a time, shortest first;
- * CBCT_SCHED_SHARE advances every admitted request every step.  Each result
+ * CBCT_SCHED_RATIO orders them by response ratio (age + remaining time) /
+ * remaining time instead (remaining time from the same cost model and the
+ * measured work rate), so that a long request's priority grows while it
+ * waits; CBCT_SCHED_SHARE advances every admitted request every step.  Each result
  * equals the single-request solver's (same kernels and per-voxel / per-ray
  * summation order) up to the rounding of the blockwise norm reductions.
  * Requests use FP32 storage and LSQR or LSMR.  All calls are thread-safe
@@ -234,7 +248,7 @@ cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *geom, const float *b, fl
 typedef struct cbct_server cbct_server;   /* opaque, library-owned */
 typedef enum { CBCT_SOLVER_LSQR = 0, CBCT_SOLVER_LSMR = 1 } cbct_solver;
 
-typedef enum { CBCT_SCHED_SRPT = 0, CBCT_SCHED_SHARE = 1 } cbct_schedule;
+typedef enum { CBCT_SCHED_SRPT = 0, CBCT_SCHED_SHARE = 1, CBCT_SCHED_RATIO = 2 } cbct_schedule;
 
 typedef struct {
     size_t hbm_budget_bytes;   /* device memory the server may hold for requests (> 0) */

@@ -421,6 +421,45 @@ def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False, noise_le
     return x, hist
 
 
+# ------------------------------------------- explicit residuals and the stopping rule
+def explicit_residual_stop(op, b, method, iters, stop_tol=0.0, **kw):
+    """Run `method` ("cgls", "lsqr", "lsmr" or "hybrid_lsqr") for up to `iters`
+    iterations, computing the explicit residual norm ||b - A x_k|| after every
+    iteration (one extra product with A each), and stop at the first k whose
+    residual exceeds (1 - stop_tol) times the previous one: the result is then
+    x_{k-1} after k - 1 iterations.  stop_tol = 0 stops when the residual
+    increases, which is what the paper's toolbox does (Sec. 3.1.1: an increase
+    flags loss of orthogonality or accumulated rounding); stop_tol > 0 also
+    stops when the decrease stalls.
+
+    The iterates of a run do not depend on later iterations, so the stopped
+    run is the unstopped run cut at k - 1.  Returns (x, hist) with hist of the
+    method (cut at the returned iteration) plus ``explicit_resid`` (every
+    computed ||b - A x_k||, including the one that triggered the stop) and
+    ``stopped`` (True when the rule ended the run early).
+    """
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    fn = {"cgls": cgls, "lsqr": lsqr, "lsmr": lsmr, "hybrid_lsqr": hybrid_lsqr}[method]
+    x_full, h = fn(op, b, iters, keep_iterates=True, **kw)
+    its = h["iterates"]
+    resid = []
+    done = len(its)
+    stopped = False
+    for k, xk in enumerate(its, start=1):
+        resid.append(_norm(b - op.matvec(xk)))
+        if k > 1 and resid[-1] > (1.0 - stop_tol) * resid[-2]:
+            done = k - 1
+            stopped = True
+            break
+    x = its[done - 1].copy() if done > 0 else np.zeros(op.shape[1])
+    out = {key: (val[:done] if isinstance(val, list) and key not in ("beta", "alpha") else val)
+           for key, val in h.items()}
+    out["iterates"] = its[:done]
+    out["explicit_resid"] = resid
+    out["stopped"] = stopped
+    return x, out
+
+
 # ------------------------------------------------------------ dense Krylov reference
 def krylov_basis(a, b, k):
     """Orthonormal basis (columns) of K_k(A^T A, A^T b), Arnoldi with full

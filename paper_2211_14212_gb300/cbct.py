@@ -45,7 +45,8 @@ class _Desc(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("lam", ctypes.c_double), ("rule", ctypes.c_int),
                 ("storage", ctypes.c_int), ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
-                ("noise_level", ctypes.c_double)]
+                ("noise_level", ctypes.c_double), ("explicit_residual", ctypes.c_int),
+                ("stop_tol", ctypes.c_double)]
 
 
 class _Report(ctypes.Structure):
@@ -57,7 +58,10 @@ class _Report(ctypes.Structure):
                 ("forward_launches", ctypes.c_int64),
                 ("backward_launches", ctypes.c_int64),
                 ("forward_ms", ctypes.c_double),
-                ("backward_ms", ctypes.c_double)]
+                ("backward_ms", ctypes.c_double),
+                ("explicit_resid_norm", ctypes.POINTER(ctypes.c_double)),
+                ("explicit_count", ctypes.c_int),
+                ("stopped_on_residual", ctypes.c_int)]
 
 
 class _ServerOpts(ctypes.Structure):
@@ -262,10 +266,10 @@ def count_nnz(geom: Geometry, stream=None) -> int:
     return int(n.value)
 
 
-TUNE_TIMES = 9
+TUNE_TIMES = 11
 FWD_ROWS = (1, 2, 4)
 BWD_CONFIGS = ("4x2 columns x 32", "4x2 columns x 64", "8x1 columns x 32", "2x4 columns x 64",
-               "4x2 columns x 128", "2x4 columns x 128")
+               "4x2 columns x 128", "2x4 columns x 128", "4x2 columns x 256", "2x4 columns x 256")
 
 
 def set_launch(geom: Geometry, fwd_rows: int, bwd_config: int):
@@ -314,10 +318,12 @@ class SolveReport:
     backward_launches: int = 0
     forward_ms: float = 0.0
     backward_ms: float = 0.0
+    explicit_resid: np.ndarray = field(default=None)
+    stopped_on_residual: bool = False
 
 
 def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=True, x=None, stream=None,
-           profile=False, noise_level=0.0):
+           profile=False, noise_level=0.0, explicit_residual=False, stop_tol=0.0):
     """Run one of the C-ABI solvers.  b/x may be CUDA tensors or host (numpy or
     CPU torch, FP32) buffers; host buffers are staged by the library."""
     import torch
@@ -344,19 +350,21 @@ def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=Tru
     rule_code = ({"fixed": LAMBDA_FIXED, "gcv": LAMBDA_GCV, "dp": LAMBDA_DP}[rule] if isinstance(rule, str)
                  else int(rule))
     opts = _Opts(int(iters), float(lam), rule_code, STORAGE[storage], 1 if use_graph else 0, 1 if profile else 0,
-                 float(noise_level))
+                 float(noise_level), 1 if explicit_residual else 0, float(stop_tol))
     hr = np.zeros(iters, dtype=np.float64)
     hn = np.zeros(iters, dtype=np.float64)
     hl = np.zeros(iters, dtype=np.float64)
     dp = ctypes.POINTER(ctypes.c_double)
+    he = np.zeros(iters, dtype=np.float64)
     rep = _Report(0, hr.ctypes.data_as(dp), hn.ctypes.data_as(dp), hl.ctypes.data_as(dp))
+    rep.explicit_resid_norm = he.ctypes.data_as(dp)
     st = getattr(lib, fn)(geom.handle, ctypes.c_void_p(bptr), ctypes.c_void_p(xptr), ctypes.byref(opts),
                           ctypes.byref(rep), _stream_handle(stream))
     _check(fn, st)
     k = rep.iters_done
     return x, SolveReport(k, hr[:k].copy(), hn[:k].copy(), hl[:k].copy(), int(rep.kernel_launches),
                           int(rep.forward_launches), int(rep.backward_launches), float(rep.forward_ms),
-                          float(rep.backward_ms))
+                          float(rep.backward_ms), he[:rep.explicit_count].copy(), bool(rep.stopped_on_residual))
 
 
 def cgls(geom, b, iters, lam=0.0, **kw):
@@ -394,10 +402,11 @@ class Server:
     """Continuous-batching server (cbct_server_*): requests of different scans
     are admitted by device-memory budget and advanced in steps of one Krylov
     iteration; schedule "srpt" (default) advances the requests with the least
-    remaining work until a step fills the GPU, "share" advances all of them."""
+    remaining work until a step fills the GPU, "ratio" orders them by response
+    ratio (age + remaining) / remaining, "share" advances all of them."""
 
     SOLVERS = {"lsqr": 0, "lsmr": 1}
-    SCHEDULES = {"srpt": 0, "share": 1}
+    SCHEDULES = {"srpt": 0, "share": 1, "ratio": 2}
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, use_graph: bool = True, schedule: str = "srpt"):
         lib = load()

@@ -175,6 +175,6 @@ int backward_num_blocks(const DevGeom &g);
 dim3 forward_grid(const DevGeom &g);
 dim3 backward_grid(const DevGeom &g);
 BrickShape backward_shape(int config);
-constexpr int NUM_FWD_ROWS = 3, NUM_BWD_CONFIGS = 6;
+constexpr int NUM_FWD_ROWS = 3, NUM_BWD_CONFIGS = 8;
 
 }  // namespace cbct

@@ -107,7 +107,7 @@ cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaSt
 // ---------------------------------------------------------- transpose A^T y
 
 template <typename T, bool ZFAST, int CX, int K>
-__global__ void __launch_bounds__(BWD_THREADS, 4)
+__global__ void __launch_bounds__(BWD_THREADS, K >= 8 ? 3 : 4)
 backward_kernel(DevGeom g, const float *__restrict__ proj, T *__restrict__ vol, Epilogue epi, int a_begin, int a_end,
                 const float *acc_in, float *acc_out) {
     __shared__ double red[BWD_THREADS / 32];
@@ -125,6 +125,8 @@ BrickShape backward_shape(int config) {
     case 3: return BrickShape{2, 4, 64, 2};
     case 4: return BrickShape{4, 2, 128, 4};
     case 5: return BrickShape{2, 4, 128, 4};
+    case 6: return BrickShape{4, 2, 256, 8};
+    case 7: return BrickShape{2, 4, 256, 8};
     default: return BrickShape{4, 2, 32, 1};
     }
 }
@@ -151,6 +153,8 @@ static void launch_backward_t(const DevGeom &g, const float *y, void *x, const E
     case 3: backward_kernel<T, ZF, 2, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     case 4: backward_kernel<T, ZF, 4, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     case 5: backward_kernel<T, ZF, 2, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 6: backward_kernel<T, ZF, 4, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 7: backward_kernel<T, ZF, 2, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     default: backward_kernel<T, ZF, 4, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     }
 }

@@ -222,6 +222,7 @@ size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
 struct ServerImpl {
     size_t budget = 0, in_use = 0;
     int max_slots = 1, use_graph = 1, device = 0, schedule = CBCT_SCHED_SRPT;
+    double work_rate = 0.0;           // cost-model units per second, running estimate from timed steps
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -410,17 +411,31 @@ void ServerImpl::fail_all(cbct_status st, const std::string &msg) {
 // ------------------------------------------------------------------ worker
 
 // SRPT: the slots with the least remaining work (iterations left x cost of
-// one), ties by request id, as long as the step's forward tiles stay within
-// SRV_SAT_TILES (the first slot always runs); SHARE: every slot.  Returned in
-// increasing slot index.
+// one), ties by request id; RATIO: the slots with the highest response ratio
+// (time since submission + remaining time) / remaining time, the remaining
+// time estimated from the cost model and the measured work rate, so that
+// short requests go first but a waiting request's priority grows with its
+// age.  Both take slots in that order as long as the step's forward tiles stay
+// within SRV_SAT_TILES (the first slot always runs).  SHARE: every slot.
+// Returned in increasing slot index.
 std::vector<int> ServerImpl::pick_step_slots() const {
     std::vector<int> all(slots.size());
     for (size_t i = 0; i < slots.size(); ++i) all[i] = (int)i;
     if (schedule == CBCT_SCHED_SHARE) return all;
     auto remaining = [&](int i) { return (slots[i].req->iters - slots[i].steps) * slots[i].work_iter; };
+    std::vector<double> key(slots.size());
+    const double now = now_s(t0);
+    for (size_t i = 0; i < slots.size(); ++i) {
+        const double rem = remaining((int)i);
+        if (schedule == CBCT_SCHED_RATIO && work_rate > 0.0) {
+            const double rem_s = std::max(rem / work_rate, 1e-6);
+            key[i] = -(now - slots[i].req->t_submit + rem_s) / rem_s;       // higher ratio first
+        } else {
+            key[i] = rem;
+        }
+    }
     std::sort(all.begin(), all.end(), [&](int a, int b) {
-        const double ra = remaining(a), rb = remaining(b);
-        return ra != rb ? ra < rb : slots[a].req->id < slots[b].req->id;
+        return key[a] != key[b] ? key[a] < key[b] : slots[a].req->id < slots[b].req->id;
     });
     std::vector<int> pick;
     int64_t tiles = 0;
@@ -509,8 +524,15 @@ void ServerImpl::run() {
             }
             table_dirty = false;
         }
+        const double t_step = now_s(t0);
         cbct_status st = enqueue_step();
         cudaError_t e = cudaStreamSynchronize(s);
+        {   // running estimate of the work rate (cost-model units per second)
+            double w = 0.0;
+            for (int i : step_slots) w += slots[i].work_iter;
+            const double dt = now_s(t0) - t_step;
+            if (dt > 0.0 && w > 0.0) work_rate = work_rate > 0.0 ? 0.8 * work_rate + 0.2 * (w / dt) : w / dt;
+        }
         if (st != CBCT_OK || e != cudaSuccess) {
             if (e != cudaSuccess) st = cuda_fail(e, "server: step");
             fail_all(st, cbct_last_error());
@@ -562,7 +584,7 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *o, cbct_server
         set_error("cbct_server_create: need hbm_budget_bytes > 0 and 1 <= max_slots <= 64");
         return CBCT_EINVAL;
     }
-    if (o->schedule != CBCT_SCHED_SRPT && o->schedule != CBCT_SCHED_SHARE) {
+    if (o->schedule != CBCT_SCHED_SRPT && o->schedule != CBCT_SCHED_SHARE && o->schedule != CBCT_SCHED_RATIO) {
         set_error("cbct_server_create: unknown schedule");
         return CBCT_EINVAL;
     }

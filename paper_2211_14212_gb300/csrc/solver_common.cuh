@@ -77,9 +77,13 @@ k_scale_inplace(float *v, int64_t n, const double *coef, const int *stop) {
 }
 
 // Combine a basis: x[m] = sum_j coef[j] * basis_j[m], basis_j = basis + j * n.
+// When `stop` is given the launch does nothing once *stop is set (the
+// coefficients of an unfinished step are not valid then).
 template <typename T>
 __global__ void __launch_bounds__(VEC_THREADS)
-k_combine(const T *__restrict__ basis, const double *__restrict__ coef, int k, int64_t n, float *__restrict__ x) {
+k_combine(const T *__restrict__ basis, const double *__restrict__ coef, int k, int64_t n, float *__restrict__ x,
+          const int *stop = nullptr) {
+    if (stop && *stop) return;
     for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS) {
         double acc = 0.0;
         for (int j = 0; j < k; ++j) acc += coef[j] * (double)Storage<T>::ld_plain(basis + (size_t)j * n + i);

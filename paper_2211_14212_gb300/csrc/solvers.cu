@@ -13,6 +13,7 @@
 // power-of-two scale: U = su * beta_i u_i and V = sv * alpha_i v_i.  The scale
 // factors and norms enter the coefficients of the next fused epilogue, so no
 // separate normalisation pass over the vectors is needed.
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -26,6 +27,113 @@ cbct_status launch_projected_solve(const double *alphas, const double *betas, co
                                    const int *iter, const int *stop, int rule, double lambda_fixed,
                                    double noise_level, double *work, int kmax, double *coef,
                                    double *hist_lambda, double *hist_resid, cudaStream_t s);
+
+// ================================================== explicit residual monitor
+//
+// With opts->explicit_residual, every iteration ends with r = b - A x_k (one
+// forward launch whose epilogue forms b - A x and the per-block partials of
+// ||r||^2) and a single-block check: record ||r||; if it exceeds
+// (1 - stop_tol) times the previous value, set the method's stop flag (every
+// later launch of the solve then does nothing) and mark the run as stopped by
+// the rule.  x_{k-1} is kept in `xprev` (copied before each x update) and
+// restored at the end.  The paper's toolbox stops on an increase of this
+// explicit residual (Sec. 3.1.1).
+
+struct ExplicitState {
+    double prev;
+    int count, stopped;
+};
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_explicit_check(const double *part, int np, ExplicitState *es, int *stop, double *hist, int cap, double tol) {
+    __shared__ double red[RED_THREADS / 32];
+    if (*stop) return;
+    const double rr = sqrt(reduce_partials(part, np, red));
+    if (threadIdx.x) return;
+    const int c = es->count;
+    if (c < cap) hist[c] = rr;
+    es->count = c + 1;
+    if (c > 0 && !(rr <= (1.0 - tol) * es->prev)) {     // increase, stall, or not finite
+        *stop = 1;
+        es->stopped = 1;
+    }
+    es->prev = rr;
+}
+
+__global__ void __launch_bounds__(VEC_THREADS)
+k_copy_running(const float *__restrict__ src, float *__restrict__ dst, int64_t n, const int *stop) {
+    if (*stop) return;
+    for (int64_t i = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; i < n; i += (int64_t)VEC_BLOCKS * VEC_THREADS)
+        dst[i] = src[i];
+}
+
+// Buffers and launches of the monitor; inactive (no allocation, no launches)
+// unless opts->explicit_residual.
+struct ExplicitMonitor {
+    bool on = false;
+    float *r = nullptr, *xprev = nullptr;
+    double *part = nullptr, *hist = nullptr;
+    ExplicitState *es = nullptr;
+    int nf = 0, cap = 0;
+    double tol = 0.0;
+
+    cbct_status init(const cbct_solve_opts *o, const DevGeom &g, int64_t n, int64_t m, Workspace &ws) {
+        on = o->explicit_residual != 0;
+        if (!on) return CBCT_OK;
+        tol = o->stop_tol;
+        cap = o->iters;
+        nf = forward_num_blocks(g);
+        CBCT_CUDA_TRY(ws.alloc(&r, (size_t)n));
+        CBCT_CUDA_TRY(ws.alloc(&xprev, (size_t)m));
+        CBCT_CUDA_TRY(ws.alloc(&part, (size_t)nf));
+        CBCT_CUDA_TRY(ws.alloc(&hist, (size_t)cap));
+        CBCT_CUDA_TRY(ws.alloc(&es, 1));
+        CBCT_CUDA_TRY(cudaMemsetAsync(es, 0, sizeof(ExplicitState), ws.s));
+        CBCT_CUDA_TRY(cudaMemsetAsync(xprev, 0, sizeof(float) * m, ws.s));     // x_0 = 0
+        return CBCT_OK;
+    }
+    // before the x update of an iteration
+    void keep(const float *x, int64_t m, const int *stop, cudaStream_t s, Tracker &tr) {
+        if (!on) return;
+        k_copy_running<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(x, xprev, m, stop);
+        ++tr.launches;
+    }
+    // after the x update: r = b - A x, the check
+    template <typename Fwd>
+    cbct_status check(Fwd &&fwd32, const float *x, const float *b_vfast, int *stop, cudaStream_t s, Tracker &tr) {
+        if (!on) return CBCT_OK;
+        const Epilogue e{nullptr, nullptr, -1.0, 1.0, part, stop, b_vfast};
+        cbct_status st = fwd32(x, r, e);
+        if (st != CBCT_OK) return st;
+        k_explicit_check<<<1, RED_THREADS, 0, s>>>(part, nf, es, stop, hist, cap, tol);
+        ++tr.launches;
+        CBCT_CUDA_TRY(cudaGetLastError());
+        return CBCT_OK;
+    }
+    // after the loop: restore x_{k-1} if the rule stopped the run, fill the report
+    cbct_status finish(float *x, int64_t m, cudaStream_t s, cbct_solve_report *rep, int *iters_done) {
+        if (!on) {
+            if (rep) { rep->explicit_count = 0; rep->stopped_on_residual = 0; }
+            return CBCT_OK;
+        }
+        ExplicitState h;
+        CBCT_CUDA_TRY(cudaMemcpyAsync(&h, es, sizeof h, cudaMemcpyDeviceToHost, s));
+        std::vector<double> hv((size_t)cap);
+        CBCT_CUDA_TRY(cudaMemcpyAsync(hv.data(), hist, sizeof(double) * cap, cudaMemcpyDeviceToHost, s));
+        CBCT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h.stopped) {
+            CBCT_CUDA_TRY(cudaMemcpyAsync(x, xprev, sizeof(float) * m, cudaMemcpyDeviceToDevice, s));
+            *iters_done = h.count - 1;
+        }
+        if (rep) {
+            const int c = std::min(h.count, cap);
+            if (rep->explicit_resid_norm) std::memcpy(rep->explicit_resid_norm, hv.data(), sizeof(double) * c);
+            rep->explicit_count = c;
+            rep->stopped_on_residual = h.stopped;
+        }
+        return CBCT_OK;
+    }
+};
 
 // ===================================================================== CGLS
 //
@@ -178,6 +286,10 @@ static cbct_status check_solve_args(const cbct_geometry *g, const float *b, floa
         return CBCT_EINVAL;
     }
     if (!(o->lambda >= 0.0) || !std::isfinite(o->lambda)) { set_error("solver: lambda must be finite and >= 0"); return CBCT_EINVAL; }
+    if (o->explicit_residual && !(o->stop_tol >= 0.0 && o->stop_tol < 1.0)) {
+        set_error("solver: stop_tol must be in [0, 1)");
+        return CBCT_EINVAL;
+    }
     return CBCT_OK;
 }
 
@@ -293,6 +405,18 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
         ++tr.fwd;
         return r;
     };
+    auto fwd32 = [&](const void *in, void *out, const Epilogue &e) -> cbct_status {
+        cbct_status r = tr.mark(0);
+        if (r == CBCT_OK) r = launch_forward(g, in, out, CBCT_F32, e, s, true);
+        if (r == CBCT_OK) r = tr.mark(0);
+        ++tr.launches;
+        ++tr.fwd;
+        return r;
+    };
+    ExplicitMonitor em;
+    st = em.init(o, g, n, m, ws);
+    if (st != CBCT_OK) return st;
+    int *stopw = &dst->stop;
     auto bwd = [&](const float *in, void *out, const Epilogue &e) -> cbct_status {
         cbct_status r = tr.mark(1);
         if (r == CBCT_OK) r = launch_backward(g, in, out, t, e, s, true, accum);
@@ -349,6 +473,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
         gk_after_backward<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method, hist_r, hist_n, alpha_arr,
                                                      scale_arr, iters);
         tr.launches += 3;            // two finalize kernels + the update / projected solve
+        em.keep(io.xz, m, stop, s, tr);
         if (method == M_LSQR) {
             k_lsqr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.xz, w, m, dst);
         } else if (method == M_LSMR) {
@@ -357,9 +482,13 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
             r = launch_projected_solve(alpha_arr, beta_arr, scale_arr, &dst->iter, stop, (int)o->rule, o->lambda,
                                        o->noise_level, work, iters, coef, hist_l, hist_r, s);
             if (r != CBCT_OK) return r;
+            if (em.on) {                 // the monitor needs x_k itself: x_k = V_k y_k
+                k_combine<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(basis, coef, k + 1, m, io.xz, stop);
+                ++tr.launches;
+            }
         }
         CBCT_CUDA_TRY(cudaGetLastError());
-        return CBCT_OK;
+        return em.check(fwd32, io.xz, io.b_dev, stopw, s, tr);
     };
     if (method == M_HYBRID) {
         for (k = 0; k < iters; ++k) {
@@ -380,17 +509,20 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     CBCT_CUDA_TRY(cudaMemcpyAsync(&fin, dst, sizeof fin, cudaMemcpyDeviceToHost, s));
     CBCT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * 3 * iters, cudaMemcpyDeviceToHost, s));
     CBCT_CUDA_TRY(cudaStreamSynchronize(s));
-    if (method == M_HYBRID && fin.iter > 0) {
+    if (method == M_HYBRID && fin.iter > 0 && !em.on) {
         // x_k = V_k y_k with the coefficients of the last completed projected solve
         k_combine<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(basis, coef, fin.iter, m, io.xz);
         ++tr.launches;
         CBCT_CUDA_TRY(cudaGetLastError());
     }
+    int done = fin.iter;
+    st = em.finish(io.xz, m, s, rep, &done);
+    if (st != CBCT_OK) return st;
     st = finish_io(geom, io, s);
     if (st != CBCT_OK) return st;
     ++tr.launches;                   // the final re-layout of x
     if (io.x_is_host || method == M_HYBRID) CBCT_CUDA_TRY(cudaStreamSynchronize(s));
-    copy_report(rep, fin.iter, h, iters);
+    copy_report(rep, done, h, iters);
     tr.fill(rep);
     if (fin.status == CBCT_EBREAKDOWN) set_error("Krylov breakdown: a norm became zero or non-finite");
     return (cbct_status)fin.status;
@@ -447,6 +579,10 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     init.lam2 = o->lambda * o->lambda;
     CBCT_CUDA_TRY(cudaMemcpyAsync(dst, &init, sizeof init, cudaMemcpyHostToDevice, s));
     const int *stop = &dst->stop;
+    int *stopw = &dst->stop;
+    ExplicitMonitor em;
+    st = em.init(o, g, n, m, ws);
+    if (st != CBCT_OK) return st;
 
     // r = b; s = A^T r; gamma = ||s||^2; p = s
     k_copy_sumsq<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, r, nullptr, n, nullptr, nullptr);
@@ -475,12 +611,13 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
         Epilogue eb{nullptr, nullptr, 1.0, 0.0, nullptr, stop, nullptr};
         rr = bwd(wr, sv, eb);
         if (rr != CBCT_OK) return rr;
+        em.keep(io.xz, m, stop, s, tr);
         k_cg_xs<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.xz, sv, p, m, ps, dst);
         cg_after_backward<<<1, RED_THREADS, 0, s>>>(dst, ps, VEC_BLOCKS, pr, VEC_BLOCKS, hist_r, hist_n, iters);
         k_cg_p<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(p, sv, m, pp, dst);
         tr.launches += 6;
         CBCT_CUDA_TRY(cudaGetLastError());
-        return CBCT_OK;
+        return em.check(fwd, io.xz, io.b_dev, stopw, s, tr);
     };
     const Tracker before = tr.snapshot();
     int replays = 0;
@@ -491,11 +628,15 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     std::vector<double> h((size_t)3 * iters);
     CBCT_CUDA_TRY(cudaMemcpyAsync(&fin, dst, sizeof fin, cudaMemcpyDeviceToHost, s));
     CBCT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * 3 * iters, cudaMemcpyDeviceToHost, s));
+    CBCT_CUDA_TRY(cudaStreamSynchronize(s));
+    int done = fin.iter;
+    st = em.finish(io.xz, m, s, rep, &done);
+    if (st != CBCT_OK) return st;
     st = finish_io(geom, io, s);
     if (st != CBCT_OK) return st;
     ++tr.launches;                   // the final re-layout of x
     CBCT_CUDA_TRY(cudaStreamSynchronize(s));
-    copy_report(rep, fin.iter, h, iters);
+    copy_report(rep, done, h, iters);
     tr.fill(rep);
     if (fin.status == CBCT_EBREAKDOWN) set_error("Krylov breakdown: a norm became zero or non-finite");
     return (cbct_status)fin.status;

@@ -127,7 +127,7 @@ def test_many_requests_continuous(cbct):
     assert st["bytes_in_use"] == 0 and st["active"] == 0 and st["pending"] == 0
 
 
-@pytest.mark.parametrize("schedule", ["srpt", "share"])
+@pytest.mark.parametrize("schedule", ["srpt", "ratio", "share"])
 def test_schedule(cbct, schedule):
     """A large request (more forward tiles than one step needs to fill the GPU)
     and a short one submitted right after it: SRPT runs the short one alone,
@@ -147,7 +147,9 @@ def test_schedule(cbct, schedule):
     if schedule == "srpt":
         assert st["steps"] == 34
         assert r_small.finish_s <= r_big.finish_s
-    else:
+    elif schedule == "share":
         assert st["steps"] < 34
+    else:                       # the young short request has the higher response ratio
+        assert r_small.finish_s <= r_big.finish_s
     alone, _ = cbct.lsqr(cbct.Geometry(small), b_small, 4)
     assert rel(r_small.x, alone) <= MIX_TOL

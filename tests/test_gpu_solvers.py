@@ -306,3 +306,43 @@ def test_rejects_bad_storage_for_cgls(cbct, c1_problem):
     geom = cbct.Geometry(g)
     with pytest.raises(cbct.CbctError):
         cbct.cgls(geom, dev(b), 3, storage="f16")
+
+
+# ------------------------------- explicit residuals and the stopping rule (Sec. 3.1.1)
+def _explicit_close(got, ref, b):
+    got, ref = np.asarray(got), np.asarray(ref)
+    assert got.shape == ref.shape
+    # ||b - A x|| of an FP32 x: the cancellation in b - A x costs ~1e-7 ||b||
+    assert np.all(np.abs(got - ref) <= 1e-4 * ref + 1e-6 * np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("method", ["cgls", "lsqr", "lsmr", "hybrid_lsqr"])
+def test_explicit_residual_history(cbct, c1_problem, method):
+    """||b - A x_k|| after every iteration (one more forward projection each)
+    equals the oracle's explicit residual; the iterates are unchanged and, in
+    this well-conditioned range, the rule does not stop the solve."""
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    k = 12
+    x0, _ = getattr(cbct, method)(geom, dev(b), k)
+    x, rep = getattr(cbct, method)(geom, dev(b), k, explicit_residual=True)
+    assert rep.iters_done == k and not rep.stopped_on_residual
+    assert rel(x.cpu().numpy(), x0.cpu().numpy()) <= 1e-6
+    _, h = krylov.explicit_residual_stop(oracle.Operator(g), b, method, k)
+    _explicit_close(rep.explicit_resid, h["explicit_resid"], b)
+    assert rep.forward_launches == 2 * k            # the method's product + the explicit residual
+
+
+@pytest.mark.parametrize("method", ["cgls", "lsqr"])
+def test_explicit_residual_stops_on_stall(cbct, c1_problem, method):
+    """stop_tol = 0.15: the solve stops at the first iteration that reduces the
+    explicit residual by less than 15 % (k = 8 here, ratio 0.90 against the
+    threshold 0.85) and returns the previous iterate, as the oracle does."""
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    x, rep = getattr(cbct, method)(geom, dev(b), 30, explicit_residual=True, stop_tol=0.15)
+    x_ref, h = krylov.explicit_residual_stop(oracle.Operator(g), b, method, 30, stop_tol=0.15)
+    assert h["stopped"] and rep.stopped_on_residual
+    assert rep.iters_done == len(h["iterates"]) == 7
+    _explicit_close(rep.explicit_resid, h["explicit_resid"], b)
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL

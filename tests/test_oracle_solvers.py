@@ -237,3 +237,61 @@ def test_dp_bisection_brackets_the_root():
     y = np.linalg.solve(h.T @ h + lam * lam * np.eye(k), h.T @ (beta1 * np.eye(k + 1)[0]))
     assert abs(np.linalg.norm(beta1 * np.eye(k + 1)[0] - h @ y) - target) <= 1e-8 * beta1
     assert krylov.dp_lambda(sigma, p[0], beta1, 0.5 * r0) == 0.0
+
+
+# ------------------------------- explicit residuals and the stopping rule (Sec. 3.1.1)
+class _UnmatchedOperator:
+    """A with a mismatched 'transpose' B = D A^T (D a fixed positive diagonal on
+    the voxel side), the situation the paper's toolbox meets with its
+    approximately matched backprojector."""
+
+    def __init__(self, a, seed):
+        self.a = a
+        self.shape = a.shape
+        self.d = np.random.default_rng(seed).uniform(0.3, 1.7, a.shape[1])
+
+    def matvec(self, x):
+        return self.a @ x
+
+    def rmatvec(self, y):
+        return self.d * (self.a.T @ y)
+
+
+def test_explicit_residuals_equal_lsqr_estimates(tiny_system):
+    """With the exact transpose in FP64 the explicit ||b - A x_k|| equals LSQR's
+    recurrence estimate, decreases, and never triggers the stop."""
+    a, b = tiny_system
+    x, h = krylov.explicit_residual_stop(oracle.DenseOperator(a), b, "lsqr", 12)
+    assert not h["stopped"] and len(h["iterates"]) == 12
+    np.testing.assert_allclose(h["explicit_resid"], h["resid"], rtol=1e-9)
+    assert np.all(np.diff(h["explicit_resid"]) < 0)
+
+
+def test_stop_on_increase_with_unmatched_backprojector(tiny_system):
+    """An unmatched B makes the explicit residual of LSQR increase at some k;
+    the rule returns x_{k-1} (the unstopped run's iterate), and all residuals
+    before the stop decrease."""
+    a, b = tiny_system
+    op = _UnmatchedOperator(a, 5)
+    _, full = krylov.lsqr(op, b, 40, keep_iterates=True)
+    res = [np.linalg.norm(b - a @ xk) for xk in full["iterates"]]
+    first_up = next(k for k in range(1, len(res)) if res[k] > res[k - 1])      # 0-based index of iterate k+1
+    x, h = krylov.explicit_residual_stop(op, b, "lsqr", 40)
+    assert h["stopped"]
+    assert len(h["iterates"]) == first_up
+    np.testing.assert_array_equal(x, full["iterates"][first_up - 1])
+    np.testing.assert_allclose(h["explicit_resid"], res[:first_up + 1], rtol=1e-12)
+    assert np.all(np.diff(h["explicit_resid"][:-1]) < 0)
+
+
+def test_stop_on_stalled_decrease(tiny_system):
+    """stop_tol = 0.1: stop at the first iteration that reduces the explicit
+    residual by less than 10 %."""
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    _, full = krylov.cgls(op, b, 30, keep_iterates=True)
+    res = [np.linalg.norm(b - a @ xk) for xk in full["iterates"]]
+    k_stall = next(k for k in range(1, len(res)) if res[k] > 0.9 * res[k - 1])
+    x, h = krylov.explicit_residual_stop(op, b, "cgls", 30, stop_tol=0.1)
+    assert h["stopped"] and len(h["iterates"]) == k_stall
+    np.testing.assert_array_equal(x, full["iterates"][k_stall - 1])
