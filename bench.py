@@ -136,6 +136,23 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(v, world, device):
+    """Largest value of `v` over the ranks of the default process group (the
+    job's time is its slowest replica's)."""
+    if world == 1:
+        return v
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, elapsed_s):
+    """Replicas: every rank processes the same number of units (weak scaling);
+    the job rate is all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / elapsed_s
+
+
 def oracle_sample_rate(g, nangles=CPU_SAMPLE_ANGLES, gpu_nnz=None):
     """FP64 oracle A x and A^T y on `nangles` angles of the workload; Gupdates/s."""
     import numpy as np
@@ -220,13 +237,6 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     with torch.cuda.stream(s):
         for _ in range(args.warmup):
             step(b, x1, x2, False)
@@ -260,9 +270,9 @@ def run_ours(args):
             ev1.record(s)
             torch.cuda.nvtx.range_pop()
         barrier()
-    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     clocks = clk.summary()
-    value = world * nnz * products / (elapsed_ms * 1e-3) / 1e9
+    value = whole_job_rate(nnz * products, world, elapsed_ms * 1e-3) / 1e9
     lsqr_ips = ITERS * args.steps / lsqr_s
 
     # ---- end to end: b from pinned host memory, x back to host, inside the timed region
@@ -277,8 +287,8 @@ def run_ours(args):
             r1, r2, _ = step(bh, xh1.numpy(), xh2.numpy(), False)
             e2e_products += r1.forward_launches + r1.backward_launches + r2.forward_launches + r2.backward_launches
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = world * nnz * e2e_products / e2e_s / 1e9
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = whole_job_rate(nnz * e2e_products, world, e2e_s) / 1e9
 
     if rank != 0:
         return 0

@@ -1,0 +1,50 @@
+"""The FP64 oracle against its stored regression values (tests/golden/, written
+by tests/golden/make_golden.py from the oracle alone; the paper prints no
+worked example with numbers).  Any change of the oracle's arithmetic shows up
+here and must name the passage of the paper that justifies it."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import krylov
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_regression.json")
+RTOL = 1e-10          # FP64 sums whose grouping may depend on the thread count
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def test_tiny_projector_values(golden):
+    t = golden["tiny"]
+    g = synth.config("tiny")
+    x = synth.ellipsoid_phantom(g, 4, seed=3).astype(np.float64)
+    np.testing.assert_allclose(oracle.project_rays(g, x, np.array(t["rays"])), t["project_rays"], rtol=RTOL)
+    y = synth.random_projections(g, 8)
+    np.testing.assert_allclose(oracle.backproject_voxels(g, y, np.array(t["voxels"])), t["backproject_voxels"],
+                               rtol=RTOL)
+    assert oracle.nnz(g) == t["nnz"]
+
+
+def test_c1_solver_histories(golden):
+    c = golden["c1"]
+    g = synth.config("c1")
+    xt = synth.ellipsoid_phantom(g, 10, seed=0).astype(np.float64)
+    b = oracle.project(g, xt).ravel()
+    op = oracle.Operator(g)
+    for m in ("cgls", "lsqr", "lsmr"):
+        _, h = getattr(krylov, m)(op, b, 6)
+        np.testing.assert_allclose(h["resid"], c[m]["resid"], rtol=RTOL)
+        np.testing.assert_allclose(h["normal_resid"], c[m]["normal_resid"], rtol=RTOL)
+    bn = synth.poisson_log_noise(b, 1e3, seed=5).astype(np.float64)
+    _, h = krylov.hybrid_lsqr(op, bn, 6, rule="gcv")
+    np.testing.assert_allclose(h["lambda"], c["hybrid_gcv_lambda"], rtol=1e-8)
+    _, h = krylov.hybrid_lsqr(op, bn, 6, rule="dp", noise_level=c["dp_noise_level"])
+    np.testing.assert_allclose(h["lambda"], c["hybrid_dp_lambda"], rtol=1e-8)
