@@ -45,8 +45,8 @@ CPU_SAMPLE_ANGLES = 24          # about 20 s of FP64 oracle work on 16 host core
 NCU_TRAFFIC = {
     # one launch of the 2x4x128 transpose tile at 256^3 / 512^2 / 360 (ncu --set full,
     # the cbct_backproject launch of the projectors mode; the solver's launch of the
-    # same tile differs only in the output layout): 7.071 GB read + 0.121 GB written
-    "backward": (7192121000, "6bf8558d2cfed6ce"),
+    # same tile differs only in the output layout): 7.230 GB read + 0.120 GB written
+    "backward": (7350106000, "4956e8f69c1fe615"),
 }
 
 

@@ -221,6 +221,17 @@ cbct_status cbct_lsmr_solve(const cbct_geometry *geom, const float *b, float *x,
 cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *geom, const float *b, float *x,
                                    const cbct_solve_opts *opts, cbct_solve_report *report,
                                    cbct_stream stream);
+/* Hybrid LSMR: the generalisation of the hybrid method to LSMR that Sec. 2.2.2
+ * mentions (replace the projected matrix and right-hand side): Tikhonov on
+ * LSMR's projected problem, y_k = argmin ||alpha_1 beta_1 e_1 - Hbar_k y||^2 +
+ * lambda_k^2 ||y||^2 with Hbar_k = [H_k^T H_k ; alpha_{k+1} beta_{k+1} e_k^T],
+ * x_k = V_k y_k (x_k minimises ||A^T (b - A x)||^2 + lambda_k^2 ||x||^2 over
+ * the Krylov space).  lambda_k fixed or by GCV on that problem
+ * (CBCT_LAMBDA_DP is rejected: it bounds ||r||, not ||A^T r||);
+ * normal_resid_norm receives ||alpha_1 beta_1 e_1 - Hbar_k y_k||. */
+cbct_status cbct_hybrid_lsmr_solve(const cbct_geometry *geom, const float *b, float *x,
+                                   const cbct_solve_opts *opts, cbct_solve_report *report,
+                                   cbct_stream stream);
 
 /* ------------------------------------------------------------------ serving
  * A server reconstructs many scans concurrently on the current CUDA device

@@ -421,6 +421,76 @@ def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False, noise_le
     return x, hist
 
 
+# ------------------------------------------------------------- hybrid LSMR
+def lsmr_projection(alphas, betas, k):
+    """LSMR's projected matrix after k Golub-Kahan steps (Fong-Saunders):
+    A^T A V_k = V_{k+1} Hbar_k with Hbar_k = [H_k^T H_k ; alpha_{k+1} beta_{k+1} e_k^T]
+    ((k+1) x k), and A^T b = alpha_1 beta_1 v_1, so that
+    A^T (b - A V_k y) = V_{k+1} (alpha_1 beta_1 e_1 - Hbar_k y)."""
+    h = _bidiagonal(alphas, betas, k)
+    hb = np.zeros((k + 1, k))
+    hb[:k, :] = h.T @ h
+    hb[k, k - 1] = alphas[k] * betas[k]
+    return hb
+
+
+def hybrid_lsmr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False):
+    """Hybrid LSMR: Tikhonov regularisation of LSMR's projected problem,
+        y_k = argmin ||alpha_1 beta_1 e_1 - Hbar_k y||^2 + lam_k^2 ||y||^2,
+    x_k = V_k y_k, i.e. x_k minimises ||A^T (b - A x)||^2 + lam_k^2 ||x||^2 over
+    K_k(A^T A, A^T b); lam_k fixed or by GCV on the projected problem.  The
+    paper (Sec. 2.2.2) notes that GCV generalises to other Krylov methods such
+    as LSMR by replacing the projected matrix and right-hand side; this is that
+    replacement.  History: ``normal_resid`` = ||alpha_1 beta_1 e_1 - Hbar_k y_k||
+    (= ||A^T r_k|| in exact arithmetic), ``lambda``, ``alpha``/``beta``."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    x = np.zeros(op.shape[1])
+    beta1 = _norm(b)
+    hist = {"normal_resid": [], "lambda": [], "alpha": [], "beta": [beta1], "iterates": []}
+    if beta1 == 0.0:
+        return x, hist
+    u = b / beta1
+    v = op.rmatvec(u)
+    alpha = _norm(v)
+    hist["alpha"].append(alpha)
+    if alpha == 0.0:
+        return x, hist
+    v = v / alpha
+    rhs1 = alpha * beta1
+    basis = [v]
+    for k in range(1, iters + 1):
+        u = op.matvec(v) - alpha * u
+        beta = _norm(u)
+        if beta > 0.0:
+            u = u / beta
+        v = op.rmatvec(u) - beta * v
+        alpha = _norm(v)
+        if alpha > 0.0:
+            v = v / alpha
+        hist["beta"].append(beta)
+        hist["alpha"].append(alpha)
+        hb = lsmr_projection(hist["alpha"], hist["beta"], k)
+        svd = np.linalg.svd(hb, full_matrices=True)
+        if rule == "gcv":
+            lam_k = gcv_lambda(svd[1], svd[0][0, :], rhs1)
+        elif rule == "fixed":
+            lam_k = float(lam)
+        else:
+            raise ValueError(rule)
+        y = projected_tikhonov(hb, rhs1, lam_k, svd)
+        x = np.stack(basis, axis=1) @ y
+        rhs = np.zeros(k + 1)
+        rhs[0] = rhs1
+        hist["normal_resid"].append(_norm(rhs - hb @ y))
+        hist["lambda"].append(lam_k)
+        if keep_iterates:
+            hist["iterates"].append(x.copy())
+        basis.append(v)
+        if beta == 0.0 or alpha == 0.0:
+            break
+    return x, hist
+
+
 # ------------------------------------------- explicit residuals and the stopping rule
 def explicit_residual_stop(op, b, method, iters, stop_tol=0.0, **kw):
     """Run `method` ("cgls", "lsqr", "lsmr" or "hybrid_lsqr") for up to `iters`
@@ -439,7 +509,7 @@ def explicit_residual_stop(op, b, method, iters, stop_tol=0.0, **kw):
     ``stopped`` (True when the rule ended the run early).
     """
     b = np.asarray(b, dtype=np.float64).reshape(-1)
-    fn = {"cgls": cgls, "lsqr": lsqr, "lsmr": lsmr, "hybrid_lsqr": hybrid_lsqr}[method]
+    fn = {"cgls": cgls, "lsqr": lsqr, "lsmr": lsmr, "hybrid_lsqr": hybrid_lsqr, "hybrid_lsmr": hybrid_lsmr}[method]
     x_full, h = fn(op, b, iters, keep_iterates=True, **kw)
     its = h["iterates"]
     resid = []

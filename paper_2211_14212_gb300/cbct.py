@@ -113,7 +113,8 @@ def load(path: str = LIB_PATH):
     lib.cbct_geometry_autotune.argtypes = [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     lib.cbct_geometry_set_angle_block.argtypes = [G, ctypes.c_int]
     lib.cbct_geometry_get_angle_block.argtypes = [G, ctypes.POINTER(ctypes.c_int)]
-    for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve"):
+    for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve",
+               "cbct_hybrid_lsmr_solve"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Report), vp]
     lib.cbct_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(ctypes.c_void_p)]
     lib.cbct_server_submit.argtypes = [vp, ctypes.POINTER(_Desc), vp, ctypes.c_int, ctypes.POINTER(_Opts),
@@ -386,6 +387,12 @@ def hybrid_lsqr(geom, b, iters, rule="gcv", lam=0.0, noise_level=0.0, **kw):
     """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lambda_k fixed, by GCV or by the
     discrepancy principle with relative noise level `noise_level` (Sec. 2.2.2)."""
     return _solve("cbct_hybrid_lsqr_solve", geom, b, iters, lam=lam, rule=rule, noise_level=noise_level, **kw)
+
+
+def hybrid_lsmr(geom, b, iters, rule="gcv", lam=0.0, **kw):
+    """Hybrid LSMR: Tikhonov on LSMR's projected problem, lambda_k fixed or by
+    GCV (the generalisation mentioned in Sec. 2.2.2)."""
+    return _solve("cbct_hybrid_lsmr_solve", geom, b, iters, lam=lam, rule=rule, **kw)
 
 
 # ------------------------------------------------------------------ serving

@@ -1,5 +1,9 @@
 // Projected Tikhonov solve of hybrid LSQR (Sec. 2.2.1, Eq. 8) with the GCV
-// parameter choice (Sec. 2.2.2), in FP64 on one thread block.
+// parameter choice (Sec. 2.2.2), in FP64 on one thread block.  With
+// lsmr_proj the projected problem is LSMR's instead (hybrid LSMR, the
+// generalisation Sec. 2.2.2 mentions): matrix Hbar_k = [H_k^T H_k ;
+// alpha_{k+1} beta_{k+1} e_k^T] and right-hand side alpha_1 beta_1 e_1, so that
+// x_k minimises ||A^T (b - A x)||^2 + lambda^2 ||x||^2 over the Krylov space.
 //
 // At iteration k the Golub-Kahan process has produced the (k+1) x k lower
 // bidiagonal H_k (H[i][i] = alpha_{i+1}, H[i+1][i] = beta_{i+2}).  This kernel
@@ -74,8 +78,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(PS_THREADS)
 projected_solve_kernel(const double *__restrict__ alphas, const double *__restrict__ betas,
                        const double *__restrict__ scales, const int *iter_ptr, const int *stop, int rule,
-                       double lambda_fixed, double noise_level, double *work, int kmax, double *coef,
-                       double *hist_lambda, double *hist_resid) {
+                       double lambda_fixed, double noise_level, int lsmr_proj, double *work, int kmax,
+                       double *coef, double *hist_lambda, double *hist_resid) {
     __shared__ int rotated;
     __shared__ double gvals[GCV_POINTS];
     __shared__ double lam_sh;
@@ -88,11 +92,22 @@ projected_solve_kernel(const double *__restrict__ alphas, const double *__restri
     double *sig = Q + (size_t)k * k;  // k
     double *p1 = sig + k;             // k + 1
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double beta1 = betas[0];
+    // right-hand side beta1 e_1 of the projected problem
+    const double beta1 = lsmr_proj ? alphas[0] * betas[0] : betas[0];
 
     for (int q = tid; q < rows * k; q += PS_THREADS) {
         const int c = q / rows, r = q % rows;
-        B[q] = r == c ? alphas[c] : (r == c + 1 ? betas[c + 1] : 0.0);
+        if (!lsmr_proj) {
+            B[q] = r == c ? alphas[c] : (r == c + 1 ? betas[c + 1] : 0.0);
+        } else if (r < k) {               // (H^T H)[r][c]: tridiagonal
+            double v = 0.0;
+            if (r == c) v = alphas[c] * alphas[c] + betas[c + 1] * betas[c + 1];
+            else if (r == c + 1) v = betas[c + 1] * alphas[c + 1];
+            else if (c == r + 1) v = betas[r + 1] * alphas[r + 1];
+            B[q] = v;
+        } else {                          // last row: alpha_{k+1} beta_{k+1} e_k^T
+            B[q] = c == k - 1 ? alphas[k] * betas[k] : 0.0;
+        }
     }
     for (int q = tid; q < k * k; q += PS_THREADS) Q[q] = (q / k == q % k) ? 1.0 : 0.0;
     __syncthreads();
@@ -154,15 +169,24 @@ projected_solve_kernel(const double *__restrict__ alphas, const double *__restri
             p1[j] = s > 0.0 ? bj[0] / s : 0.0;
         }
     }
+    __syncthreads();
     if (tid == 0) {
-        // null vector of H_k^T, rescaled on the fly; p1[k] = z_0 / ||z||
-        double z = 1.0, z0 = 1.0, ss = 1.0;
-        for (int i = 0; i < k; ++i) {
-            z = -alphas[i] * z / betas[i + 1];
-            ss += z * z;
-            if (ss > 1e200) { z *= 1e-100; z0 *= 1e-100; ss *= 1e-200; }
+        if (!lsmr_proj) {
+            // null vector of H_k^T, rescaled on the fly; p1[k] = z_0 / ||z||
+            double z = 1.0, z0 = 1.0, ss = 1.0;
+            for (int i = 0; i < k; ++i) {
+                z = -alphas[i] * z / betas[i + 1];
+                ss += z * z;
+                if (ss > 1e200) { z *= 1e-100; z0 *= 1e-100; ss *= 1e-200; }
+            }
+            p1[k] = z0 / sqrt(ss);
+        } else {
+            // the first row of the orthogonal P has unit norm: its last entry is
+            // the part of e_1 outside the range of Hbar_k
+            double ss = 0.0;
+            for (int i = 0; i < k; ++i) ss += p1[i] * p1[i];
+            p1[k] = sqrt(fmax(0.0, 1.0 - ss));
         }
-        p1[k] = z0 / sqrt(ss);
     }
     __syncthreads();
 
@@ -245,10 +269,11 @@ projected_solve_kernel(const double *__restrict__ alphas, const double *__restri
 
 cbct_status launch_projected_solve(const double *alphas, const double *betas, const double *scales,
                                    const int *iter, const int *stop, int rule, double lambda_fixed,
-                                   double noise_level, double *work, int kmax, double *coef,
+                                   double noise_level, int lsmr_proj, double *work, int kmax, double *coef,
                                    double *hist_lambda, double *hist_resid, cudaStream_t s) {
     projected_solve_kernel<<<1, PS_THREADS, 0, s>>>(alphas, betas, scales, iter, stop, rule, lambda_fixed,
-                                                     noise_level, work, kmax, coef, hist_lambda, hist_resid);
+                                                     noise_level, lsmr_proj, work, kmax, coef, hist_lambda,
+                                                     hist_resid);
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }

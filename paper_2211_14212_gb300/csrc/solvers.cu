@@ -25,7 +25,7 @@ namespace cbct {
 
 cbct_status launch_projected_solve(const double *alphas, const double *betas, const double *scales,
                                    const int *iter, const int *stop, int rule, double lambda_fixed,
-                                   double noise_level, double *work, int kmax, double *coef,
+                                   double noise_level, int lsmr_proj, double *work, int kmax, double *coef,
                                    double *hist_lambda, double *hist_resid, cudaStream_t s);
 
 // ================================================== explicit residual monitor
@@ -344,7 +344,7 @@ static void copy_report(cbct_solve_report *rep, int done, const std::vector<doub
 
 template <typename T>
 static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
-                            cbct_solve_report *rep, cudaStream_t s, Method method) {
+                            cbct_solve_report *rep, cudaStream_t s, Method method, bool lsmr_proj) {
     const DevGeom &g = geom->dev;
     const int64_t n = cbct_geometry_num_rays(geom), m = cbct_geometry_num_voxels(geom);
     const int iters = o->iters;
@@ -479,8 +479,10 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
         } else if (method == M_LSMR) {
             k_lsmr_update<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, io.xz, w, h2, m, dst);
         } else {
+            // hybrid LSMR's projected residual is the normal-equation residual ||A^T r_k||
             r = launch_projected_solve(alpha_arr, beta_arr, scale_arr, &dst->iter, stop, (int)o->rule, o->lambda,
-                                       o->noise_level, work, iters, coef, hist_l, hist_r, s);
+                                       o->noise_level, lsmr_proj ? 1 : 0, work, iters, coef, hist_l,
+                                       lsmr_proj ? hist_n : hist_r, s);
             if (r != CBCT_OK) return r;
             if (em.on) {                 // the monitor needs x_k itself: x_k = V_k y_k
                 k_combine<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(basis, coef, k + 1, m, io.xz, stop);
@@ -643,7 +645,8 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
 }
 
 static cbct_status dispatch_gk(const cbct_geometry *g, const float *b, float *x, const cbct_solve_opts *o,
-                               cbct_solve_report *rep, cbct_stream stream, Method method) {
+                               cbct_solve_report *rep, cbct_stream stream, Method method,
+                               bool lsmr_proj = false) {
     cbct_status st = check_solve_args(g, b, x, o);
     if (st != CBCT_OK) return st;
     if (method == M_HYBRID && o->rule != CBCT_LAMBDA_FIXED && o->rule != CBCT_LAMBDA_GCV &&
@@ -655,11 +658,15 @@ static cbct_status dispatch_gk(const cbct_geometry *g, const float *b, float *x,
         set_error("hybrid LSQR: the discrepancy principle needs 0 <= noise_level < 1");
         return CBCT_EINVAL;
     }
+    if (lsmr_proj && o->rule == CBCT_LAMBDA_DP) {
+        set_error("hybrid LSMR: lambda by GCV or fixed (the discrepancy principle bounds ||r||, not ||A^T r||)");
+        return CBCT_EINVAL;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     switch (o->storage) {
-    case CBCT_F16: return gk_solve<__half>(g, b, x, o, rep, s, method);
-    case CBCT_BF16: return gk_solve<__nv_bfloat16>(g, b, x, o, rep, s, method);
-    default: return gk_solve<float>(g, b, x, o, rep, s, method);
+    case CBCT_F16: return gk_solve<__half>(g, b, x, o, rep, s, method, lsmr_proj);
+    case CBCT_BF16: return gk_solve<__nv_bfloat16>(g, b, x, o, rep, s, method, lsmr_proj);
+    default: return gk_solve<float>(g, b, x, o, rep, s, method, lsmr_proj);
     }
 }
 
@@ -680,6 +687,11 @@ extern "C" cbct_status cbct_lsmr_solve(const cbct_geometry *g, const float *b, f
 extern "C" cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *g, const float *b, float *x,
                                               const cbct_solve_opts *o, cbct_solve_report *rep, cbct_stream stream) {
     return dispatch_gk(g, b, x, o, rep, stream, M_HYBRID);
+}
+
+extern "C" cbct_status cbct_hybrid_lsmr_solve(const cbct_geometry *g, const float *b, float *x,
+                                              const cbct_solve_opts *o, cbct_solve_report *rep, cbct_stream stream) {
+    return dispatch_gk(g, b, x, o, rep, stream, M_HYBRID, true);
 }
 
 extern "C" cbct_status cbct_cgls_solve(const cbct_geometry *g, const float *b, float *x, const cbct_solve_opts *o,

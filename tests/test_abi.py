@@ -69,7 +69,8 @@ def test_solver_argument_checks(lib):
     from paper_2211_14212_gb300 import cbct
     opts = cbct._Opts(0, 0.0, 0, 0, 0, 0)
     rep = cbct._Report()
-    for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve"):
+    for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve",
+               "cbct_hybrid_lsmr_solve"):
         assert getattr(lib, fn)(None, None, None, ctypes.byref(opts), ctypes.byref(rep), None) == cbct.CBCT_EINVAL
 
 

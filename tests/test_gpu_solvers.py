@@ -346,3 +346,23 @@ def test_explicit_residual_stops_on_stall(cbct, c1_problem, method):
     assert rep.iters_done == len(h["iterates"]) == 7
     _explicit_close(rep.explicit_resid, h["explicit_resid"], b)
     assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+
+
+# ------------------------------------------------ hybrid LSMR (Sec. 2.2.2 generalisation)
+@pytest.mark.parametrize("rule,lam", [("gcv", 0.0), ("fixed", 5.0), ("fixed", 0.0)])
+def test_hybrid_lsmr(cbct, medium_problem, rule, lam):
+    g, _, b = medium_problem
+    geom = cbct.Geometry(g)
+    k = 20
+    x, rep = cbct.hybrid_lsmr(geom, dev(b), k, rule=rule, lam=lam)
+    x_ref, h = oracle_solve(g, b, "hybrid_lsmr", k, rule=rule, lam=lam)
+    assert rep.iters_done == k
+    np.testing.assert_allclose(rep.lam, h["lambda"], rtol=1e-3)
+    np.testing.assert_allclose(rep.normal_resid, h["normal_resid"], rtol=1e-3)
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+
+
+def test_hybrid_lsmr_rejects_dp(cbct, c1_problem):
+    g, _, b = c1_problem
+    with pytest.raises(cbct.CbctError):
+        cbct.hybrid_lsmr(cbct.Geometry(g), dev(b), 5, rule="dp", noise_level=0.01)

@@ -295,3 +295,60 @@ def test_stop_on_stalled_decrease(tiny_system):
     x, h = krylov.explicit_residual_stop(op, b, "cgls", 30, stop_tol=0.1)
     assert h["stopped"] and len(h["iterates"]) == k_stall
     np.testing.assert_array_equal(x, full["iterates"][k_stall - 1])
+
+
+# ------------------------------------------------ hybrid LSMR (Sec. 2.2.2 generalisation)
+def test_hybrid_lsmr_without_regularisation_is_lsmr(tiny_system):
+    """lam = 0: the projected problem is LSMR's own, so x_k is the LSMR iterate."""
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    _, h = krylov.hybrid_lsmr(op, b, 10, rule="fixed", lam=0.0, keep_iterates=True)
+    _, h_ref = krylov.lsmr(op, b, 10, keep_iterates=True)
+    for k in range(10):
+        assert rel(h["iterates"][k], h_ref["iterates"][k]) <= 1e-9
+    np.testing.assert_allclose(h["normal_resid"], h_ref["normal_resid"], rtol=1e-7)
+
+
+@pytest.mark.parametrize("lam", [0.3, 3.0])
+def test_hybrid_lsmr_minimises_tikhonov_normal_residual_over_krylov_space(tiny_system, lam):
+    """Fixed lam: x_k = argmin over K_k of ||A^T (b - A x)||^2 + lam^2 ||x||^2,
+    computed directly on a dense orthonormal basis of K_k."""
+    a, b = tiny_system
+    k = 8
+    x, _ = krylov.hybrid_lsmr(oracle.DenseOperator(a), b, k, rule="fixed", lam=lam)
+    v = krylov.krylov_basis(a, b, k)
+    aug = np.vstack([a.T @ (a @ v), lam * np.eye(k)])
+    rhs = np.concatenate([a.T @ b, np.zeros(k)])
+    z = np.linalg.lstsq(aug, rhs, rcond=None)[0]
+    assert rel(x, v @ z) <= 1e-8
+
+
+def test_lsmr_projection_identity(tiny_system):
+    """A^T A V_k = V_{k+1} Hbar_k on the Golub-Kahan basis."""
+    a, b = tiny_system
+    k = 6
+    beta = np.linalg.norm(b)
+    u = b / beta
+    v = a.T @ u
+    alpha = np.linalg.norm(v)
+    v /= alpha
+    alphas, betas, vs = [alpha], [beta], [v]
+    for _ in range(k):
+        u = a @ v - alpha * u
+        beta = np.linalg.norm(u)
+        u /= beta
+        v = a.T @ u - beta * v
+        alpha = np.linalg.norm(v)
+        v /= alpha
+        alphas.append(alpha)
+        betas.append(beta)
+        vs.append(v)
+    vk, vk1 = np.stack(vs[:k], axis=1), np.stack(vs[:k + 1], axis=1)
+    hb = krylov.lsmr_projection(alphas, betas, k)
+    assert np.linalg.norm(a.T @ (a @ vk) - vk1 @ hb) <= 1e-9 * np.linalg.norm(a) ** 2
+
+
+def test_hybrid_lsmr_gcv_runs(tiny_system):
+    a, b = tiny_system
+    x, h = krylov.hybrid_lsmr(oracle.DenseOperator(a), b, 10, rule="gcv")
+    assert all(l > 0 for l in h["lambda"]) and np.isfinite(x).all()
