@@ -179,6 +179,9 @@ typedef struct {
                                 paper's toolbox stops once the explicit residual increases,
                                 Sec. 3.1.1); costs one product with A per iteration */
     double stop_tol;         /* 0 <= stop_tol < 1; 0 = stop on increase */
+    int gmres_backprojector; /* AB-/BA-GMRES: 0 = B = A^T; 1 = B = C A^T R with the SIRT weights
+                                R = 1 / (A 1), C = 1 / (A^T 1) (a backprojector that is not the
+                                transpose of A) */
 } cbct_solve_opts;
 
 /* Per-iteration histories, written to caller-allocated HOST arrays of length
@@ -221,6 +224,22 @@ cbct_status cbct_lsmr_solve(const cbct_geometry *geom, const float *b, float *x,
 cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *geom, const float *b, float *x,
                                    const cbct_solve_opts *opts, cbct_solve_report *report,
                                    cbct_stream stream);
+/* AB-GMRES and BA-GMRES (Sec. 2.1.4): GMRES with the backprojector B as a
+ * right or left preconditioner, for backprojectors that are not exactly the
+ * transpose of A.  AB: x_k = B z_k with z_k minimising ||b - A B z|| over
+ * K_k(A B, b); BA: x_k minimises ||B (b - A x)|| over K_k(B A, B b).  B is set
+ * by opts->gmres_backprojector; with B = A^T they reach LSQR's (AB) and LSMR's
+ * (BA) iterates in exact arithmetic.  Arnoldi with classical Gram-Schmidt
+ * applied twice (FP64 dots), FP32 Krylov vectors ((iters + 1) of them, rays
+ * for AB, voxels for BA), the Hessenberg least-squares problem in FP64.
+ * resid_norm (AB) or normal_resid_norm (BA) receive the minimised residual per
+ * iteration; iters_done is smaller than iters if the Krylov space is
+ * exhausted.  FP32 storage only; the explicit-residual monitor is rejected. */
+cbct_status cbct_ab_gmres_solve(const cbct_geometry *geom, const float *b, float *x,
+                                const cbct_solve_opts *opts, cbct_solve_report *report, cbct_stream stream);
+cbct_status cbct_ba_gmres_solve(const cbct_geometry *geom, const float *b, float *x,
+                                const cbct_solve_opts *opts, cbct_solve_report *report, cbct_stream stream);
+
 /* Hybrid LSMR: the generalisation of the hybrid method to LSMR that Sec. 2.2.2
  * mentions (replace the projected matrix and right-hand side): Tikhonov on
  * LSMR's projected problem, y_k = argmin ||alpha_1 beta_1 e_1 - Hbar_k y||^2 +

@@ -491,6 +491,95 @@ def hybrid_lsmr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False):
     return x, hist
 
 
+# ------------------------------------------------------------- AB-/BA-GMRES
+def sirt_weights(op):
+    """R = 1 / (A 1) (each ray's length inside the volume) and C = 1 / (A^T 1)
+    (each voxel's total intersection length), 0 where the sum is 0: the
+    diagonal weights of the SIRT family."""
+    m = op.shape[1]
+    row = op.matvec(np.ones(m))
+    col = op.rmatvec(np.ones(op.shape[0]))
+    r = np.where(row > 0, 1.0 / np.where(row > 0, row, 1.0), 0.0)
+    c = np.where(col > 0, 1.0 / np.where(col > 0, col, 1.0), 0.0)
+    return r, c
+
+
+class WeightedBackprojector:
+    """B = C A^T R (SIRT weights): a backprojector that is not the transpose of
+    A, standing in for the approximately matched backprojectors the paper's
+    AB-/BA-GMRES are meant for (Sec. 2.1.4)."""
+
+    def __init__(self, op):
+        self.op = op
+        self.r, self.c = sirt_weights(op)
+
+    def __call__(self, y):
+        return self.c * self.op.rmatvec(self.r * np.asarray(y, dtype=np.float64).reshape(-1))
+
+
+def _arnoldi_gmres(apply, r0, iters):
+    """GMRES on K_k(M, r0) for the operator `apply` = M: Arnoldi with modified
+    Gram-Schmidt in FP64; y_k = argmin ||beta e_1 - Hbar_k y|| for every k.
+    Returns (basis list, [y_k], [||beta e_1 - Hbar_k y_k||])."""
+    beta = _norm(r0)
+    if beta == 0.0:
+        return [], [], []
+    vs = [r0 / beta]
+    h = np.zeros((iters + 1, iters))
+    ys, res = [], []
+    for j in range(iters):
+        w = apply(vs[j])
+        for i in range(j + 1):
+            h[i, j] = float(np.dot(w, vs[i]))
+            w = w - h[i, j] * vs[i]
+        h[j + 1, j] = _norm(w)
+        rhs = np.zeros(j + 2)
+        rhs[0] = beta
+        y = np.linalg.lstsq(h[:j + 2, :j + 1], rhs, rcond=None)[0]
+        ys.append(y)
+        res.append(_norm(rhs - h[:j + 2, :j + 1] @ y))
+        if h[j + 1, j] == 0.0:
+            break
+        vs.append(w / h[j + 1, j])
+    return vs, ys, res
+
+
+def ab_gmres(op, b, iters, backprojector=None, keep_iterates=False):
+    """AB-GMRES (Sec. 2.1.4): GMRES on min ||b - A B z|| (B as a right
+    preconditioner), x_k = B z_k, z_k in K_k(A B, b).  B defaults to A^T, in
+    which case x_k is the LSQR iterate.  History: ``resid`` = ||b - A x_k||
+    from the Hessenberg least-squares problem."""
+    bproj = backprojector or op.rmatvec
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    vs, ys, res = _arnoldi_gmres(lambda z: op.matvec(bproj(z)), b, iters)
+    hist = {"resid": res, "iterates": []}
+    if not ys:
+        return np.zeros(op.shape[1]), hist
+    if keep_iterates:
+        for y in ys:
+            hist["iterates"].append(bproj(np.stack(vs[:len(y)], axis=1) @ y))
+        return hist["iterates"][-1].copy(), hist
+    y = ys[-1]
+    return bproj(np.stack(vs[:len(y)], axis=1) @ y), hist
+
+
+def ba_gmres(op, b, iters, backprojector=None, keep_iterates=False):
+    """BA-GMRES (Sec. 2.1.4): GMRES on min ||B (b - A x)|| (B as a left
+    preconditioner), x_k in K_k(B A, B b).  B defaults to A^T, in which case
+    x_k is the LSMR iterate.  History: ``resid`` = ||B (b - A x_k)||."""
+    bproj = backprojector or op.rmatvec
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    vs, ys, res = _arnoldi_gmres(lambda x: bproj(op.matvec(x)), bproj(b), iters)
+    hist = {"resid": res, "iterates": []}
+    if not ys:
+        return np.zeros(op.shape[1]), hist
+    for y in (ys if keep_iterates else ys[-1:]):
+        x = np.stack(vs[:len(y)], axis=1) @ y
+        if keep_iterates:
+            hist["iterates"].append(x)
+    return x.copy(), hist
+
+
 # ------------------------------------------- explicit residuals and the stopping rule
 def explicit_residual_stop(op, b, method, iters, stop_tol=0.0, **kw):
     """Run `method` ("cgls", "lsqr", "lsmr" or "hybrid_lsqr") for up to `iters`

@@ -46,7 +46,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("lam", ctypes.c_double), ("rule", ctypes.c_int),
                 ("storage", ctypes.c_int), ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
                 ("noise_level", ctypes.c_double), ("explicit_residual", ctypes.c_int),
-                ("stop_tol", ctypes.c_double)]
+                ("stop_tol", ctypes.c_double), ("gmres_backprojector", ctypes.c_int)]
 
 
 class _Report(ctypes.Structure):
@@ -114,7 +114,7 @@ def load(path: str = LIB_PATH):
     lib.cbct_geometry_set_angle_block.argtypes = [G, ctypes.c_int]
     lib.cbct_geometry_get_angle_block.argtypes = [G, ctypes.POINTER(ctypes.c_int)]
     for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve",
-               "cbct_hybrid_lsmr_solve"):
+               "cbct_hybrid_lsmr_solve", "cbct_ab_gmres_solve", "cbct_ba_gmres_solve"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Report), vp]
     lib.cbct_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(ctypes.c_void_p)]
     lib.cbct_server_submit.argtypes = [vp, ctypes.POINTER(_Desc), vp, ctypes.c_int, ctypes.POINTER(_Opts),
@@ -324,7 +324,7 @@ class SolveReport:
 
 
 def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=True, x=None, stream=None,
-           profile=False, noise_level=0.0, explicit_residual=False, stop_tol=0.0):
+           profile=False, noise_level=0.0, explicit_residual=False, stop_tol=0.0, backprojector="transpose"):
     """Run one of the C-ABI solvers.  b/x may be CUDA tensors or host (numpy or
     CPU torch, FP32) buffers; host buffers are staged by the library."""
     import torch
@@ -351,7 +351,8 @@ def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=Tru
     rule_code = ({"fixed": LAMBDA_FIXED, "gcv": LAMBDA_GCV, "dp": LAMBDA_DP}[rule] if isinstance(rule, str)
                  else int(rule))
     opts = _Opts(int(iters), float(lam), rule_code, STORAGE[storage], 1 if use_graph else 0, 1 if profile else 0,
-                 float(noise_level), 1 if explicit_residual else 0, float(stop_tol))
+                 float(noise_level), 1 if explicit_residual else 0, float(stop_tol),
+                 {"transpose": 0, "sirt": 1}[backprojector])
     hr = np.zeros(iters, dtype=np.float64)
     hn = np.zeros(iters, dtype=np.float64)
     hl = np.zeros(iters, dtype=np.float64)
@@ -387,6 +388,17 @@ def hybrid_lsqr(geom, b, iters, rule="gcv", lam=0.0, noise_level=0.0, **kw):
     """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lambda_k fixed, by GCV or by the
     discrepancy principle with relative noise level `noise_level` (Sec. 2.2.2)."""
     return _solve("cbct_hybrid_lsqr_solve", geom, b, iters, lam=lam, rule=rule, noise_level=noise_level, **kw)
+
+
+def ab_gmres(geom, b, iters, backprojector="transpose", **kw):
+    """AB-GMRES (Sec. 2.1.4); backprojector "transpose" (B = A^T) or "sirt"
+    (B = C A^T R with the SIRT weights)."""
+    return _solve("cbct_ab_gmres_solve", geom, b, iters, backprojector=backprojector, **kw)
+
+
+def ba_gmres(geom, b, iters, backprojector="transpose", **kw):
+    """BA-GMRES (Sec. 2.1.4); backprojector as for ab_gmres."""
+    return _solve("cbct_ba_gmres_solve", geom, b, iters, backprojector=backprojector, **kw)
 
 
 def hybrid_lsmr(geom, b, iters, rule="gcv", lam=0.0, **kw):

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -207,6 +208,83 @@ cbct_status run_iterations(int iters, bool use_graph, cudaStream_t s, F &&enqueu
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize");
     return CBCT_OK;
+}
+
+// ------------------------------------------------- solver input / output
+//
+// The solvers keep b v-fastest and the iterate z-fastest; host buffers are
+// staged through device memory.
+
+struct SolveIO {
+    const float *b_dev;   // b re-laid v-fastest, y[a][iu][iv], like the projection-side vectors
+    float *x_dev;         // caller layout x[k][j][i] (device; staging buffer for host x)
+    float *xz;            // the iterate in the solvers' z-fastest layout x[j][i][k]
+    bool x_is_host;
+    float *x_host;
+};
+
+inline cbct_status check_solve_args(const cbct_geometry *g, const float *b, float *x, const cbct_solve_opts *o) {
+    if (!g || !b || !x || !o) { set_error("solver: null argument"); return CBCT_EINVAL; }
+    if (o->iters < 1) { set_error("solver: iters must be >= 1"); return CBCT_EINVAL; }
+    if (o->storage != CBCT_F32 && o->storage != CBCT_F16 && o->storage != CBCT_BF16) {
+        set_error("solver: unknown storage type");
+        return CBCT_EINVAL;
+    }
+    if (!(o->lambda >= 0.0) || !std::isfinite(o->lambda)) { set_error("solver: lambda must be finite and >= 0"); return CBCT_EINVAL; }
+    if (o->explicit_residual && !(o->stop_tol >= 0.0 && o->stop_tol < 1.0)) {
+        set_error("solver: stop_tol must be in [0, 1)");
+        return CBCT_EINVAL;
+    }
+    return CBCT_OK;
+}
+
+// Stage host b / x through device memory when needed.
+inline cbct_status setup_io(const cbct_geometry *g, const float *b, float *x, Workspace &ws, SolveIO &io) {
+    const int64_t n = cbct_geometry_num_rays(g), m = cbct_geometry_num_voxels(g);
+    io.x_dev = x;
+    io.x_is_host = false;
+    io.x_host = nullptr;
+    const float *bsrc = b;
+    if (!is_device_pointer(b)) {
+        float *bd = nullptr;
+        CBCT_CUDA_TRY(ws.alloc(&bd, (size_t)n));
+        CBCT_CUDA_TRY(cudaMemcpyAsync(bd, b, sizeof(float) * n, cudaMemcpyHostToDevice, ws.s));
+        bsrc = bd;
+    }
+    float *bv = nullptr;
+    CBCT_CUDA_TRY(ws.alloc(&bv, (size_t)n));
+    cbct_status st = launch_proj_relayout(g->dev, bsrc, bv, CBCT_F32, true, ws.s);
+    if (st != CBCT_OK) return st;
+    io.b_dev = bv;
+    if (!is_device_pointer(x)) {
+        float *xd = nullptr;
+        CBCT_CUDA_TRY(ws.alloc(&xd, (size_t)m));
+        io.x_dev = xd;
+        io.x_is_host = true;
+        io.x_host = x;
+    }
+    CBCT_CUDA_TRY(ws.alloc(&io.xz, (size_t)m));
+    CBCT_CUDA_TRY(cudaMemsetAsync(io.xz, 0, sizeof(float) * m, ws.s));
+    return CBCT_OK;
+}
+
+// x (caller layout) <- the z-fastest iterate; then to the host if x is a host buffer.
+inline cbct_status finish_io(const cbct_geometry *g, SolveIO &io, cudaStream_t s) {
+    cbct_status st = launch_relayout(g->dev, io.xz, io.x_dev, CBCT_F32, false, s);
+    if (st != CBCT_OK) return st;
+    if (io.x_is_host)
+        CBCT_CUDA_TRY(cudaMemcpyAsync(io.x_host, io.x_dev, sizeof(float) * cbct_geometry_num_voxels(g),
+                                      cudaMemcpyDeviceToHost, s));
+    return CBCT_OK;
+}
+
+inline void copy_report(cbct_solve_report *rep, int done, const std::vector<double> &h, int iters) {
+    if (!rep) return;
+    rep->iters_done = done;
+    const int c = done < iters ? done : iters;
+    if (rep->resid_norm) std::memcpy(rep->resid_norm, h.data(), sizeof(double) * c);
+    if (rep->normal_resid_norm) std::memcpy(rep->normal_resid_norm, h.data() + iters, sizeof(double) * c);
+    if (rep->lambda_k) std::memcpy(rep->lambda_k, h.data() + 2 * iters, sizeof(double) * c);
 }
 
 }  // namespace cbct

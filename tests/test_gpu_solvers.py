@@ -366,3 +366,24 @@ def test_hybrid_lsmr_rejects_dp(cbct, c1_problem):
     g, _, b = c1_problem
     with pytest.raises(cbct.CbctError):
         cbct.hybrid_lsmr(cbct.Geometry(g), dev(b), 5, rule="dp", noise_level=0.01)
+
+
+# ------------------------------------------------------ AB-/BA-GMRES (Sec. 2.1.4)
+@pytest.mark.parametrize("variant", ["ab", "ba"])
+@pytest.mark.parametrize("backprojector", ["transpose", "sirt"])
+def test_gmres(cbct, c1_problem, variant, backprojector):
+    """GMRES with B = A^T or the SIRT-weighted B = C A^T R against the oracle's
+    Arnoldi/least-squares GMRES: iterate and minimised residual after 10
+    iterations, residual history non-increasing."""
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    k = 10
+    x, rep = getattr(cbct, variant + "_gmres")(geom, dev(b), k, backprojector=backprojector)
+    op = oracle.Operator(g)
+    bp = krylov.WeightedBackprojector(op) if backprojector == "sirt" else None
+    x_ref, h = getattr(krylov, variant + "_gmres")(op, b, k, backprojector=bp)
+    assert rep.iters_done == k
+    hist = rep.resid if variant == "ab" else rep.normal_resid
+    np.testing.assert_allclose(hist, h["resid"], rtol=1e-4)
+    assert np.all(np.diff(hist) <= 1e-6 * hist[0])
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL

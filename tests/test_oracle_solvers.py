@@ -352,3 +352,58 @@ def test_hybrid_lsmr_gcv_runs(tiny_system):
     a, b = tiny_system
     x, h = krylov.hybrid_lsmr(oracle.DenseOperator(a), b, 10, rule="gcv")
     assert all(l > 0 for l in h["lambda"]) and np.isfinite(x).all()
+
+
+# ------------------------------------------------------ AB-/BA-GMRES (Sec. 2.1.4)
+def test_ab_gmres_with_the_transpose_is_lsqr(tiny_system):
+    """B = A^T: min ||b - A A^T z|| over K_k(A A^T, b) is LSQR's problem."""
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    _, h = krylov.ab_gmres(op, b, 10, keep_iterates=True)
+    _, h_ref = krylov.lsqr(op, b, 10, keep_iterates=True)
+    for k in range(10):
+        assert rel(h["iterates"][k], h_ref["iterates"][k]) <= 1e-8
+    np.testing.assert_allclose(h["resid"], h_ref["resid"], rtol=1e-8)
+
+
+def test_ba_gmres_with_the_transpose_is_lsmr(tiny_system):
+    """B = A^T: min ||A^T (b - A x)|| over K_k(A^T A, A^T b) is LSMR's problem."""
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    _, h = krylov.ba_gmres(op, b, 10, keep_iterates=True)
+    _, h_ref = krylov.lsmr(op, b, 10, keep_iterates=True)
+    for k in range(10):
+        assert rel(h["iterates"][k], h_ref["iterates"][k]) <= 1e-8
+    np.testing.assert_allclose(h["resid"], h_ref["normal_resid"], rtol=1e-7)
+
+
+@pytest.mark.parametrize("variant", ["ab", "ba"])
+def test_gmres_with_unmatched_backprojector_minimises_over_krylov_space(tiny_system, variant):
+    """B = C A^T R (SIRT weights, B != A^T): the iterate is the minimiser of the
+    GMRES objective over the Krylov space, computed on a dense basis; the
+    residual never increases."""
+    a, b = tiny_system
+    op = oracle.DenseOperator(a)
+    bw = krylov.WeightedBackprojector(op)
+    bm = np.diag(bw.c) @ a.T @ np.diag(bw.r)
+    assert np.linalg.norm(bm - a.T) > 0.1 * np.linalg.norm(a)
+    k = 7
+    if variant == "ab":
+        x, h = krylov.ab_gmres(op, b, k, backprojector=bw)
+        m_op, r0 = a @ bm, b
+    else:
+        x, h = krylov.ba_gmres(op, b, k, backprojector=bw)
+        m_op, r0 = bm @ a, bm @ b
+    # dense orthonormal basis of K_k(M, r0)
+    q = np.zeros((r0.size, k))
+    v = r0 / np.linalg.norm(r0)
+    for j in range(k):
+        q[:, j] = v
+        v = m_op @ v
+        for _ in range(2):
+            v = v - q[:, :j + 1] @ (q[:, :j + 1].T @ v)
+        v = v / np.linalg.norm(v)
+    z = np.linalg.lstsq(m_op @ q, r0, rcond=None)[0]
+    ref = bm @ (q @ z) if variant == "ab" else q @ z
+    assert rel(x, ref) <= 1e-7
+    assert np.all(np.diff(h["resid"]) <= 1e-12 * h["resid"][0])
