@@ -182,6 +182,9 @@ typedef struct {
     int gmres_backprojector; /* AB-/BA-GMRES: 0 = B = A^T; 1 = B = C A^T R with the SIRT weights
                                 R = 1 / (A 1), C = 1 / (A^T 1) (a backprojector that is not the
                                 transpose of A) */
+    int tv_outer;            /* CGLS-TV: reweighting (outer) steps, 1 <= tv_outer <= iters; the
+                                iters CGLS iterations are spread evenly over them */
+    double tv_tau;           /* CGLS-TV: smoothing tau > 0 of the weights (|D x|^2 + tau^2)^(-1/4) */
 } cbct_solve_opts;
 
 /* Per-iteration histories, written to caller-allocated HOST arrays of length
@@ -224,6 +227,18 @@ cbct_status cbct_lsmr_solve(const cbct_geometry *geom, const float *b, float *x,
 cbct_status cbct_hybrid_lsqr_solve(const cbct_geometry *geom, const float *b, float *x,
                                    const cbct_solve_opts *opts, cbct_solve_report *report,
                                    cbct_stream stream);
+/* CGLS-TV (Sec. 2.3.1): isotropic 3D total variation by iteratively
+ * reweighted norms.  Each of the tv_outer steps fixes the weights
+ * W = diag((|D x|^2 + tv_tau^2)^(-1/4)) from the current x (uniform at x_0 = 0)
+ * and runs CGLS on min ||A x - b||^2 + lambda^2 ||W D x||^2 from the current x,
+ * with D the forward-difference gradient (zero last difference, Neumann
+ * boundary) along i, j, k; lambda is opts->lambda.  resid_norm receives
+ * ||b - A x|| and normal_resid_norm the stacked system's normal residual after
+ * every CGLS iteration; an outer step ends early once that normal residual
+ * falls to 1e-14 of its start.  FP32 storage only. */
+cbct_status cbct_cgls_tv_solve(const cbct_geometry *geom, const float *b, float *x,
+                               const cbct_solve_opts *opts, cbct_solve_report *report, cbct_stream stream);
+
 /* AB-GMRES and BA-GMRES (Sec. 2.1.4): GMRES with the backprojector B as a
  * right or left preconditioner, for backprojectors that are not exactly the
  * transpose of A.  AB: x_k = B z_k with z_k minimising ||b - A B z|| over

@@ -46,7 +46,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("lam", ctypes.c_double), ("rule", ctypes.c_int),
                 ("storage", ctypes.c_int), ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
                 ("noise_level", ctypes.c_double), ("explicit_residual", ctypes.c_int),
-                ("stop_tol", ctypes.c_double), ("gmres_backprojector", ctypes.c_int)]
+                ("stop_tol", ctypes.c_double), ("gmres_backprojector", ctypes.c_int),
+                ("tv_outer", ctypes.c_int), ("tv_tau", ctypes.c_double)]
 
 
 class _Report(ctypes.Structure):
@@ -114,7 +115,7 @@ def load(path: str = LIB_PATH):
     lib.cbct_geometry_set_angle_block.argtypes = [G, ctypes.c_int]
     lib.cbct_geometry_get_angle_block.argtypes = [G, ctypes.POINTER(ctypes.c_int)]
     for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve",
-               "cbct_hybrid_lsmr_solve", "cbct_ab_gmres_solve", "cbct_ba_gmres_solve"):
+               "cbct_hybrid_lsmr_solve", "cbct_ab_gmres_solve", "cbct_ba_gmres_solve", "cbct_cgls_tv_solve"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Report), vp]
     lib.cbct_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(ctypes.c_void_p)]
     lib.cbct_server_submit.argtypes = [vp, ctypes.POINTER(_Desc), vp, ctypes.c_int, ctypes.POINTER(_Opts),
@@ -324,7 +325,8 @@ class SolveReport:
 
 
 def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=True, x=None, stream=None,
-           profile=False, noise_level=0.0, explicit_residual=False, stop_tol=0.0, backprojector="transpose"):
+           profile=False, noise_level=0.0, explicit_residual=False, stop_tol=0.0, backprojector="transpose",
+           tv_outer=1, tv_tau=1e-3):
     """Run one of the C-ABI solvers.  b/x may be CUDA tensors or host (numpy or
     CPU torch, FP32) buffers; host buffers are staged by the library."""
     import torch
@@ -352,7 +354,7 @@ def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=Tru
                  else int(rule))
     opts = _Opts(int(iters), float(lam), rule_code, STORAGE[storage], 1 if use_graph else 0, 1 if profile else 0,
                  float(noise_level), 1 if explicit_residual else 0, float(stop_tol),
-                 {"transpose": 0, "sirt": 1}[backprojector])
+                 {"transpose": 0, "sirt": 1}[backprojector], int(tv_outer), float(tv_tau))
     hr = np.zeros(iters, dtype=np.float64)
     hn = np.zeros(iters, dtype=np.float64)
     hl = np.zeros(iters, dtype=np.float64)
@@ -388,6 +390,12 @@ def hybrid_lsqr(geom, b, iters, rule="gcv", lam=0.0, noise_level=0.0, **kw):
     """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lambda_k fixed, by GCV or by the
     discrepancy principle with relative noise level `noise_level` (Sec. 2.2.2)."""
     return _solve("cbct_hybrid_lsqr_solve", geom, b, iters, lam=lam, rule=rule, noise_level=noise_level, **kw)
+
+
+def cgls_tv(geom, b, iters, lam, outer, tau=1e-3, **kw):
+    """CGLS-TV (Sec. 2.3.1): `outer` reweighting steps sharing `iters` CGLS
+    iterations on min ||A x - b||^2 + lam^2 ||W D x||^2."""
+    return _solve("cbct_cgls_tv_solve", geom, b, iters, lam=lam, tv_outer=outer, tv_tau=tau, **kw)
 
 
 def ab_gmres(geom, b, iters, backprojector="transpose", **kw):

@@ -70,7 +70,7 @@ def test_solver_argument_checks(lib):
     opts = cbct._Opts(0, 0.0, 0, 0, 0, 0)
     rep = cbct._Report()
     for fn in ("cbct_cgls_solve", "cbct_lsqr_solve", "cbct_lsmr_solve", "cbct_hybrid_lsqr_solve",
-               "cbct_hybrid_lsmr_solve", "cbct_ab_gmres_solve", "cbct_ba_gmres_solve"):
+               "cbct_hybrid_lsmr_solve", "cbct_ab_gmres_solve", "cbct_ba_gmres_solve", "cbct_cgls_tv_solve"):
         assert getattr(lib, fn)(None, None, None, ctypes.byref(opts), ctypes.byref(rep), None) == cbct.CBCT_EINVAL
 
 

@@ -387,3 +387,23 @@ def test_gmres(cbct, c1_problem, variant, backprojector):
     np.testing.assert_allclose(hist, h["resid"], rtol=1e-4)
     assert np.all(np.diff(hist) <= 1e-6 * hist[0])
     assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+
+
+# ------------------------------------------------------------ CGLS-TV (Sec. 2.3.1)
+def test_cgls_tv(cbct, c1_problem):
+    """3 reweighting steps of 5 CGLS iterations each on min ||A x - b||^2 +
+    lam^2 ||W D x||^2: iterate and the residual at the end of every outer step
+    as the oracle's IRN scheme."""
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    lam, tau, outer, inner = 2.0, 1e-2, 3, 5
+    x, rep = cbct.cgls_tv(geom, dev(b), outer * inner, lam, outer, tau)
+    x_ref, h = krylov.cgls_tv(oracle.Operator(g), g.vol_shape, b, outer, inner, lam, tau)
+    assert rep.iters_done == outer * inner
+    ends = rep.resid[inner - 1::inner]
+    np.testing.assert_allclose(ends, h["resid"], rtol=1e-4)
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+    # the TV term did something: less total variation than plain CGLS after the same iterations
+    x_cg, _ = cbct.cgls(geom, dev(b), outer * inner)
+    assert krylov.total_variation(x.cpu().numpy().astype(np.float64)) < \
+        krylov.total_variation(x_cg.cpu().numpy().astype(np.float64))

@@ -407,3 +407,59 @@ def test_gmres_with_unmatched_backprojector_minimises_over_krylov_space(tiny_sys
     ref = bm @ (q @ z) if variant == "ab" else q @ z
     assert rel(x, ref) <= 1e-7
     assert np.all(np.diff(h["resid"]) <= 1e-12 * h["resid"][0])
+
+
+# ------------------------------------------------------------ CGLS-TV (Sec. 2.3)
+def test_gradient_adjoint_and_tv_closed_form():
+    rng = np.random.default_rng(41)
+    x = rng.standard_normal((5, 6, 7))
+    u = rng.standard_normal((3, 5, 6, 7))
+    lhs = float(np.sum(krylov.grad3(x) * u))
+    rhs = float(np.sum(x * krylov.grad3_adjoint(u)))
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(u)
+    # a unit cube of ones inside zeros: TV counts the jumps across its faces;
+    # a voxel next to the cube on its + side along one axis sees one jump of 1,
+    # a voxel inside on the - faces sees jumps toward the outside
+    c = np.zeros((6, 6, 6))
+    c[2:4, 2:4, 2:4] = 1.0
+    d = krylov.grad3(c)
+    mag = np.sqrt(np.sum(d * d, axis=0))
+    assert abs(krylov.total_variation(c) - float(mag.sum())) <= 1e-12
+    # brute force by the definition, voxel by voxel
+    tv = 0.0
+    for k in range(6):
+        for j in range(6):
+            for i in range(6):
+                gi = c[k, j, i + 1] - c[k, j, i] if i < 5 else 0.0
+                gj = c[k, j + 1, i] - c[k, j, i] if j < 5 else 0.0
+                gk = c[k + 1, j, i] - c[k, j, i] if k < 5 else 0.0
+                tv += np.sqrt(gi * gi + gj * gj + gk * gk)
+    assert abs(krylov.total_variation(c) - tv) <= 1e-12
+
+
+def test_cgls_tv_inner_solve_is_the_weighted_tikhonov_solution(tiny_system):
+    """One outer step with enough inner iterations reaches the solution of the
+    normal equations (A^T A + lam^2 D^T W^2 D) x = A^T b (dense solve)."""
+    a, b = tiny_system
+    g = synth.config("tiny")
+    shape = g.vol_shape
+    lam, tau = 0.5, 1e-2
+    x, _ = krylov.cgls_tv(oracle.DenseOperator(a), shape, b, 1, 1000, lam, tau)
+    m = a.shape[1]
+    eye = np.eye(m)
+    dmat = np.stack([krylov.grad3(eye[:, c].reshape(shape)).ravel() for c in range(m)], axis=1)   # (3M, M)
+    w = krylov.irn_weights(np.zeros(shape), tau).ravel()
+    w3 = np.concatenate([w, w, w])
+    lhs = a.T @ a + lam * lam * dmat.T @ (w3[:, None] ** 2 * dmat)
+    x_ref = np.linalg.solve(lhs, a.T @ b)
+    assert rel(x.ravel(), x_ref) <= 1e-6
+
+
+def test_cgls_tv_objective_decreases(tiny_system):
+    """IRN is a majorise-minimise scheme: with (nearly) exact inner solves the
+    TV objective ||A x - b||^2 + lam^2 TV(x) does not increase."""
+    a, b = tiny_system
+    shape = synth.config("tiny").vol_shape
+    _, h = krylov.cgls_tv(oracle.DenseOperator(a), shape, b, 6, 150, 0.5, 1e-3)
+    obj = h["objective"]
+    assert all(o2 <= o1 * (1 + 1e-6) for o1, o2 in zip(obj, obj[1:]))
