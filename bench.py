@@ -38,6 +38,7 @@ ITERS = 30
 I0 = 1e5
 BYTES_PER_UPDATE = 4          # one FP32 voxel (forward) or projection (backward) value per ray-voxel update
 CPU_SAMPLE_ANGLES = 24          # about 20 s of FP64 oracle work on 16 host cores
+REF_STEP_ANGLES = 8             # --impl reference: about 7 s per step, so K steps stay within minutes
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by the projector sources it was measured on (projector_hash()); the
@@ -182,11 +183,11 @@ def run_reference(args):
     vals, times = [], []
     cores = nnz = None
     for _ in range(args.steps):
-        v, cores, dt, nnz = oracle_sample_rate(g, CPU_SAMPLE_ANGLES)
+        v, cores, dt, nnz = oracle_sample_rate(g, REF_STEP_ANGLES)
         vals.append(v)
         times.append(dt)
     value = sum(2 * nnz for _ in times) / sum(times) / 1e9
-    sample = "FP64 oracle A x + A^T y on %d of %d angles (%d updates each)" % (CPU_SAMPLE_ANGLES, g.nangles, nnz)
+    sample = "FP64 oracle A x + A^T y on %d of %d angles (%d updates each)" % (REF_STEP_ANGLES, g.nangles, nnz)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
