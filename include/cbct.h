@@ -185,6 +185,10 @@ typedef struct {
     int tv_outer;            /* CGLS-TV: reweighting (outer) steps, 1 <= tv_outer <= iters; the
                                 iters CGLS iterations are spread evenly over them */
     double tv_tau;           /* CGLS-TV: smoothing tau > 0 of the weights (|D x|^2 + tau^2)^(-1/4) */
+    int reorth;              /* LSQR, LSMR, hybrid LSQR/LSMR: nonzero = re-orthogonalise every new
+                                u and v against all earlier ones (classical Gram-Schmidt twice,
+                                FP64 dots; Sec. 3.1.1 and Sec. 4), keeping (iters + 1) normalised
+                                vectors of each kind; FP32 storage only */
 } cbct_solve_opts;
 
 /* Per-iteration histories, written to caller-allocated HOST arrays of length

@@ -35,6 +35,19 @@ def _norm(v):
     return float(np.sqrt(np.dot(v, v)))
 
 
+def _reorthogonalise(vec, basis):
+    """Classical Gram-Schmidt against the stored orthonormal vectors, applied
+    twice ("twice is enough"): removes the components along earlier Krylov
+    vectors that rounding reintroduces (the re-orthogonalisation the paper
+    discusses for LSQR-type methods, Sec. 3.1.1 and Sec. 4)."""
+    if not basis:
+        return vec
+    q = np.stack(basis, axis=1)
+    for _ in range(2):
+        vec = vec - q @ (q.T @ vec)
+    return vec
+
+
 def _rotation(a, b):
     """Givens rotation (c, s, r) with [c s; -s c] [a; b] = [r; 0], r = hypot(a, b) >= 0."""
     r = math.hypot(a, b)
@@ -80,7 +93,7 @@ def cgls(op, b, iters, damp=0.0, keep_iterates=False):
 
 
 # --------------------------------------------------------------------------- LSQR
-def lsqr(op, b, iters, damp=0.0, keep_iterates=False):
+def lsqr(op, b, iters, damp=0.0, keep_iterates=False, reorth=False):
     """LSQR (Sec. 2.1.2): Golub-Kahan bidiagonalisation + Paige-Saunders recurrences.
 
     Bidiagonalisation: beta_1 u_1 = b, alpha_1 v_1 = A^T u_1,
@@ -100,25 +113,35 @@ def lsqr(op, b, iters, damp=0.0, keep_iterates=False):
     if beta == 0.0:
         return x, hist
     u = b / beta
+    ub = [u] if reorth else []
     v = op.rmatvec(u)
     alpha = _norm(v)
     hist["alpha"].append(alpha)
     if alpha == 0.0:
         return x, hist
     v = v / alpha
+    vb = [v] if reorth else []
     w = v.copy()
     phibar = beta
     rhobar = alpha
     psi_sq = 0.0
     for _ in range(iters):
         u = op.matvec(v) - alpha * u
+        if reorth:
+            u = _reorthogonalise(u, ub)
         beta = _norm(u)
         if beta > 0.0:
             u = u / beta
+        if reorth:
+            ub.append(u)
         v = op.rmatvec(u) - beta * v
+        if reorth:
+            v = _reorthogonalise(v, vb)
         alpha_next = _norm(v)
         if alpha_next > 0.0:
             v = v / alpha_next
+        if reorth:
+            vb.append(v)
         hist["beta"].append(beta)
         hist["alpha"].append(alpha_next)
         # rotation that eliminates the damping term
@@ -145,7 +168,7 @@ def lsqr(op, b, iters, damp=0.0, keep_iterates=False):
 
 
 # --------------------------------------------------------------------------- LSMR
-def lsmr(op, b, iters, damp=0.0, keep_iterates=False):
+def lsmr(op, b, iters, damp=0.0, keep_iterates=False, reorth=False):
     """LSMR (Sec. 2.1.3): Golub-Kahan + Fong-Saunders recurrences.
 
     x_k minimises ||A^T r_k|| (of the damped system when damp = lam) over
@@ -163,11 +186,13 @@ def lsmr(op, b, iters, damp=0.0, keep_iterates=False):
     if beta == 0.0:
         return x, hist
     u = b / beta
+    ub = [u] if reorth else []
     v = op.rmatvec(u)
     alpha = _norm(v)
     if alpha == 0.0:
         return x, hist
     v = v / alpha
+    vb = [v] if reorth else []
 
     alphabar = alpha
     zetabar = alpha * beta
@@ -187,13 +212,21 @@ def lsmr(op, b, iters, damp=0.0, keep_iterates=False):
 
     for _ in range(iters):
         u = op.matvec(v) - alpha * u
+        if reorth:
+            u = _reorthogonalise(u, ub)
         beta = _norm(u)
         if beta > 0.0:
             u = u / beta
+        if reorth:
+            ub.append(u)
         v = op.rmatvec(u) - beta * v
+        if reorth:
+            v = _reorthogonalise(v, vb)
         alpha = _norm(v)
         if alpha > 0.0:
             v = v / alpha
+        if reorth:
+            vb.append(v)
 
         chat, shat, alphahat = _rotation(alphabar, lam)          # P-hat_k
         rho_prev = rho
@@ -363,7 +396,7 @@ def projected_tikhonov(h, beta1, lam, svd=None):
     return qt.T @ coef
 
 
-def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False, noise_level=0.0):
+def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False, noise_level=0.0, reorth=False):
     """Hybrid LSQR (Sec. 2.2.1, Eq. 8) with lam_k fixed, chosen by GCV or by the
     discrepancy principle with relative noise level nl = noise_level (Sec. 2.2.2).
 
@@ -379,22 +412,32 @@ def hybrid_lsqr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False, noise_le
     if beta1 == 0.0:
         return x, hist
     u = b / beta1
+    ub = [u] if reorth else []
     v = op.rmatvec(u)
     alpha = _norm(v)
     hist["alpha"].append(alpha)
     if alpha == 0.0:
         return x, hist
     v = v / alpha
+    vb = [v] if reorth else []
     basis = [v]
     for k in range(1, iters + 1):
         u = op.matvec(v) - alpha * u
+        if reorth:
+            u = _reorthogonalise(u, ub)
         beta = _norm(u)
         if beta > 0.0:
             u = u / beta
+        if reorth:
+            ub.append(u)
         v = op.rmatvec(u) - beta * v
+        if reorth:
+            v = _reorthogonalise(v, vb)
         alpha = _norm(v)
         if alpha > 0.0:
             v = v / alpha
+        if reorth:
+            vb.append(v)
         hist["beta"].append(beta)
         hist["alpha"].append(alpha)
         h = _bidiagonal(hist["alpha"], hist["beta"], k)

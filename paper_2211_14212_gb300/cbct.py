@@ -47,7 +47,7 @@ class _Opts(ctypes.Structure):
                 ("storage", ctypes.c_int), ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
                 ("noise_level", ctypes.c_double), ("explicit_residual", ctypes.c_int),
                 ("stop_tol", ctypes.c_double), ("gmres_backprojector", ctypes.c_int),
-                ("tv_outer", ctypes.c_int), ("tv_tau", ctypes.c_double)]
+                ("tv_outer", ctypes.c_int), ("tv_tau", ctypes.c_double), ("reorth", ctypes.c_int)]
 
 
 class _Report(ctypes.Structure):
@@ -326,7 +326,7 @@ class SolveReport:
 
 def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=True, x=None, stream=None,
            profile=False, noise_level=0.0, explicit_residual=False, stop_tol=0.0, backprojector="transpose",
-           tv_outer=1, tv_tau=1e-3):
+           tv_outer=1, tv_tau=1e-3, reorth=False):
     """Run one of the C-ABI solvers.  b/x may be CUDA tensors or host (numpy or
     CPU torch, FP32) buffers; host buffers are staged by the library."""
     import torch
@@ -354,7 +354,7 @@ def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=Tru
                  else int(rule))
     opts = _Opts(int(iters), float(lam), rule_code, STORAGE[storage], 1 if use_graph else 0, 1 if profile else 0,
                  float(noise_level), 1 if explicit_residual else 0, float(stop_tol),
-                 {"transpose": 0, "sirt": 1}[backprojector], int(tv_outer), float(tv_tau))
+                 {"transpose": 0, "sirt": 1}[backprojector], int(tv_outer), float(tv_tau), 1 if reorth else 0)
     hr = np.zeros(iters, dtype=np.float64)
     hn = np.zeros(iters, dtype=np.float64)
     hl = np.zeros(iters, dtype=np.float64)

@@ -135,6 +135,102 @@ struct ExplicitMonitor {
     }
 };
 
+// ============================================ re-orthogonalised Golub-Kahan
+//
+// With opts->reorth, every new u and v is re-orthogonalised against all
+// earlier (normalised, stored) ones by classical Gram-Schmidt applied twice
+// with FP64 dot products, before its norm is taken; the norm partials of the
+// fused epilogue are then replaced by fresh ones.  The number of stored
+// vectors is read from the device state (st->iter + 1), so an iteration can
+// still be captured once as a CUDA graph.
+
+constexpr int RO_CHUNK = 8;
+
+// partial[i * VEC_BLOCKS + block] = block share of w . Q_i, i < *iter + 1
+__global__ void __launch_bounds__(VEC_THREADS)
+k_ro_dot(const float *__restrict__ w, const float *__restrict__ Q, int64_t n, const GkState *st, double *partial) {
+    __shared__ double red[VEC_THREADS / 32];
+    if (st->stop) return;
+    const int count = st->iter + 1;
+    for (int c0 = 0; c0 < count; c0 += RO_CHUNK) {
+        const int nc = min(RO_CHUNK, count - c0);
+        double acc[RO_CHUNK];
+#pragma unroll
+        for (int q = 0; q < RO_CHUNK; ++q) acc[q] = 0.0;
+        for (int64_t e = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; e < n;
+             e += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+            const double we = w[e];
+#pragma unroll
+            for (int q = 0; q < RO_CHUNK; ++q)
+                if (q < nc) acc[q] += we * (double)Q[(size_t)(c0 + q) * n + e];
+        }
+#pragma unroll
+        for (int q = 0; q < RO_CHUNK; ++q) {
+            if (q >= nc) break;
+            const double sum = block_sum<VEC_THREADS>(acc[q], red);
+            if (threadIdx.x == 0) partial[(size_t)(c0 + q) * VEC_BLOCKS + blockIdx.x] = sum;
+        }
+    }
+}
+
+// d[i] = sum of the partials of dot i (one block per possible dot; the extra blocks idle)
+__global__ void __launch_bounds__(RED_THREADS) k_ro_reduce(const double *partial, const GkState *st, double *d) {
+    __shared__ double red[RED_THREADS / 32];
+    if (st->stop || (int)blockIdx.x > st->iter) return;
+    const double sum = reduce_partials(partial + (size_t)blockIdx.x * VEC_BLOCKS, VEC_BLOCKS, red);
+    if (threadIdx.x == 0) d[blockIdx.x] = sum;
+}
+
+// w -= sum_i d_i Q_i (FP64 correction)
+__global__ void __launch_bounds__(VEC_THREADS)
+k_ro_sub(float *__restrict__ w, const float *__restrict__ Q, const double *__restrict__ d, int64_t n, const GkState *st) {
+    if (st->stop) return;
+    const int count = st->iter + 1;
+    for (int64_t e = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; e < n; e += (int64_t)VEC_BLOCKS * VEC_THREADS) {
+        double corr = 0.0;
+        for (int i = 0; i < count; ++i) corr += d[i] * (double)Q[(size_t)i * n + e];
+        w[e] = (float)((double)w[e] - corr);
+    }
+}
+
+// Q_{*iter + 1 + off} = w / (scale * norm): u_{i+2} = U / (su beta), v_{i+2} = V / (sv alpha)
+__global__ void __launch_bounds__(VEC_THREADS)
+k_ro_store(const float *__restrict__ w, float *__restrict__ Q, int64_t n, const GkState *st, int which, int off) {
+    if (st->stop) return;
+    const double c = which == 0 ? 1.0 / (st->su * st->beta) : 1.0 / (st->sv * st->alpha);
+    float *dst = Q + (size_t)(st->iter + off) * n;
+    const float cf = (float)c;
+    for (int64_t e = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; e < n; e += (int64_t)VEC_BLOCKS * VEC_THREADS)
+        dst[e] = w[e] * cf;
+}
+
+struct Reorth {
+    bool on = false;
+    float *Ub = nullptr, *Vb = nullptr;
+    double *partial = nullptr, *d = nullptr;
+    int cap = 0;
+
+    cbct_status init(const cbct_solve_opts *o, int64_t n, int64_t m, Workspace &ws) {
+        on = o->reorth != 0;
+        if (!on) return CBCT_OK;
+        cap = o->iters + 1;
+        CBCT_CUDA_TRY(ws.alloc(&Ub, (size_t)cap * n));
+        CBCT_CUDA_TRY(ws.alloc(&Vb, (size_t)cap * m));
+        CBCT_CUDA_TRY(ws.alloc(&partial, (size_t)cap * VEC_BLOCKS));
+        CBCT_CUDA_TRY(ws.alloc(&d, (size_t)cap));
+        return CBCT_OK;
+    }
+    // two classical Gram-Schmidt passes of w against Q_0 .. Q_{iter}
+    void orthogonalise(float *w, const float *Q, int64_t n, const GkState *st, cudaStream_t s, Tracker &tr) {
+        for (int pass = 0; pass < 2; ++pass) {
+            k_ro_dot<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(w, Q, n, st, partial);
+            k_ro_reduce<<<cap, RED_THREADS, 0, s>>>(partial, st, d);
+            k_ro_sub<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(w, Q, d, n, st);
+        }
+        tr.launches += 6;
+    }
+};
+
 // ===================================================================== CGLS
 //
 // Conjugate gradients on the normal equations (Sec. 2.1.1), damped form on
@@ -355,11 +451,22 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
         return r;
     };
 
+    Reorth ro;
+    if constexpr (std::is_same<T, float>::value) {
+        st = ro.init(o, n, m, ws);
+        if (st != CBCT_OK) return st;
+    }
     // beta_1 u_1 = b
     k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, n, pv);
     gk_begin<<<1, RED_THREADS, 0, s>>>(dst, pv, VEC_BLOCKS);
     k_scale_to<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(io.b_dev, U, n, &dst->c0, stop);
     tr.launches += 4;
+    if constexpr (std::is_same<T, float>::value) {
+        if (ro.on) {
+            k_ro_store<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(U, ro.Ub, n, dst, 0, 0);       // u_1
+            ++tr.launches;
+        }
+    }
     CBCT_CUDA_TRY(cudaGetLastError());
     st = launch_weight(g, U, t, W, s);
     if (st != CBCT_OK) return st;
@@ -375,6 +482,12 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     }
     gk_begin2<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method);
     ++tr.launches;
+    if constexpr (std::is_same<T, float>::value) {
+        if (ro.on) {
+            k_ro_store<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, ro.Vb, m, dst, 1, 0);       // v_1
+            ++tr.launches;
+        }
+    }
     if (method == M_LSQR)
         k_start_dirs<T><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(V, w, nullptr, nullptr, m, dst);
     else if (method == M_LSMR)
@@ -392,15 +505,41 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     auto one_iteration = [&]() -> cbct_status {
         T *Vin = method == M_HYBRID ? basis + (size_t)k * m : V;
         T *Vout = method == M_HYBRID ? basis + (size_t)(k + 1) * m : V;
-        Epilogue ef{&dst->fa, &dst->fb, 0, 0, pf, stop, nullptr, W};
+        Epilogue ef{&dst->fa, &dst->fb, 0, 0, pf, stop, nullptr, ro.on ? nullptr : W};
         cbct_status r = fwd(Vin, U, ef);
         if (r != CBCT_OK) return r;
-        gk_after_forward<<<1, RED_THREADS, 0, s>>>(dst, pf, nf, beta_arr);
+        bool done_fwd = false, done_bwd = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (ro.on) {                 // u against u_1 .. u_{i+1}, then its norm, u_{i+2}, w = |d'| u
+                ro.orthogonalise(U, ro.Ub, n, dst, s, tr);
+                k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(U, n, pv);
+                gk_after_forward<<<1, RED_THREADS, 0, s>>>(dst, pv, VEC_BLOCKS, beta_arr);
+                k_ro_store<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(U, ro.Ub, n, dst, 0, 1);
+                tr.launches += 2;
+                r = launch_weight(g, U, t, W, s);
+                if (r != CBCT_OK) return r;
+                ++tr.launches;
+                done_fwd = true;
+            }
+        }
+        if (!done_fwd) gk_after_forward<<<1, RED_THREADS, 0, s>>>(dst, pf, nf, beta_arr);
         Epilogue eb{&dst->ba, &dst->bb, 0, 0, pb, stop, method == M_HYBRID ? (const void *)Vin : nullptr};
         r = bwd(W, Vout, eb);
         if (r != CBCT_OK) return r;
-        gk_after_backward<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method, hist_r, hist_n, alpha_arr,
-                                                     scale_arr, iters);
+        if constexpr (std::is_same<T, float>::value) {
+            if (ro.on) {                 // v against v_1 .. v_{i+1}, then its norm and v_{i+2}
+                ro.orthogonalise(Vout, ro.Vb, m, dst, s, tr);
+                k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(Vout, m, pv);
+                gk_after_backward<<<1, RED_THREADS, 0, s>>>(dst, pv, VEC_BLOCKS, (int)method, hist_r, hist_n,
+                                                             alpha_arr, scale_arr, iters);
+                k_ro_store<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(Vout, ro.Vb, m, dst, 1, 0);
+                tr.launches += 2;
+                done_bwd = true;
+            }
+        }
+        if (!done_bwd)
+            gk_after_backward<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method, hist_r, hist_n, alpha_arr,
+                                                         scale_arr, iters);
         tr.launches += 3;            // two finalize kernels + the update / projected solve
         em.keep(io.xz, m, stop, s, tr);
         if (method == M_LSQR) {
@@ -587,6 +726,10 @@ static cbct_status dispatch_gk(const cbct_geometry *g, const float *b, float *x,
         set_error("hybrid LSQR: the discrepancy principle needs 0 <= noise_level < 1");
         return CBCT_EINVAL;
     }
+    if (o->reorth && o->storage != CBCT_F32) {
+        set_error("re-orthogonalisation needs FP32 storage");
+        return CBCT_EINVAL;
+    }
     if (lsmr_proj && o->rule == CBCT_LAMBDA_DP) {
         set_error("hybrid LSMR: lambda by GCV or fixed (the discrepancy principle bounds ||r||, not ||A^T r||)");
         return CBCT_EINVAL;
@@ -629,6 +772,10 @@ extern "C" cbct_status cbct_cgls_solve(const cbct_geometry *g, const float *b, f
     if (st != CBCT_OK) return st;
     if (o->storage != CBCT_F32) {
         set_error("CGLS supports FP32 storage only");
+        return CBCT_EINVAL;
+    }
+    if (o->reorth) {
+        set_error("CGLS has no Golub-Kahan basis to re-orthogonalise");
         return CBCT_EINVAL;
     }
     return cgls_solve(g, b, x, o, rep, (cudaStream_t)stream);

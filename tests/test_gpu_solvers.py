@@ -407,3 +407,32 @@ def test_cgls_tv(cbct, c1_problem):
     x_cg, _ = cbct.cgls(geom, dev(b), outer * inner)
     assert krylov.total_variation(x.cpu().numpy().astype(np.float64)) < \
         krylov.total_variation(x_cg.cpu().numpy().astype(np.float64))
+
+
+# --------------------------------------- re-orthogonalised Golub-Kahan (Sec. 3.1.1, Sec. 4)
+@pytest.mark.parametrize("method", ["lsqr", "lsmr", "hybrid_lsqr"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_reorthogonalised_solvers(cbct, c1_problem, method, use_graph):
+    """Re-orthogonalised Golub-Kahan (graph-replayed or not) against the
+    oracle's re-orthogonalised recurrences at k = 12, and within FP32 rounding
+    of the plain process in this well-conditioned range."""
+    g, _, b = c1_problem
+    geom = cbct.Geometry(g)
+    k = 12
+    kw = {"rule": "fixed", "lam": 0.5} if method == "hybrid_lsqr" else {}
+    x, rep = getattr(cbct, method)(geom, dev(b), k, reorth=True, use_graph=use_graph, **kw)
+    x0, _ = getattr(cbct, method)(geom, dev(b), k, **kw)
+    okw = {"rule": "fixed", "lam": 0.5} if method == "hybrid_lsqr" else {}
+    x_ref, h = getattr(krylov, method)(oracle.Operator(g), b, k, reorth=True, **okw)
+    assert rep.iters_done == k
+    assert rel(x.cpu().numpy(), x_ref) <= ITER_TOL
+    assert rel(x.cpu().numpy(), x0.cpu().numpy()) <= ITER_TOL
+    np.testing.assert_allclose(rep.resid, h["resid"], rtol=1e-4)
+
+
+def test_reorthogonalisation_needs_fp32(cbct, c1_problem):
+    g, _, b = c1_problem
+    with pytest.raises(cbct.CbctError):
+        cbct.lsqr(cbct.Geometry(g), dev(b), 5, reorth=True, storage="f16")
+    with pytest.raises(cbct.CbctError):
+        cbct.cgls(cbct.Geometry(g), dev(b), 5, reorth=True)
