@@ -351,10 +351,11 @@ def run_projectors(args):
         cbct.project(geom, x, out=y)
         cbct.backproject(geom, y, out=xb)
     torch.cuda.synchronize()
-    times = {"forward": [], "backward": []}
+    times = {"forward": [], "backward": [], "voxel_driven_backward": []}
     for _ in range(args.steps):
         for name, fn in (("forward", lambda: cbct.project(geom, x, out=y)),
-                         ("backward", lambda: cbct.backproject(geom, y, out=xb))):
+                         ("backward", lambda: cbct.backproject(geom, y, out=xb)),
+                         ("voxel_driven_backward", lambda: cbct.backproject_voxel_driven(geom, y, out=xb))):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
             fn()

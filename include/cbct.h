@@ -115,6 +115,17 @@ cbct_status cbct_backproject(const cbct_geometry *geom, const void *y, void *x,
 cbct_status cbct_project_static(const cbct_geometry *geom, const void *x, void *y,
                                 cbct_dtype dtype, cbct_stream stream);
 
+/* A voxel-driven, interpolating backprojector: an approximation of A^T that is
+ * not its transpose, the kind of backprojector Sec. 2.1.4 says fast CBCT codes
+ * use.  Every voxel centre is projected onto every detector, the projection
+ * is sampled there by bilinear interpolation (zero outside the detector) and
+ * weighted by dx dy dz mag^2 |d'| / (du dv DSD), the expected sum of A's
+ * entries of the rays through the voxel (mag = DSD / (DSO - <c, s_hat>), |d'|
+ * the source-to-sample distance).  y: N FP32 device values y[a][iv][iu];
+ * x: M FP32 device values x[k][j][i].  Asynchronous on `stream`. */
+cbct_status cbct_backproject_voxel_driven(const cbct_geometry *geom, const float *y, float *x,
+                                          cbct_stream stream);
+
 /* Number of nonzeros of A (positive-length ray/voxel pairs in FP32), counted
  * by the forward traversal.  Synchronises `stream`. */
 cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream stream);
@@ -180,8 +191,9 @@ typedef struct {
                                 Sec. 3.1.1); costs one product with A per iteration */
     double stop_tol;         /* 0 <= stop_tol < 1; 0 = stop on increase */
     int gmres_backprojector; /* AB-/BA-GMRES: 0 = B = A^T; 1 = B = C A^T R with the SIRT weights
-                                R = 1 / (A 1), C = 1 / (A^T 1) (a backprojector that is not the
-                                transpose of A) */
+                                R = 1 / (A 1), C = 1 / (A^T 1); 2 = the voxel-driven
+                                interpolating backprojector (cbct_backproject_voxel_driven);
+                                1 and 2 are not the transpose of A */
     int tv_outer;            /* CGLS-TV: reweighting (outer) steps, 1 <= tv_outer <= iters; the
                                 iters CGLS iterations are spread evenly over them */
     double tv_tau;           /* CGLS-TV: smoothing tau > 0 of the weights (|D x|^2 + tau^2)^(-1/4) */

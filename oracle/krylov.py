@@ -560,6 +560,55 @@ class WeightedBackprojector:
         return self.c * self.op.rmatvec(self.r * np.asarray(y, dtype=np.float64).reshape(-1))
 
 
+class VoxelDrivenBackprojector:
+    """A voxel-driven, interpolating backprojector, the usual fast GPU
+    approximation of A^T that is not its exact transpose (Sec. 2.1.4): every
+    voxel centre is projected onto every detector and the projection is
+    sampled there by bilinear interpolation (zero outside the detector),
+    weighted by the expected sum of A's entries of the rays through the voxel,
+        w = dx dy dz mag^2 |d'| / (du dv DSD),   mag = DSD / (DSO - <c, s_hat>),
+    |d'| the source-to-pixel distance of the sampled point: rays through the
+    voxel are spaced du dv DSD / (|d'| mag^2) apart perpendicular to their
+    direction at the voxel's depth.  Geometry conventions as the projector's
+    (rotation axis z, source (DSO cos t, DSO sin t, 0), detector u along
+    (-sin t, cos t, 0), v along z)."""
+
+    def __init__(self, g):
+        self.g = g
+        nx, ny, nz = g.nx, g.ny, g.nz
+        self.xc = (np.arange(nx) - 0.5 * (nx - 1)) * g.dx
+        self.yc = (np.arange(ny) - 0.5 * (ny - 1)) * g.dy
+        self.zc = (np.arange(nz) - 0.5 * (nz - 1)) * g.dz
+
+    def __call__(self, y):
+        g = self.g
+        y = np.asarray(y, dtype=np.float64).reshape(g.nangles, g.nv, g.nu)
+        zz, yy, xx = np.meshgrid(self.zc, self.yc, self.xc, indexing="ij")
+        out = np.zeros((g.nz, g.ny, g.nx))
+        vol = g.dx * g.dy * g.dz
+        for a, t in enumerate(g.angles):
+            ct, st = math.cos(t), math.sin(t)
+            along = g.dso - (xx * ct + yy * st)
+            mag = g.dsd / along
+            u = (-xx * st + yy * ct) * mag
+            v = zz * mag
+            fu = u / g.du + 0.5 * (g.nu - 1)
+            fv = v / g.dv + 0.5 * (g.nv - 1)
+            iu = np.floor(fu).astype(np.int64)
+            iv = np.floor(fv).astype(np.int64)
+            tu = fu - iu
+            tv = fv - iv
+            val = np.zeros_like(fu)
+            for du_, dv_, wgt in ((0, 0, (1 - tu) * (1 - tv)), (1, 0, tu * (1 - tv)),
+                                  (0, 1, (1 - tu) * tv), (1, 1, tu * tv)):
+                cu, cv = iu + du_, iv + dv_
+                ok = (cu >= 0) & (cu < g.nu) & (cv >= 0) & (cv < g.nv)
+                val += np.where(ok, wgt * y[a, np.clip(cv, 0, g.nv - 1), np.clip(cu, 0, g.nu - 1)], 0.0)
+            dlen = np.sqrt(g.dsd * g.dsd + u * u + v * v)
+            out += vol * mag * mag * dlen / (g.du * g.dv * g.dsd) * val
+        return out.ravel()
+
+
 def _arnoldi_gmres(apply, r0, iters):
     """GMRES on K_k(M, r0) for the operator `apply` = M: Arnoldi with modified
     Gram-Schmidt in FP64; y_k = argmin ||beta e_1 - Hbar_k y|| for every k.

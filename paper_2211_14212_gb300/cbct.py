@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
     for fn in ("cbct_project", "cbct_backproject", "cbct_project_static"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.c_int, vp]
     lib.cbct_count_nnz.argtypes = [G, ctypes.POINTER(i64), vp]
+    lib.cbct_backproject_voxel_driven.argtypes = [G, vp, vp, vp]
     lib.cbct_geometry_set_launch.argtypes = [G, ctypes.c_int, ctypes.c_int]
     lib.cbct_geometry_get_launch.argtypes = [G, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.cbct_geometry_autotune.argtypes = [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
@@ -228,6 +229,22 @@ def project(geom: Geometry, x, out=None, stream=None):
     _check("cbct_project", load().cbct_project(geom.handle, ctypes.c_void_p(x.data_ptr()),
                                                ctypes.c_void_p(out.data_ptr()), _dtype_code(x.dtype),
                                                _stream_handle(stream)))
+    return out
+
+
+def backproject_voxel_driven(geom: Geometry, y, out=None, stream=None):
+    """The voxel-driven interpolating approximation of A^T (not its transpose),
+    FP32 (cbct_backproject_voxel_driven)."""
+    import torch
+    _require_cuda(y, "y", geom.num_rays)
+    if y.dtype != torch.float32:
+        raise TypeError("y must be float32")
+    if out is None:
+        out = torch.empty(geom.vol_shape, dtype=torch.float32, device=y.device)
+    _require_cuda(out, "out", geom.num_voxels)
+    _check("cbct_backproject_voxel_driven",
+           load().cbct_backproject_voxel_driven(geom.handle, ctypes.c_void_p(y.data_ptr()),
+                                                ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
     return out
 
 
@@ -354,7 +371,8 @@ def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=Tru
                  else int(rule))
     opts = _Opts(int(iters), float(lam), rule_code, STORAGE[storage], 1 if use_graph else 0, 1 if profile else 0,
                  float(noise_level), 1 if explicit_residual else 0, float(stop_tol),
-                 {"transpose": 0, "sirt": 1}[backprojector], int(tv_outer), float(tv_tau), 1 if reorth else 0)
+                 {"transpose": 0, "sirt": 1, "voxel": 2}[backprojector], int(tv_outer), float(tv_tau),
+                 1 if reorth else 0)
     hr = np.zeros(iters, dtype=np.float64)
     hn = np.zeros(iters, dtype=np.float64)
     hl = np.zeros(iters, dtype=np.float64)
@@ -399,8 +417,8 @@ def cgls_tv(geom, b, iters, lam, outer, tau=1e-3, **kw):
 
 
 def ab_gmres(geom, b, iters, backprojector="transpose", **kw):
-    """AB-GMRES (Sec. 2.1.4); backprojector "transpose" (B = A^T) or "sirt"
-    (B = C A^T R with the SIRT weights)."""
+    """AB-GMRES (Sec. 2.1.4); backprojector "transpose" (B = A^T), "sirt"
+    (B = C A^T R with the SIRT weights) or "voxel" (voxel-driven, interpolating)."""
     return _solve("cbct_ab_gmres_solve", geom, b, iters, backprojector=backprojector, **kw)
 
 

@@ -170,6 +170,9 @@ cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_d
 cbct_status launch_proj_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_vfast,
                                  cudaStream_t s);
 cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaStream_t s);
+// Voxel-driven interpolating backprojector (an approximation of A^T), FP32,
+// v-fastest projections in, either volume layout out (vdbp.cu).
+cbct_status launch_voxel_backproject(const DevGeom &g, const float *y_vfast, float *x, bool zfast, cudaStream_t s);
 int forward_num_blocks(const DevGeom &g);
 int backward_num_blocks(const DevGeom &g);
 dim3 forward_grid(const DevGeom &g);

@@ -6,8 +6,9 @@
 //   BA: min ||B (b - A x)|| over x in K_k(B A, B b),    x_k itself
 //
 // B is A^T (then AB-GMRES computes LSQR's iterates and BA-GMRES LSMR's, in
-// exact arithmetic) or the SIRT-weighted C A^T R, R = 1 / (A 1) per ray and
-// C = 1 / (A^T 1) per voxel, which is not the transpose of A.
+// exact arithmetic), the SIRT-weighted C A^T R, R = 1 / (A 1) per ray and
+// C = 1 / (A^T 1) per voxel, or the voxel-driven interpolating backprojector
+// of vdbp.cu; the last two are not the transpose of A.
 //
 // Arnoldi runs on the device: the Krylov vectors are FP32 (projection-side,
 // v-fastest, for AB; volume-side, z-fastest, for BA), each new vector is
@@ -142,8 +143,15 @@ struct GmresOperator {
         ++tr.fwd;
         return launch_forward(g, x, y, CBCT_F32, e, s, true);
     }
+    bool voxel_driven = false;
+
     // x = B y
     cbct_status B(const float *y, float *x) {
+        if (voxel_driven) {
+            ++tr.launches;
+            ++tr.bwd;
+            return launch_voxel_backproject(g, y, x, true, s);
+        }
         const float *src = y;
         if (weighted) {
             k_diag<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(R, y, tn, n);
@@ -181,6 +189,7 @@ static cbct_status gmres_solve(const cbct_geometry *geom, const float *b, float 
     tr.s = s;
     GmresOperator op{g, s, tr, n, m};
     op.weighted = o->gmres_backprojector == 1;
+    op.voxel_driven = o->gmres_backprojector == 2;
     float *V = nullptr, *w = nullptr, *yn = nullptr, *xm = nullptr;
     double *partial = nullptr, *pn = nullptr, *H = nullptr, *d2 = nullptr, *beta = nullptr, *ycoef = nullptr;
     CBCT_CUDA_TRY(ws.alloc(&V, (size_t)(iters + 1) * len));
@@ -326,8 +335,8 @@ static cbct_status dispatch_gmres(const cbct_geometry *g, const float *b, float 
         set_error("GMRES: the explicit-residual monitor is not available (GMRES minimises its residual)");
         return CBCT_EINVAL;
     }
-    if (o->gmres_backprojector != 0 && o->gmres_backprojector != 1) {
-        set_error("GMRES: gmres_backprojector must be 0 (A^T) or 1 (SIRT-weighted)");
+    if (o->gmres_backprojector < 0 || o->gmres_backprojector > 2) {
+        set_error("GMRES: gmres_backprojector must be 0 (A^T), 1 (SIRT-weighted) or 2 (voxel-driven)");
         return CBCT_EINVAL;
     }
     return gmres_solve(g, b, x, o, rep, (cudaStream_t)stream, ab);

@@ -61,6 +61,7 @@ def test_null_arguments(lib):
     assert lib.cbct_project(None, None, None, 0, None) == cbct.CBCT_EINVAL
     assert lib.cbct_backproject(None, None, None, 0, None) == cbct.CBCT_EINVAL
     assert lib.cbct_project_static(None, None, None, 0, None) == cbct.CBCT_EINVAL
+    assert lib.cbct_backproject_voxel_driven(None, None, None, None) == cbct.CBCT_EINVAL
     assert lib.cbct_geometry_num_rays(None) == -1
     lib.cbct_geometry_destroy(None)          # no-op
 

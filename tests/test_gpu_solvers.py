@@ -370,17 +370,19 @@ def test_hybrid_lsmr_rejects_dp(cbct, c1_problem):
 
 # ------------------------------------------------------ AB-/BA-GMRES (Sec. 2.1.4)
 @pytest.mark.parametrize("variant", ["ab", "ba"])
-@pytest.mark.parametrize("backprojector", ["transpose", "sirt"])
+@pytest.mark.parametrize("backprojector", ["transpose", "sirt", "voxel"])
 def test_gmres(cbct, c1_problem, variant, backprojector):
-    """GMRES with B = A^T or the SIRT-weighted B = C A^T R against the oracle's
-    Arnoldi/least-squares GMRES: iterate and minimised residual after 10
-    iterations, residual history non-increasing."""
+    """GMRES with B = A^T, the SIRT-weighted B = C A^T R or the voxel-driven
+    interpolating B against the oracle's Arnoldi/least-squares GMRES: iterate
+    and minimised residual after 10 iterations, residual history
+    non-increasing."""
     g, _, b = c1_problem
     geom = cbct.Geometry(g)
     k = 10
     x, rep = getattr(cbct, variant + "_gmres")(geom, dev(b), k, backprojector=backprojector)
     op = oracle.Operator(g)
-    bp = krylov.WeightedBackprojector(op) if backprojector == "sirt" else None
+    bp = {"transpose": None, "sirt": krylov.WeightedBackprojector(op),
+          "voxel": krylov.VoxelDrivenBackprojector(g)}[backprojector]
     x_ref, h = getattr(krylov, variant + "_gmres")(op, b, k, backprojector=bp)
     assert rep.iters_done == k
     hist = rep.resid if variant == "ab" else rep.normal_resid
