@@ -336,33 +336,44 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
         const float x0 = g.bx0 + i * g.dx, x1 = x0 + g.dx;
         const float y0 = g.by0 + j * g.dy, y1 = y0 + g.dy;
         const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
-        const float m = g.dso / g.dsd;
         // The detector windows below only select candidates (every length is
         // then computed exactly from plane_alpha), so they use fast
         // approximate divisions: their relative error (~1e-6) stays far below
         // the 0.05-pixel margins.
         const float inv_du = 1.0f / g.du, inv_dv = 1.0f / g.dv;
-        float zr_lo[K], zr_hi[K];        // voxel slab bottom / top over dv
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            const float za = g.bz0 + (k0 + kk * 32 + lane) * g.dz;
-            zr_lo[kk] = za * inv_dv;
-            zr_hi[kk] = (za + g.dz) * inv_dv;
-        }
         const size_t nuv = (size_t)g.nu * g.nv;
         for (int a = a_begin; a < a_end; ++a) {
             const float2 cs = g.trig[a];
-            float umin = FLT_MAX, umax = -FLT_MAX;
+            float umin = FLT_MAX, umax = -FLT_MAX, magmin = FLT_MAX, magmax = 0.0f;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float px = (c & 1) ? x1 : x0, py = (c & 2) ? y1 : y0;
                 const float along = g.dso - (px * cs.x + py * cs.y);   // > 0: source outside
-                const float u = (-px * cs.y + py * cs.x) * __fdividef(g.dsd, along);
+                const float mag = __fdividef(g.dsd, along);
+                const float u = (-px * cs.y + py * cs.x) * mag;
                 umin = fminf(umin, u);
                 umax = fmaxf(umax, u);
+                magmin = fminf(magmin, mag);
+                magmax = fmaxf(magmax, mag);
             }
             const int iu0 = max(0, (int)ceilf(__fmaf_rn(umin, inv_du, cu - 0.05f)));
             const int iu1 = min(g.nu - 1, (int)floorf(__fmaf_rn(umax, inv_du, cu + 0.05f)));
+            // Rows that can meet the lane's voxel at this angle: a point at
+            // height z and source depth `along` lies on row v = z dsd / along,
+            // and the column's depths span the corners' (mag = dsd / along is
+            // extreme at a corner).  The window holds for every detector
+            // column below; a row that misses the voxel for one of them adds
+            // an exact zero.
+            int r0[K], r1[K];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int k = k0 + kk * 32 + lane;
+                const float zlo = (g.bz0 + k * g.dz) * inv_dv, zhi = (g.bz0 + (k + 1) * g.dz) * inv_dv;
+                const float vmin = fminf(zlo * magmin, zlo * magmax);
+                const float vmax = fmaxf(zhi * magmin, zhi * magmax);
+                r0[kk] = max(0, (int)ceilf(vmin + (cv - 0.05f)));
+                r1[kk] = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
+            }
             const float *pa = wproj + (size_t)a * nuv;
             for (int iu = iu0; iu <= iu1; ++iu) {
                 const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
@@ -372,19 +383,11 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                 clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
                 clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
                 if (miss || !(ain < aout)) continue;
-                // rows whose ray can be inside z slab [z, z + dz] for some alpha in [ain, aout]
-                const float rlo = __fdividef(1.0f, m + ain), rhi = __fdividef(1.0f, m + aout);
                 const float *wcol = pa + (size_t)iu * g.nv;
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) {
-                    const int k = k0 + kk * 32 + lane;
-                    if (k >= g.nz) continue;
-                    const float vmin = fminf(zr_lo[kk] * rlo, zr_lo[kk] * rhi);
-                    const float vmax = fmaxf(zr_hi[kk] * rlo, zr_hi[kk] * rhi);
-                    const int r0 = max(0, (int)ceilf(vmin + (cv - 0.05f)));
-                    const int r1 = min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f)));
-                    const float2 *zb = g.zbox + (size_t)k * g.nv;
-                    for (int iv = r0; iv <= r1; ++iv) {
+                    const float2 *zb = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv;
+                    for (int iv = r0[kk]; iv <= r1[kk]; ++iv) {
                         const float2 e = zb[iv];         // row iv's alpha interval in slab k
                         const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
                         // a miss adds exactly zero: the same sum as skipping it
