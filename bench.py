@@ -46,8 +46,8 @@ REF_STEP_ANGLES = 8             # --impl reference: about 7 s per step, so K ste
 NCU_TRAFFIC = {
     # one launch of the 2x4x128 transpose tile at 256^3 / 512^2 / 360 (ncu --set full,
     # the cbct_backproject launch of the projectors mode; the solver's launch of the
-    # same tile differs only in the output layout): 7.230 GB read + 0.120 GB written
-    "backward": (7350106000, "4956e8f69c1fe615"),
+    # same tile differs only in the output layout): 8.368 GB read + 0.071 GB written
+    "backward": (8439319624, "1719a040d9495f79"),
 }
 
 
