@@ -308,6 +308,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
 // w[a][iu][iv] = |d'| * y.
 
 constexpr int BWD_THREADS = 256;
+constexpr int BWD_SHORT_ROWS = 3;
 
 // Angles [a_begin, a_end) are summed in one call.  A scan whose projections
 // do not fit in L2 is summed in passes over blocks of angles (launch_backward):
@@ -374,6 +375,14 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                 r0[kk] = max(0, (int)ceilf(vmin + (cv - 0.05f)));
                 r1[kk] = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
             }
+            // Windows of at most BWD_SHORT_ROWS rows in every lane (the usual
+            // case: a slab spans dz * mag / dv rows) take a fixed, predicated
+            // sequence instead of a loop; the same rows are summed in the same
+            // order either way.
+            bool short_rows = true;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) short_rows = short_rows && r1[kk] - r0[kk] < BWD_SHORT_ROWS;
+            short_rows = __all_sync(0xffffffffu, short_rows);
             const float *pa = wproj + (size_t)a * nuv;
             for (int iu = iu0; iu <= iu1; ++iu) {
                 const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
@@ -384,14 +393,30 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                 clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
                 if (miss || !(ain < aout)) continue;
                 const float *wcol = pa + (size_t)iu * g.nv;
+                if (short_rows) {
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    const float2 *zb = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv;
-                    for (int iv = r0[kk]; iv <= r1[kk]; ++iv) {
-                        const float2 e = zb[iv];         // row iv's alpha interval in slab k
-                        const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
-                        // a miss adds exactly zero: the same sum as skipping it
-                        acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
+                    for (int kk = 0; kk < K; ++kk) {
+                        const float2 *zb = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv;
+#pragma unroll
+                        for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
+                            const int iv = r0[kk] + t;
+                            if (iv <= r1[kk]) {
+                                const float2 e = zb[iv];
+                                const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
+                                acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) {
+                        const float2 *zb = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv;
+                        for (int iv = r0[kk]; iv <= r1[kk]; ++iv) {
+                            const float2 e = zb[iv];         // row iv's alpha interval in slab k
+                            const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
+                            // a miss adds exactly zero: the same sum as skipping it
+                            acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
+                        }
                     }
                 }
             }
