@@ -46,8 +46,8 @@ REF_STEP_ANGLES = 8             # --impl reference: about 7 s per step, so K ste
 NCU_TRAFFIC = {
     # one launch of the 2x4x128 transpose tile at 256^3 / 512^2 / 360 (ncu --set full,
     # the cbct_backproject launch of the projectors mode; the solver's launch of the
-    # same tile differs only in the output layout): 8.368 GB read + 0.071 GB written
-    "backward": (8439319624, "1719a040d9495f79"),
+    # same tile differs only in the output layout): 11.800 GB read + 0.122 GB written
+    "backward": (11921397568, "053ead427d138a32"),
 }
 
 
