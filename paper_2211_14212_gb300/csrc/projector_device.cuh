@@ -293,12 +293,13 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
 // the volume is written once (fused epilogue), so there are no atomics and the
 // result does not depend on scheduling.  A warp owns one column (i, j) and
 // 32 K consecutive k (k = k0 + kk * 32 + lane); a tile is 8 warps on a
-// CX x (8 / CX) patch of columns.  For every angle the warp finds the detector
-// columns whose xy projection crosses cell (i, j) (the cell's four corners),
-// and for each of them the alpha interval [ain, aout] of that crossing (x and
-// y plane crossings, warp-uniform).  A lane then inverts z(alpha) =
-// v (dso/dsd + alpha) over [ain, aout] to get the detector rows that can meet
-// its voxel's z slab, and takes for each the segment
+// CX x (8 / CX) patch of columns.  For every angle the warp projects the
+// cell's four corners to find the detector columns whose xy projection
+// crosses cell (i, j), and each lane the detector rows that can meet its
+// voxel's z slab (v = z dsd / depth over the corners' depths).  For each such
+// column the warp takes the alpha interval [ain, aout] of the crossing (x and
+// y plane crossings, warp-uniform), and a lane takes for each of its rows
+// the segment
 //     [max(ain, z entry), min(aout, z exit)].
 // The z entry/exit of a row's ray in slab k does not depend on the angle
 // (circular orbit), so it is read from the table DevGeom::zbox, which
