@@ -314,16 +314,107 @@ def get_angle_block(geom: Geometry) -> int:
     return int(a.value)
 
 
-def autotune(geom: Geometry, max_angles: int = 32, stream=None) -> dict:
+TUNE_CACHE_VERSION = 1
+
+
+def tune_key(params: dict, nangles: int, device: str) -> str:
+    """The geometry class a launch-shape choice is cached under: volume and
+    detector sizes and spacings, source distances, angle count, the device's
+    name and the library's shape tables (a cache written for other shapes
+    does not match)."""
+    p = params
+    return "|".join((
+        "vol %dx%dx%d @ %.6g,%.6g,%.6g" % (int(p["nx"]), int(p["ny"]), int(p["nz"]),
+                                           float(p["dx"]), float(p["dy"]), float(p["dz"])),
+        "det %dx%d @ %.6g,%.6g" % (int(p["nu"]), int(p["nv"]), float(p["du"]), float(p["dv"])),
+        "dso %.6g dsd %.6g" % (float(p["dso"]), float(p["dsd"])),
+        "angles %d" % int(nangles),
+        device,
+        "rows %s" % ",".join(str(r) for r in FWD_ROWS),
+        "tiles %s" % ";".join(BWD_CONFIGS)))
+
+
+class TuneCache:
+    """Launch shapes chosen by `autotune`, per geometry class, in a JSON file
+    {"version": 1, "entries": {key: {"fwd_rows", "bwd_config", ...}}}.  A
+    missing, unreadable or other-version file reads as empty; `put` merges
+    with what is on disk and replaces the file atomically."""
+
+    def __init__(self, path):
+        self.path = os.fspath(path)
+
+    def _read(self) -> dict:
+        import json
+        try:
+            with open(self.path) as f:
+                data = json.load(f)
+        except (OSError, ValueError):
+            return {}
+        if not isinstance(data, dict) or data.get("version") != TUNE_CACHE_VERSION:
+            return {}
+        entries = data.get("entries")
+        return entries if isinstance(entries, dict) else {}
+
+    def get(self, key: str):
+        e = self._read().get(key)
+        if not isinstance(e, dict):
+            return None
+        f, b = e.get("fwd_rows"), e.get("bwd_config")
+        if f not in FWD_ROWS or not isinstance(b, int) or not 0 <= b < len(BWD_CONFIGS):
+            return None
+        return e
+
+    def put(self, key: str, entry: dict):
+        import json
+        import tempfile
+        entries = self._read()
+        entries[key] = entry
+        d = os.path.dirname(os.path.abspath(self.path))
+        os.makedirs(d, exist_ok=True)
+        fd, tmp = tempfile.mkstemp(prefix=".tune-", suffix=".json", dir=d)
+        try:
+            with os.fdopen(fd, "w") as f:
+                json.dump({"version": TUNE_CACHE_VERSION, "entries": entries}, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+        except BaseException:
+            if os.path.exists(tmp):
+                os.unlink(tmp)
+            raise
+
+
+def _device_name() -> str:
+    import torch
+    if torch.cuda.is_available():
+        return torch.cuda.get_device_name(torch.cuda.current_device())
+    return "no device"
+
+
+def autotune(geom: Geometry, max_angles: int = 32, stream=None, cache=None) -> dict:
     """Time every launch shape on <= max_angles angles and keep the fastest
-    (cbct_geometry_autotune).  Returns the chosen shapes and all timings."""
+    (cbct_geometry_autotune).  Returns the chosen shapes and all timings.
+
+    With `cache` (a JSON file path; default: the CBCT_TUNE_CACHE environment
+    variable, if set) a geometry class tuned before takes its cached shapes
+    without timing (`"cached": True`), and a new choice is added to the file."""
+    cache = cache if cache is not None else os.environ.get("CBCT_TUNE_CACHE")
+    key = store = None
+    if cache:
+        store = TuneCache(cache)
+        key = tune_key(geom.params, len(geom.angles), _device_name())
+        e = store.get(key)
+        if e is not None:
+            set_launch(geom, e["fwd_rows"], e["bwd_config"])
+            return dict(e, bwd_shape=BWD_CONFIGS[e["bwd_config"]], cached=True)
     t = (ctypes.c_double * TUNE_TIMES)()
     _check("cbct_geometry_autotune", load().cbct_geometry_autotune(geom.handle, int(max_angles), t,
                                                                      _stream_handle(stream)))
     f, b = get_launch(geom)
-    return {"fwd_rows": f, "bwd_config": b, "bwd_shape": BWD_CONFIGS[b],
-            "forward_ms": {str(r): t[i] for i, r in enumerate(FWD_ROWS)},
-            "backward_ms": {BWD_CONFIGS[c]: t[len(FWD_ROWS) + c] for c in range(len(BWD_CONFIGS))}}
+    out = {"fwd_rows": f, "bwd_config": b, "bwd_shape": BWD_CONFIGS[b],
+           "forward_ms": {str(r): t[i] for i, r in enumerate(FWD_ROWS)},
+           "backward_ms": {BWD_CONFIGS[c]: t[len(FWD_ROWS) + c] for c in range(len(BWD_CONFIGS))}}
+    if store is not None:
+        store.put(key, dict(out, max_angles=int(max_angles)))
+    return dict(out, cached=False)
 
 
 @dataclass

@@ -141,14 +141,19 @@ def test_transpose_in_angle_passes_matches_oracle(cbct, name):
         cbct.set_angle_block(geom, -1)
 
 
-def test_autotune_picks_a_valid_shape(cbct):
+def test_autotune_picks_a_valid_shape(cbct, tmp_path):
     g = synth.config("c1")
     geom = cbct.Geometry(g)
-    res = cbct.autotune(geom, max_angles=8)
-    assert res["fwd_rows"] in cbct.FWD_ROWS and res["bwd_shape"] in cbct.BWD_CONFIGS
+    cache = tmp_path / "tune.json"
+    res = cbct.autotune(geom, max_angles=8, cache=cache)
+    assert res["fwd_rows"] in cbct.FWD_ROWS and res["bwd_shape"] in cbct.BWD_CONFIGS and not res["cached"]
     assert all(t > 0 for t in res["forward_ms"].values()) and all(t > 0 for t in res["backward_ms"].values())
     x = synth.random_volume(g, 23).astype(np.float32)
     assert_close(cbct.project(geom, dev(x)).cpu().numpy(), oracle.project(g, x.astype(np.float64)))
+    # a second scan of the same class takes the cached shapes without timing
+    geom2 = cbct.Geometry(g)
+    res2 = cbct.autotune(geom2, max_angles=8, cache=cache)
+    assert res2["cached"] and cbct.get_launch(geom2) == (res["fwd_rows"], res["bwd_config"])
 
 
 @pytest.mark.parametrize("name", ["small", "c1", "short_scan"])
