@@ -117,11 +117,11 @@ projected_solve_kernel(const double *__restrict__ alphas, const double *__restri
     for (int sweep = 0; sweep < JACOBI_SWEEPS; ++sweep) {
         if (tid == 0) rotated = 0;
         __syncthreads();
-        for (int round = 0; round < K - 1; ++round) {
+        for (int pairing = 0; pairing < K - 1; ++pairing) {
             for (int pi = warp; pi < K / 2; pi += PS_WARPS) {
                 int p, q;
-                if (pi == 0) { p = K - 1; q = round; }
-                else { p = (round + pi) % (K - 1); q = (round - pi + K - 1) % (K - 1); }
+                if (pi == 0) { p = K - 1; q = pairing; }
+                else { p = (pairing + pi) % (K - 1); q = (pairing - pi + K - 1) % (K - 1); }
                 if (p >= k || q >= k) continue;
                 if (p > q) { const int t = p; p = q; q = t; }
                 double *bp = B + (size_t)p * rows, *bq = B + (size_t)q * rows;
