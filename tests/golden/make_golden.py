@@ -38,6 +38,7 @@ def fixtures():
         "voxels": vox.tolist(),
         "backproject_voxels": oracle.backproject_voxels(g, y, vox, THREADS).tolist(),
         "nnz": int(oracle.nnz(g)),
+        "voxel_driven_voxels": krylov.VoxelDrivenBackprojector(g)(y)[vox].tolist(),
     }
     g = synth.config("c1")
     xt = synth.ellipsoid_phantom(g, 10, seed=0).astype(np.float64)
@@ -54,6 +55,17 @@ def fixtures():
     _, h = krylov.hybrid_lsqr(op, bn, 6, rule="dp", noise_level=nl)
     res["hybrid_dp_lambda"] = h["lambda"]
     res["dp_noise_level"] = nl
+    _, h = krylov.hybrid_lsmr(op, bn, 6, rule="gcv")
+    res["hybrid_lsmr_gcv_lambda"] = h["lambda"]
+    _, h = krylov.lsqr(op, bn, 6, reorth=True)
+    res["lsqr_reorth_resid"] = h["resid"]
+    bps = {"transpose": None, "sirt": krylov.WeightedBackprojector(op), "voxel": krylov.VoxelDrivenBackprojector(g)}
+    for name, bp in bps.items():
+        for variant in ("ab", "ba"):
+            _, h = getattr(krylov, variant + "_gmres")(op, b, 5, backprojector=bp)
+            res["%s_gmres_%s_resid" % (variant, name)] = h["resid"]
+    _, h = krylov.cgls_tv(op, g.vol_shape, bn, 2, 3, 2.0, 1e-2)
+    res["cgls_tv_resid"] = h["resid"]
     out["c1"] = res
     return out
 

@@ -48,3 +48,33 @@ def test_c1_solver_histories(golden):
     np.testing.assert_allclose(h["lambda"], c["hybrid_gcv_lambda"], rtol=1e-8)
     _, h = krylov.hybrid_lsqr(op, bn, 6, rule="dp", noise_level=c["dp_noise_level"])
     np.testing.assert_allclose(h["lambda"], c["hybrid_dp_lambda"], rtol=1e-8)
+
+
+def test_voxel_driven_backprojector_values(golden):
+    t = golden["tiny"]
+    g = synth.config("tiny")
+    y = synth.random_projections(g, 8)
+    got = krylov.VoxelDrivenBackprojector(g)(y)[np.array(t["voxels"])]
+    np.testing.assert_allclose(got, t["voxel_driven_voxels"], rtol=RTOL)
+
+
+def test_c1_extended_solver_histories(golden):
+    """Hybrid LSMR (GCV), re-orthogonalised LSQR, AB-/BA-GMRES with each
+    backprojector and CGLS-TV on the c1 problem."""
+    c = golden["c1"]
+    g = synth.config("c1")
+    xt = synth.ellipsoid_phantom(g, 10, seed=0).astype(np.float64)
+    b = oracle.project(g, xt).ravel()
+    bn = synth.poisson_log_noise(b, 1e3, seed=5).astype(np.float64)
+    op = oracle.Operator(g)
+    _, h = krylov.hybrid_lsmr(op, bn, 6, rule="gcv")
+    np.testing.assert_allclose(h["lambda"], c["hybrid_lsmr_gcv_lambda"], rtol=1e-8)
+    _, h = krylov.lsqr(op, bn, 6, reorth=True)
+    np.testing.assert_allclose(h["resid"], c["lsqr_reorth_resid"], rtol=RTOL)
+    bps = {"transpose": None, "sirt": krylov.WeightedBackprojector(op), "voxel": krylov.VoxelDrivenBackprojector(g)}
+    for name, bp in bps.items():
+        for variant in ("ab", "ba"):
+            _, h = getattr(krylov, variant + "_gmres")(op, b, 5, backprojector=bp)
+            np.testing.assert_allclose(h["resid"], c["%s_gmres_%s_resid" % (variant, name)], rtol=RTOL)
+    _, h = krylov.cgls_tv(op, g.vol_shape, bn, 2, 3, 2.0, 1e-2)
+    np.testing.assert_allclose(h["resid"], c["cgls_tv_resid"], rtol=RTOL)
