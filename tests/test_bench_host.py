@@ -1,0 +1,85 @@
+"""Host-side parts of bench.py on the CPU: the oracle's CPU-baseline sample and
+the reference arm's JSON line (the FP64 oracle timed on the host cores), on a
+tiny workload in place of the 256^3 one; and the clock-record summary."""
+import json
+import os
+import sys
+from types import SimpleNamespace
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+
+@pytest.fixture
+def tiny_workload(monkeypatch):
+    g = synth.config("small")
+    monkeypatch.setattr(bench, "workload_config", lambda: (g, {"workload": "small test scan"}))
+    monkeypatch.setattr(bench, "REF_STEP_ANGLES", 4)
+    for var in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(var, raising=False)
+    return g
+
+
+def test_cpu_baseline_sample_counts_the_sampled_updates(tiny_workload):
+    g = tiny_workload
+    rate, cores, dt, nnz = bench.oracle_sample_rate(g, 4)
+    sub = g.angle_subset(4)
+    assert sub.nangles == 4
+    assert nnz == oracle.nnz(sub)
+    assert cores >= 1 and dt > 0
+    assert rate == pytest.approx(2 * nnz / dt / 1e9)
+
+
+def test_reference_arm_prints_one_complete_line(tiny_workload, capsys):
+    args = SimpleNamespace(gpus=1, steps=2, warmup=3)
+    assert bench.run_reference(args) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
+    assert d["config"] == {"workload": "small test scan"}
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "4 of" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only(tiny_workload, monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.run_reference(SimpleNamespace(gpus=2, steps=1, warmup=3)) == 0
+    assert capsys.readouterr().out.strip() == ""
+
+
+def test_clock_record_summary(tmp_path):
+    """Median SM clock, the largest max clock and the throttle reasons seen
+    active while the timed region ran, from nvidia-smi's CSV rows."""
+    rows = [
+        "0, 2070, 2070, 910.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1201.7, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbled line",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    s = bench.ClockSampler(0)
+    s.proc = object()                      # stands for the sampling process
+    s.out = open(path, "a")
+    try:
+        summary = s.summary()
+    finally:
+        s.out.close()
+    assert summary == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not path.exists()               # the temporary record is removed
+
+
+def test_clock_record_absent_without_sampler():
+    assert bench.ClockSampler(0).summary() is None
