@@ -108,7 +108,7 @@ struct Epilogue {
     double *partial;
     const int *stop;         // when non-null and *stop != 0, the launch does nothing
     const void *old;         // where out_old is read (same storage type); null = the output itself
-    float *weighted;         // forward, v-fastest output only: when non-null, also receives
+    float *weighted = nullptr;  // forward, v-fastest output only: when non-null, also receives
                              // |d'| * (stored output), the transpose's input (launch_backward)
 };
 

@@ -182,7 +182,7 @@ static cbct_status gmres_solve(const cbct_geometry *geom, const float *b, float 
     const int64_t len = ab ? n : m;                 // Krylov vectors: projections (AB) or volumes (BA)
     const int ld = iters + 1;                       // Hessenberg: column-major (iters + 1) x iters
     Workspace ws(s);
-    SolveIO io;
+    SolveIO io{};
     cbct_status st = setup_io(geom, b, x, ws, io);
     if (st != CBCT_OK) return st;
     Tracker tr;

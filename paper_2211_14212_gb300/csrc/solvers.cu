@@ -375,7 +375,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     const int iters = o->iters;
     const int nf = forward_num_blocks(g), nb = backward_num_blocks(g);
     Workspace ws(s);
-    SolveIO io;
+    SolveIO io{};
     cbct_status st = setup_io(geom, b, x, ws, io);
     if (st != CBCT_OK) return st;
 
@@ -605,7 +605,7 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     const int iters = o->iters;
     const int nf = forward_num_blocks(g);
     Workspace ws(s);
-    SolveIO io;
+    SolveIO io{};
     cbct_status st = setup_io(geom, b, x, ws, io);
     if (st != CBCT_OK) return st;
     float *r = nullptr, *q = nullptr, *sv = nullptr, *p = nullptr, *wr = nullptr;

@@ -188,7 +188,7 @@ static cbct_status cgls_tv_solve(const cbct_geometry *geom, const float *b, floa
     const VolIndex vi{g.nx, g.ny, g.nz};
     const int nf = forward_num_blocks(g);
     Workspace ws(s);
-    SolveIO io;
+    SolveIO io{};
     cbct_status st = setup_io(geom, b, x, ws, io);
     if (st != CBCT_OK) return st;
     float *w = nullptr, *ra = nullptr, *rd = nullptr, *qa = nullptr, *qd = nullptr, *p = nullptr, *sv = nullptr,

@@ -1,6 +1,7 @@
 """Host-side parts of bench.py on the CPU: the oracle's CPU-baseline sample and
 the reference arm's JSON line (the FP64 oracle timed on the host cores), on a
-tiny workload in place of the 256^3 one; and the clock-record summary."""
+tiny workload in place of the 256^3 one; the clock-record summary; and the
+source hash that keys the stored ncu counters."""
 import json
 import os
 import sys
@@ -83,3 +84,21 @@ def test_clock_record_summary(tmp_path):
 
 def test_clock_record_absent_without_sampler():
     assert bench.ClockSampler(0).summary() is None
+
+
+def test_projector_hash_ignores_comments_only():
+    """The ncu counters stay attached to the kernels while only comments or
+    whitespace change, and detach when the code changes."""
+    base = {"projector.cu": 'int f(int a) { return a + 1; } // one\n/* two */ const char *s = "//x /*y*/";\n',
+            "projector_device.cuh": "#pragma once\nint g();\n"}
+    h = bench.projector_hash(base)
+    recommented = {"projector.cu": '/* header */\nint f(int a)\n{\n    return a + 1;  // changed note\n}\n'
+                                   'const char *s = "//x /*y*/";\n',
+                   "projector_device.cuh": "#pragma once   // guard\nint g();\n"}
+    assert bench.projector_hash(recommented) == h
+    changed = dict(base, **{"projector.cu": base["projector.cu"].replace("a + 1", "a + 2")})
+    assert bench.projector_hash(changed) != h
+    in_string = dict(base, **{"projector.cu": base["projector.cu"].replace('"//x /*y*/"', '"//x /*z*/"')})
+    assert bench.projector_hash(in_string) != h
+    assert bench.code_only('a /* b */ c // d\n  e') == "a c e"
+
