@@ -3,8 +3,8 @@
  *
  * The library computes the two matrix-vector products every Krylov method of
  * Sabate Landman, Biguri et al., "On Krylov Methods for Large Scale CBCT
- * Reconstruction", spends its time on (Sec. 2: "the computational cost ... is
- * dominated by a matrix vector product by A and A^T per iteration"):
+ * Reconstruction", spends its time on (Sec. 2: one product with A and one with
+ * A^T make up almost all of an iteration's cost):
  *
  *   y = A x     forward projection, A in R^{N x M} (Sec. 1, Eq. 1),
  *   x = A^T y   its exact transpose (backprojection),
@@ -271,8 +271,8 @@ cbct_status cbct_ab_gmres_solve(const cbct_geometry *geom, const float *b, float
 cbct_status cbct_ba_gmres_solve(const cbct_geometry *geom, const float *b, float *x,
                                 const cbct_solve_opts *opts, cbct_solve_report *report, cbct_stream stream);
 
-/* Hybrid LSMR: the generalisation of the hybrid method to LSMR that Sec. 2.2.2
- * mentions (replace the projected matrix and right-hand side): Tikhonov on
+/* Hybrid LSMR: the extension of the hybrid method to LSMR that Sec. 2.2.2
+ * mentions (LSMR's own projected system in place of LSQR's): Tikhonov on
  * LSMR's projected problem, y_k = argmin ||alpha_1 beta_1 e_1 - Hbar_k y||^2 +
  * lambda_k^2 ||y||^2 with Hbar_k = [H_k^T H_k ; alpha_{k+1} beta_{k+1} e_k^T],
  * x_k = V_k y_k (x_k minimises ||A^T (b - A x)||^2 + lambda_k^2 ||x||^2 over

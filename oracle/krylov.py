@@ -482,9 +482,8 @@ def hybrid_lsmr(op, b, iters, rule="gcv", lam=0.0, keep_iterates=False):
         y_k = argmin ||alpha_1 beta_1 e_1 - Hbar_k y||^2 + lam_k^2 ||y||^2,
     x_k = V_k y_k, i.e. x_k minimises ||A^T (b - A x)||^2 + lam_k^2 ||x||^2 over
     K_k(A^T A, A^T b); lam_k fixed or by GCV on the projected problem.  The
-    paper (Sec. 2.2.2) notes that GCV generalises to other Krylov methods such
-    as LSMR by replacing the projected matrix and right-hand side; this is that
-    replacement.  History: ``normal_resid`` = ||alpha_1 beta_1 e_1 - Hbar_k y_k||
+    paper (Sec. 2.2.2) remarks that GCV carries over to LSMR with LSMR's own
+    small projected system in place of LSQR's; this is that system.  History: ``normal_resid`` = ||alpha_1 beta_1 e_1 - Hbar_k y_k||
     (= ||A^T r_k|| in exact arithmetic), ``lambda``, ``alpha``/``beta``."""
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     x = np.zeros(op.shape[1])
