@@ -540,3 +540,16 @@ def test_voxel_driven_backprojector_interpolates_exactly_and_approximates_the_tr
     r = bp(np.ones(full.num_rays)).reshape(full.vol_shape) / op.rmatvec(np.ones(full.num_rays)).reshape(full.vol_shape)
     inner = r[2:-2, 2:-2, 2:-2]
     assert 0.9 < inner.mean() < 1.1
+
+
+def test_voxel_driven_weight_is_the_ray_density():
+    """With pixels much finer than the voxels (20 rays per voxel width at the
+    rotation centre) A^T 1 at a voxel is its volume times the density of rays
+    through it, which the voxel-driven weight dx dy dz mag^2 |d'| / (du dv DSD)
+    states in closed form: B 1 = A^T 1 per voxel within 0.5 %, on a wide cone
+    (|d'| / DSD up to 1.03 averaged over the angles, so a dropped |d'| factor,
+    a wrong power of mag or a missing pixel area fails)."""
+    g = synth.Geometry(8, 8, 8, 1.0, 1.0, 1.0, 300, 300, 0.1, 0.1, 20.0, 40.0, synth.circular_angles(8))
+    ones = np.ones(g.proj_shape)
+    ratio = krylov.VoxelDrivenBackprojector(g)(ones) / oracle.backproject(g, ones).ravel()
+    assert np.abs(ratio - 1.0).max() < 5e-3
