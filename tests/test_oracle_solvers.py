@@ -437,6 +437,36 @@ def test_gradient_adjoint_and_tv_closed_form():
     assert abs(krylov.total_variation(c) - tv) <= 1e-12
 
 
+def test_irn_weights_give_the_tv_majorant():
+    """IRN (Sec. 2.3) works because, per voxel, sqrt(t) <= t / (2 sqrt(c)) +
+    sqrt(c) / 2 (equality at t = c): with w = W(D x_k) the quadratic
+        Q(x) = sum (|D x|^2 + tau^2) w^2 / 2 + 1 / (2 w^2)
+    majorises the smoothed TV, sum sqrt(|D x|^2 + tau^2), and touches it at
+    x_k.  Only the exponent -1/4 in w gives both; and as tau -> 0,
+    ||W(Dx) D x||^2 tends to TV(x)."""
+    rng = np.random.default_rng(43)
+    tau = 0.1
+    xk = rng.standard_normal((5, 6, 7))
+    w2 = krylov.irn_weights(xk, tau) ** 2
+
+    def smoothed_tv(x):
+        return float(np.sum(np.sqrt(np.sum(krylov.grad3(x) ** 2, axis=0) + tau * tau)))
+
+    def q(x):
+        t = np.sum(krylov.grad3(x) ** 2, axis=0) + tau * tau
+        return float(np.sum(t * w2 / 2 + 1 / (2 * w2)))
+
+    assert abs(q(xk) - smoothed_tv(xk)) <= 1e-12 * smoothed_tv(xk)
+    for _ in range(20):
+        x = xk + rng.standard_normal(xk.shape) * rng.uniform(0.01, 3.0)
+        assert q(x) >= smoothed_tv(x) * (1 - 1e-12)
+    c = np.zeros((6, 6, 6))
+    c[2:4, 2:4, 2:4] = 1.0
+    wc = krylov.irn_weights(c, 1e-9)
+    weighted = float(np.sum(wc ** 2 * np.sum(krylov.grad3(c) ** 2, axis=0)))
+    assert abs(weighted - krylov.total_variation(c)) <= 1e-8 * krylov.total_variation(c)
+
+
 def test_cgls_tv_inner_solve_is_the_weighted_tikhonov_solution(tiny_system):
     """One outer step with enough inner iterations reaches the solution of the
     normal equations (A^T A + lam^2 D^T W^2 D) x = A^T b (dense solve)."""
