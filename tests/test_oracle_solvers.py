@@ -583,3 +583,23 @@ def test_voxel_driven_weight_is_the_ray_density():
     ones = np.ones(g.proj_shape)
     ratio = krylov.VoxelDrivenBackprojector(g)(ones) / oracle.backproject(g, ones).ravel()
     assert np.abs(ratio - 1.0).max() < 5e-3
+
+
+def test_sirt_weighted_backprojector_inverts_a_on_constants():
+    """With R = 1 / (A 1) and C = 1 / (A^T 1), B = C A^T R maps A 1 back to 1
+    on every voxel some ray meets (R A 1 = 1 on every ray that meets the
+    volume, then C A^T 1 = 1), and B y is zero where no ray meets the voxel;
+    swapping R and C, or dropping either, breaks it.  B is not A^T: <A x, y> and
+    <x, B y> differ."""
+    g = synth.Geometry(10, 9, 8, 1.0, 1.0, 1.0, 4, 10, 1.3, 1.3, 60.0, 100.0, np.radians([0.0, 90.0]))
+    op = oracle.Operator(g)
+    bw = krylov.WeightedBackprojector(op)
+    one = np.ones(op.shape[1])
+    met = op.rmatvec(np.ones(op.shape[0])) > 0
+    assert 0 < met.sum() < met.size                          # the narrow detector misses the corners
+    out = bw(op.matvec(one))
+    np.testing.assert_allclose(out[met], 1.0, rtol=1e-12)
+    assert np.all(out[~met] == 0.0)
+    rng = np.random.default_rng(44)
+    x, y = rng.standard_normal(op.shape[1]), rng.standard_normal(op.shape[0])
+    assert abs(np.dot(op.matvec(x), y) - np.dot(x, bw(y))) > 1e-3 * abs(np.dot(op.matvec(x), y))
