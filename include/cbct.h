@@ -80,9 +80,14 @@ typedef struct {
 typedef struct cbct_geometry cbct_geometry;   /* opaque, library-owned */
 
 /* Builds the device-side ray tables of a scan (on the current CUDA device).
- * On success *out owns device memory until cbct_geometry_destroy. */
+ * On success *out owns device memory until cbct_geometry_destroy.  Every
+ * call below that queues GPU work for a geometry must be made with the
+ * geometry's device current; otherwise it returns CBCT_EINVAL before any
+ * work is queued (the caller's buffers must live on that device too). */
 cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct_geometry **out);
 void cbct_geometry_destroy(cbct_geometry *geom);
+/* Ordinal of the CUDA device the geometry's tables live on, or -1 for NULL. */
+int cbct_geometry_device(const cbct_geometry *geom);
 int64_t cbct_geometry_num_voxels(const cbct_geometry *geom);   /* M, or -1 for NULL */
 int64_t cbct_geometry_num_rays(const cbct_geometry *geom);     /* N, or -1 for NULL */
 

@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH):
     lib.cbct_geometry_num_voxels.restype = i64
     lib.cbct_geometry_num_rays.argtypes = [G]
     lib.cbct_geometry_num_rays.restype = i64
+    lib.cbct_geometry_device.argtypes = [G]
+    lib.cbct_geometry_device.restype = ctypes.c_int
     for fn in ("cbct_project", "cbct_backproject", "cbct_project_static"):
         getattr(lib, fn).argtypes = [G, vp, vp, ctypes.c_int, vp]
     lib.cbct_count_nnz.argtypes = [G, ctypes.POINTER(i64), vp]
@@ -189,6 +191,7 @@ class Geometry:
         self._h = h
         self.num_voxels = int(lib.cbct_geometry_num_voxels(h))
         self.num_rays = int(lib.cbct_geometry_num_rays(h))
+        self.device = int(lib.cbct_geometry_device(h))
         self.vol_shape = (int(kw["nz"]), int(kw["ny"]), int(kw["nx"]))
         self.proj_shape = (int(self.angles.shape[0]), int(kw["nv"]), int(kw["nu"]))
 
@@ -208,9 +211,13 @@ class Geometry:
             pass
 
 
-def _require_cuda(t, name, numel):
+def _require_cuda(t, name, numel, device=None):
+    """A contiguous CUDA tensor of `numel` elements, on CUDA device `device`
+    (the geometry's) when given."""
     if not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
+    if device is not None and t.device.index != device:
+        raise ValueError("%s is on cuda:%s but the geometry lives on cuda:%d" % (name, t.device.index, device))
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
     if t.numel() != numel:
@@ -220,10 +227,10 @@ def _require_cuda(t, name, numel):
 def project(geom: Geometry, x, out=None, stream=None):
     """y = A x on the GPU (cbct_project); x and y share one dtype (f32/f16/bf16)."""
     import torch
-    _require_cuda(x, "x", geom.num_voxels)
+    _require_cuda(x, "x", geom.num_voxels, geom.device)
     if out is None:
         out = torch.empty(geom.proj_shape, dtype=x.dtype, device=x.device)
-    _require_cuda(out, "out", geom.num_rays)
+    _require_cuda(out, "out", geom.num_rays, geom.device)
     if out.dtype != x.dtype:
         raise TypeError("x and out must share a dtype")
     _check("cbct_project", load().cbct_project(geom.handle, ctypes.c_void_p(x.data_ptr()),
@@ -236,12 +243,12 @@ def backproject_voxel_driven(geom: Geometry, y, out=None, stream=None):
     """The voxel-driven interpolating approximation of A^T (not its transpose),
     FP32 (cbct_backproject_voxel_driven)."""
     import torch
-    _require_cuda(y, "y", geom.num_rays)
+    _require_cuda(y, "y", geom.num_rays, geom.device)
     if y.dtype != torch.float32:
         raise TypeError("y must be float32")
     if out is None:
         out = torch.empty(geom.vol_shape, dtype=torch.float32, device=y.device)
-    _require_cuda(out, "out", geom.num_voxels)
+    _require_cuda(out, "out", geom.num_voxels, geom.device)
     _check("cbct_backproject_voxel_driven",
            load().cbct_backproject_voxel_driven(geom.handle, ctypes.c_void_p(y.data_ptr()),
                                                 ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
@@ -252,10 +259,10 @@ def project_static(geom: Geometry, x, out=None, stream=None):
     """y = A x like project(), through cbct_project_static, which allocates no
     device memory (volume of at most 64 MiB; calls must not overlap on the GPU)."""
     import torch
-    _require_cuda(x, "x", geom.num_voxels)
+    _require_cuda(x, "x", geom.num_voxels, geom.device)
     if out is None:
         out = torch.empty(geom.proj_shape, dtype=x.dtype, device=x.device)
-    _require_cuda(out, "out", geom.num_rays)
+    _require_cuda(out, "out", geom.num_rays, geom.device)
     if out.dtype != x.dtype:
         raise TypeError("x and out must share a dtype")
     _check("cbct_project_static", load().cbct_project_static(geom.handle, ctypes.c_void_p(x.data_ptr()),
@@ -267,10 +274,10 @@ def project_static(geom: Geometry, x, out=None, stream=None):
 def backproject(geom: Geometry, y, out=None, stream=None):
     """x = A^T y on the GPU (cbct_backproject), the exact transpose of project()."""
     import torch
-    _require_cuda(y, "y", geom.num_rays)
+    _require_cuda(y, "y", geom.num_rays, geom.device)
     if out is None:
         out = torch.empty(geom.vol_shape, dtype=y.dtype, device=y.device)
-    _require_cuda(out, "out", geom.num_voxels)
+    _require_cuda(out, "out", geom.num_voxels, geom.device)
     if out.dtype != y.dtype:
         raise TypeError("y and out must share a dtype")
     _check("cbct_backproject", load().cbct_backproject(geom.handle, ctypes.c_void_p(y.data_ptr()),
@@ -441,12 +448,12 @@ def _solve(fn, geom, b, iters, lam=0.0, storage="f32", rule="gcv", use_graph=Tru
     lib = load()
     on_device = isinstance(b, torch.Tensor) and b.is_cuda
     if on_device:
-        _require_cuda(b, "b", geom.num_rays)
+        _require_cuda(b, "b", geom.num_rays, geom.device)
         if b.dtype != torch.float32:
             raise TypeError("b must be float32")
         if x is None:
             x = torch.empty(geom.vol_shape, dtype=torch.float32, device=b.device)
-        _require_cuda(x, "x", geom.num_voxels)
+        _require_cuda(x, "x", geom.num_voxels, geom.device)
         bptr, xptr = b.data_ptr(), x.data_ptr()
     else:
         bh = b.numpy() if isinstance(b, torch.Tensor) else np.asarray(b)

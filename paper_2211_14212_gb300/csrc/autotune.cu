@@ -79,6 +79,8 @@ extern "C" cbct_status cbct_geometry_get_angle_block(const cbct_geometry *g, int
 extern "C" cbct_status cbct_geometry_autotune(cbct_geometry *g, int max_angles, double *times_ms,
                                               cbct_stream stream) {
     if (!g) { set_error("cbct_geometry_autotune: null geometry"); return CBCT_EINVAL; }
+    const cbct_status dst = require_geometry_device(g, "cbct_geometry_autotune");
+    if (dst != CBCT_OK) return dst;
     cudaStream_t s = (cudaStream_t)stream;
     const int na = g->desc.nangles;
     const int keep = max_angles > 0 && max_angles < na ? max_angles : na;

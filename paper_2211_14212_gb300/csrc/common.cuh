@@ -132,6 +132,13 @@ __device__ __forceinline__ double block_sum(double v, double *scratch /* NT/32 d
 
 // ---------------------------------------------------------------- host side
 void set_error(const std::string &msg);
+// CBCT_OK when the calling thread's current CUDA device is the one the
+// geometry's tables were created on; CBCT_EINVAL (message names `who` and
+// both devices) otherwise, CBCT_ECUDA when the current device cannot be read.
+// Every entry point that launches work for a geometry checks this first: a
+// launch on another device would read the tables and the caller's buffers
+// through addresses that are not valid there.
+cbct_status require_geometry_device(const cbct_geometry *g, const char *who);
 cbct_status validate_geometry_desc(const cbct_geometry_desc *d);   // CBCT_EINVAL with a message
 cbct_status cuda_fail(cudaError_t err, const char *what);
 

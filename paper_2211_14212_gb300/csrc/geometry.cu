@@ -28,6 +28,20 @@ static cbct_status invalid(const char *msg) {
     return CBCT_EINVAL;
 }
 
+cbct_status require_geometry_device(const cbct_geometry *g, const char *who) {
+    int dev = -1;
+    const cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return cuda_fail(err, who);
+    if (dev != g->device) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "%s: the geometry lives on CUDA device %d but the current device is %d", who,
+                 g->device, dev);
+        set_error(buf);
+        return CBCT_EINVAL;
+    }
+    return CBCT_OK;
+}
+
 // Per-ray constants of one axis: the index pq of the plane nearest to the ray
 // origin q, the offset f = plane(pq) - q (mm) and I = 1 / d (d = direction
 // component along the axis).  Exactly parallel rays keep a fixed voxel index
@@ -191,6 +205,8 @@ extern "C" void cbct_geometry_destroy(cbct_geometry *g) {
     delete[] g->angles;
     delete g;
 }
+
+extern "C" int cbct_geometry_device(const cbct_geometry *g) { return g ? g->device : -1; }
 
 extern "C" int64_t cbct_geometry_num_voxels(const cbct_geometry *g) {
     return g ? (int64_t)g->dev.nx * g->dev.ny * g->dev.nz : -1;

@@ -56,12 +56,8 @@ extern "C" cbct_status cbct_project_static(const cbct_geometry *g, const void *x
                   "(at most 2^24 FP32 or 2^25 FP16/BF16 voxels)");
         return CBCT_EINVAL;
     }
-    int dev = 0;
-    CBCT_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev != g->device) {
-        set_error("cbct_project_static: the geometry's device is not the current device");
-        return CBCT_EINVAL;
-    }
+    cbct_status st0 = require_geometry_device(g, "cbct_project_static");
+    if (st0 != CBCT_OK) return st0;
     void *scratch = nullptr;
     cbct_status st = scratch_for_current_device(&scratch);
     if (st != CBCT_OK) return st;

@@ -404,15 +404,15 @@ cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_d
 
 using namespace cbct;
 
-static cbct_status check_pair(const cbct_geometry *g, const void *a, const void *b, cbct_dtype t) {
-    if (!g || !a || !b) { set_error("null geometry or buffer"); return CBCT_EINVAL; }
-    if (t != CBCT_F32 && t != CBCT_F16 && t != CBCT_BF16) { set_error("unknown dtype"); return CBCT_EINVAL; }
-    return CBCT_OK;
+static cbct_status check_pair(const cbct_geometry *g, const void *a, const void *b, cbct_dtype t, const char *who) {
+    if (!g || !a || !b) { set_error(std::string(who) + ": null geometry or buffer"); return CBCT_EINVAL; }
+    if (t != CBCT_F32 && t != CBCT_F16 && t != CBCT_BF16) { set_error(std::string(who) + ": unknown dtype"); return CBCT_EINVAL; }
+    return require_geometry_device(g, who);
 }
 
 extern "C" cbct_status cbct_project(const cbct_geometry *g, const void *x, void *y, cbct_dtype t,
                                     cbct_stream stream) {
-    cbct_status st = check_pair(g, x, y, t);
+    cbct_status st = check_pair(g, x, y, t, "cbct_project");
     if (st != CBCT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     // the forward kernel reads the z-fastest layout: re-lay the caller's volume first
@@ -429,7 +429,7 @@ extern "C" cbct_status cbct_project(const cbct_geometry *g, const void *x, void 
 
 extern "C" cbct_status cbct_backproject(const cbct_geometry *g, const void *y, void *x, cbct_dtype t,
                                         cbct_stream stream) {
-    cbct_status st = check_pair(g, y, x, t);
+    cbct_status st = check_pair(g, y, x, t, "cbct_backproject");
     if (st != CBCT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     // the transpose reads |d'| * y, v-fastest: re-lay and weight the caller's stack first
@@ -455,6 +455,8 @@ extern "C" cbct_status cbct_backproject(const cbct_geometry *g, const void *y, v
 
 extern "C" cbct_status cbct_count_nnz(const cbct_geometry *g, int64_t *nnz, cbct_stream stream) {
     if (!g || !nnz) { set_error("cbct_count_nnz: null argument"); return CBCT_EINVAL; }
+    const cbct_status dst = require_geometry_device(g, "cbct_count_nnz");
+    if (dst != CBCT_OK) return dst;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *d = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync(&d, sizeof(unsigned long long), s));

@@ -235,7 +235,7 @@ inline cbct_status check_solve_args(const cbct_geometry *g, const float *b, floa
         set_error("solver: stop_tol must be in [0, 1)");
         return CBCT_EINVAL;
     }
-    return CBCT_OK;
+    return require_geometry_device(g, "solver");
 }
 
 // Stage host b / x through device memory when needed.

@@ -94,6 +94,8 @@ using namespace cbct;
 extern "C" cbct_status cbct_backproject_voxel_driven(const cbct_geometry *g, const float *y, float *x,
                                                      cbct_stream stream) {
     if (!g || !y || !x) { set_error("cbct_backproject_voxel_driven: null argument"); return CBCT_EINVAL; }
+    const cbct_status dst = require_geometry_device(g, "cbct_backproject_voxel_driven");
+    if (dst != CBCT_OK) return dst;
     cudaStream_t s = (cudaStream_t)stream;
     float *tmp = nullptr;
     CBCT_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)cbct_geometry_num_rays(g) * sizeof(float), s));

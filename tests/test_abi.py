@@ -97,3 +97,32 @@ def test_server_argument_checks(lib):
     assert lib.cbct_server_poll(None, 1, ctypes.byref(done)) == cbct.CBCT_EINVAL
     assert lib.cbct_server_wait(None, 1, 0.0, None, None, None) == cbct.CBCT_EINVAL
     lib.cbct_server_destroy(None)
+
+
+def test_geometry_device_of_null(lib):
+    assert lib.cbct_geometry_device(None) == -1
+
+
+def test_binding_rejects_tensors_on_another_device():
+    """The binding refuses a buffer on another CUDA device than the
+    geometry's before calling the library (the library itself refuses a call
+    made while another device is current)."""
+    from paper_2211_14212_gb300 import cbct
+
+    class Device:
+        index = 1
+
+    class Tensor:
+        is_cuda = True
+        device = Device()
+
+        def is_contiguous(self):
+            return True
+
+        def numel(self):
+            return 10
+
+    with pytest.raises(ValueError, match="geometry lives on cuda:0"):
+        cbct._require_cuda(Tensor(), "x", 10, 0)
+    cbct._require_cuda(Tensor(), "x", 10, 1)
+    cbct._require_cuda(Tensor(), "x", 10)
