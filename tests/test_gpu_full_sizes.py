@@ -3,10 +3,19 @@
 512^3 / 768 x 512 / 720 angles (the precision-study scan) and 1024^3 /
 1536^2 / 1600 angles at magnification 6 (the micro-CT scan) are too large for
 whole oracle products, so the oracle computes sampled rays and voxels one by
-one; the GPU dot-product test covers every element.  At 512^3 the hybrid
-LSQR precision variants (FP32 / FP16 / BF16 storage) are run at the full
-iteration count and compared with each other.
+one; the GPU dot-product test covers every element.  At 512^3 the FP16 and
+BF16 projectors are compared with the FP64 oracle's stored values
+(tests/golden/precision_reference.json), and the hybrid LSQR precision
+variants (FP32 / FP16 / BF16 storage) are run at the full iteration count and
+compared with each other; at 64^3 every storage variant of LSQR, LSMR and
+hybrid LSQR is compared with the FP64 oracle's stored iterates.  At 1024^3
+the transpose is checked on sampled voxels with a projection stack that is
+nonzero on 41 of the 1600 angles (the last one among them, so that the
+projection offsets pass 2^31): the oracle sums those angles alone.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +25,11 @@ import synth
 pytestmark = pytest.mark.gpu
 
 REL_L2 = 1e-5
+PRECISION = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "precision_reference.json")
+# Relative 2-norm error against FP64 allowed for reduced-precision storage
+# (parity unpinned as exact): a few units of the storage format's rounding,
+# u = 2^-11 (FP16) and 2^-8 (BF16), on the inputs and on the stored outputs.
+STORAGE_BOUND = {"f32": REL_L2, "f16": 2e-3, "bf16": 1.6e-2}
 
 
 @pytest.fixture(scope="module")
@@ -123,6 +137,63 @@ def test_c3_hybrid_precision_variants(cbct, c3):
         assert abs(rep.lam[-1] - r32.lam[-1]) <= 10 * bound * r32.lam[-1]
 
 
+@pytest.fixture(scope="module")
+def precision_ref():
+    with open(PRECISION) as f:
+        return json.load(f)
+
+
+def torch_dtype(name):
+    import torch
+    return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[name]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_c3_storage_precision_projectors(cbct, precision_ref, storage):
+    """A x and A^T y with volume and projections stored in FP32 / FP16 / BF16
+    (FP32 ray and voxel sums, Kahan-compensated for the 16-bit formats)
+    against the FP64 oracle's values at sampled rays and voxels."""
+    import torch
+    ref = precision_ref["c3"]
+    g = synth.config("c3")
+    geom = cbct.Geometry(g)
+    dt = torch_dtype(storage)
+    x = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=ref["phantom_seed"], scale=0.02)).cuda().to(dt)
+    y = cbct.project(geom, x)
+    del x
+    got = y.view(-1)[torch.from_numpy(np.asarray(ref["rays"])).cuda()].double().cpu().numpy()
+    del y
+    fwd = rel_l2(got, ref["project_rays"])
+    yp = torch.from_numpy(synth.random_projections(g, ref["y_seed"]).astype(np.float32)).cuda().to(dt)
+    xb = cbct.backproject(geom, yp)
+    del yp
+    got = xb.view(-1)[torch.from_numpy(np.asarray(ref["voxels"])).cuda()].double().cpu().numpy()
+    bwd = rel_l2(got, ref["backproject_voxels"])
+    print("%s storage at 512^3: A x rel err vs FP64 %.3g, A^T y %.3g" % (storage, fwd, bwd))
+    assert fwd <= STORAGE_BOUND[storage] and bwd <= STORAGE_BOUND[storage]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_medium_storage_precision_solvers(cbct, precision_ref, storage):
+    """LSQR, LSMR and hybrid LSQR (GCV), 20 iterations, on the 64^3 scan
+    with FP32 / FP16 / BF16 storage of every Krylov vector (FP64 scalars)
+    against the FP64 oracle's iterates at sampled voxels; FP32 storage meets
+    the 1e-4 iterate bar, the 16-bit formats their storage bounds (reported)."""
+    import torch
+    ref = precision_ref["medium"]
+    g = synth.Geometry(64, 64, 64, 4.0, 4.0, 4.0, 128, 128, 3.2, 3.2, 1000.0, 1536.0, synth.circular_angles(90))
+    geom = cbct.Geometry(g)
+    b = torch.from_numpy(synth.random_projections(g, ref["b_seed"]).astype(np.float32)).cuda()
+    vox = torch.from_numpy(np.asarray(ref["voxels"])).cuda()
+    bound = {"f32": 1e-4, "f16": 5e-3, "bf16": 3e-2}[storage]
+    for method in ("lsqr", "lsmr", "hybrid_lsqr"):
+        x, rep = getattr(cbct, method)(geom, b, ref["iters"], storage=storage)
+        assert rep.iters_done == ref["iters"]
+        err = rel_l2(x.view(-1)[vox].double().cpu().numpy(), ref[method]["sampled"])
+        print("%s, %s storage, k = %d: rel err vs FP64 %.3g" % (method, storage, ref["iters"], err))
+        assert err <= bound
+
+
 # ------------------------------------------------- 1024^3, 1600 angles (micro-CT)
 @pytest.fixture(scope="module")
 def c5():
@@ -139,3 +210,31 @@ def test_c5_dot_product(cbct, c5):
     import torch
     g, x = c5
     dot_test(cbct, cbct.Geometry(g), g, torch.from_numpy(x).cuda(), 32)
+
+
+def test_c5_backward_sampled_voxels(cbct, c5):
+    """A^T y at 1024^3 on 250 sampled voxels (random, plus the corners of the
+    volume), y nonzero on every 40th angle and the last one (41 angles,
+    seeded uniform values): the GPU transpose over all 1600 angles against
+    the oracle's voxel route over those 41 (zero projections add nothing)."""
+    import torch
+    g, _ = c5
+    keep = sorted(set(range(0, g.nangles, 40)) | {g.nangles - 1})
+    sub = g.with_angles(g.angles[keep])
+    ysub = synth.random_projections(sub, 33).astype(np.float32)
+    geom = cbct.Geometry(g)
+    y = torch.zeros(g.proj_shape, device="cuda")
+    y[torch.tensor(keep, device="cuda")] = torch.from_numpy(ysub).cuda()
+    xb = cbct.backproject(geom, y)
+    del y
+    rng = np.random.default_rng(34)
+    vox = set(rng.choice(g.num_voxels, size=242, replace=False).tolist())
+    for k in (0, g.nz - 1):
+        for j in (0, g.ny - 1):
+            for i in (0, g.nx - 1):
+                vox.add((k * g.ny + j) * g.nx + i)
+    vox = np.array(sorted(vox), dtype=np.int64)
+    got = xb.view(-1)[torch.from_numpy(vox).cuda()].double().cpu().numpy()
+    ref = oracle.backproject_voxels(sub, ysub.astype(np.float64), vox)
+    assert rel_l2(got, ref) <= REL_L2
+    assert elementwise_ok(got, ref).all()

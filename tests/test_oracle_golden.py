@@ -78,3 +78,18 @@ def test_c1_extended_solver_histories(golden):
             np.testing.assert_allclose(h["resid"], c["%s_gmres_%s_resid" % (variant, name)], rtol=RTOL)
     _, h = krylov.cgls_tv(op, g.vol_shape, bn, 2, 3, 2.0, 1e-2)
     np.testing.assert_allclose(h["resid"], c["cgls_tv_resid"], rtol=RTOL)
+
+
+def test_precision_reference_values():
+    """The stored FP64 values of the storage-precision study (written by
+    tests/golden/make_golden_precision.py from the oracle) are the oracle's:
+    20 of the 512^3 scan's sampled rays and 5 of its sampled voxels recomputed."""
+    with open(os.path.join(os.path.dirname(GOLDEN), "precision_reference.json")) as f:
+        ref = json.load(f)["c3"]
+    g = synth.config("c3")
+    x = synth.ellipsoid_phantom(g, 10, seed=ref["phantom_seed"], scale=0.02).astype(np.float64)
+    rays = np.asarray(ref["rays"][::100])
+    np.testing.assert_allclose(oracle.project_rays(g, x, rays), ref["project_rays"][::100], rtol=RTOL)
+    sub = np.asarray(ref["voxels"][::40])
+    y = synth.random_projections(g, ref["y_seed"]).astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(oracle.backproject_voxels(g, y, sub), ref["backproject_voxels"][::40], rtol=RTOL)
