@@ -9,12 +9,21 @@ FP32 vectors, FP64 scalars).
 
 Printed JSON line (rank 0):
   value      ray-voxel Gupdates/s of the whole step (nnz(A) x projector
-             launches / step time), inputs resident in HBM;
+             launches / step time), inputs resident in HBM, on the solvers'
+             default path (one CUDA graph per iteration, replayed);
   e2e        the same metric with b read from pinned host memory and x
              written back to the host inside the timed region;
-  roofline   the dominant projector kernel: nnz x 4 B gathered per launch /
-             its CUDA-event launch time, against the measured HBM copy peak;
-  cpu_baseline  the FP64 oracle on the host cores, on an 8-angle sample.
+  roofline   the dominant projector kernel (per-launch CUDA-event times from
+             one extra profiled step): nnz x 4 B gathered per launch / its
+             launch time against the measured HBM copy peak, and the bound
+             t_bound = max(compulsory HBM bytes / HBM peak, gather bytes /
+             L2 peak, warp instructions / issue peak) term by term;
+  serving    the serving stream (64 requests of 128^3..384^3 scans, Poisson
+             arrivals at 0.8 of the one-at-a-time throughput) through the
+             continuous-batching server and through the one-request-at-a-time
+             solver, both fed in real time: recon/s, p50 / p99 / mean latency
+             and the largest relative difference between their results;
+  cpu_baseline  the FP64 oracle on the host cores, on a 24-angle sample.
 `--impl reference` times that oracle alone (the CPU reference arm).
 Multi-GPU (torchrun): independent replicas, one per rank, weak scaling.
 """
@@ -40,16 +49,15 @@ BYTES_PER_UPDATE = 4          # one FP32 voxel (forward) or projection (backward
 CPU_SAMPLE_ANGLES = 24          # about 20 s of FP64 oracle work on 16 host cores
 REF_STEP_ANGLES = 8             # --impl reference: about 7 s per step, so K steps stay within minutes
 
-# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by the code of the projector sources it was measured on
-# (projector_hash(), comments ignored); the bench reports null once that code
-# changed.
-NCU_TRAFFIC = {
-    # one launch of the 2x4x128 transpose tile at 256^3 / 512^2 / 360 (ncu --set full,
-    # the cbct_backproject launch of the projectors mode; the solver's launch of the
-    # same tile differs only in the output layout): 11.800 GB read + 0.122 GB written
-    "backward": (11921397568, "5075f4334a6e209e"),
-}
+# Counters of one launch of each solver projector kernel at 256^3 / 512^2 /
+# 360 from ncu (dram__bytes_read.sum + dram__bytes_write.sum, and
+# smsp__inst_executed.sum = warp instructions), keyed by the code of the
+# projector sources they were measured on (projector_hash(), comments
+# ignored); the bench reports null once that code changed.
+NCU_COUNTERS = {}
+
+# Instruction issue: one warp instruction per cycle per SM sub-partition.
+SMS, SUBPARTITIONS = 152, 4
 
 
 def workload_config():
@@ -232,6 +240,39 @@ def run_reference(args):
     return 0
 
 
+def roofline_block(g, nnz, fwd_ms, bwd_ms, clocks):
+    """Roofline of the dominant projector kernel.  `achieved` is the gather-
+    equivalent bandwidth (nnz x 4 B per launch / launch time) against the
+    measured HBM copy peak, the scope table's projector target.  The kernels
+    are bound by instruction issue, so `t_bound` lists the three floors of
+    max(compulsory HBM bytes / HBM peak, gather bytes / L2 peak, warp
+    instructions / issue peak): no L2 peak is measured on this machine (null),
+    and the warp-instruction count comes from ncu (NCU_COUNTERS, null once the
+    kernel source changed)."""
+    dominant = "forward" if fwd_ms >= bwd_ms else "backward"
+    avg_ms = fwd_ms if dominant == "forward" else bwd_ms
+    peak, peak_kind = measured_peak()
+    achieved = nnz * BYTES_PER_UPDATE / (avg_ms * 1e-3) / 1e9
+    c = NCU_COUNTERS.get(dominant)
+    fresh = c is not None and c.get("hash") == projector_hash()
+    warp_inst = c["warp_inst"] if fresh else None
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    issue_peak = SMS * SUBPARTITIONS * mhz * 1e6            # warp instructions per second
+    compulsory = (g.num_voxels + g.num_rays) * 4             # one read of the input, one write of the output
+    hbm_ms = compulsory / (peak * 1e9) * 1e3
+    issue_ms = warp_inst / issue_peak * 1e3 if warp_inst else None
+    terms = {"hbm": hbm_ms, "l2": None, "issue": issue_ms}
+    known = {k: v for k, v in terms.items() if v is not None}
+    return {"bound": "issue", "kernel": dominant, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": c["dram_bytes"] if fresh else None,
+            "avg_launch_ms": avg_ms, "forward_ms_per_launch": fwd_ms, "backward_ms_per_launch": bwd_ms,
+            "t_bound": {"hbm_ms": hbm_ms, "l2_ms": None, "issue_ms": issue_ms,
+                        "binding": max(known, key=known.get) if known else None,
+                        "notes": "hbm: (M + N) x 4 B compulsory bytes; l2: no L2 peak measured; issue: "
+                                 "ncu warp instructions of one launch / (152 SMs x 4 issue slots x SM clock)"},
+            "issue_util": issue_ms / avg_ms if issue_ms else None}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -276,15 +317,13 @@ def run_ours(args):
             step(b, x1, x2, False)
     barrier()
 
-    # ---- timed region: inputs resident in HBM
+    # ---- timed region: inputs resident in HBM, the solvers' default (graph-replayed) path
     gpu_index = local
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis and all(p.strip().isdigit() for p in vis.split(",")):
         gpu_index = int(vis.split(",")[local])
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     products = launches = 0
-    fwd_ms = bwd_ms = 0.0
-    fwd_n = bwd_n = 0
     lsqr_s = 0.0
     with ClockSampler(gpu_index) as clk:
         with torch.cuda.stream(s):
@@ -292,15 +331,11 @@ def run_ours(args):
             ev0.record(s)
             for _ in range(args.steps):
                 t0 = time.perf_counter()
-                r1, r2, t1 = step(b, x1, x2, True)
+                r1, r2, t1 = step(b, x1, x2, False)
                 lsqr_s += t1 - t0          # the solver synchronises its stream before returning
                 for r in (r1, r2):
                     products += r.forward_launches + r.backward_launches
                     launches += r.kernel_launches
-                    fwd_ms += r.forward_ms
-                    bwd_ms += r.backward_ms
-                    fwd_n += r.forward_launches
-                    bwd_n += r.backward_launches
             ev1.record(s)
             torch.cuda.nvtx.range_pop()
         barrier()
@@ -308,6 +343,17 @@ def run_ours(args):
     clocks = clk.summary()
     value = whole_job_rate(nnz * products, world, elapsed_ms * 1e-3) / 1e9
     lsqr_ips = ITERS * args.steps / lsqr_s
+
+    # ---- one profiled step (plain launches, CUDA events around every projector launch)
+    fwd_ms = bwd_ms = 0.0
+    fwd_n = bwd_n = 0
+    with torch.cuda.stream(s):
+        for r in step(b, x1, x2, True)[:2]:
+            fwd_ms += r.forward_ms
+            bwd_ms += r.backward_ms
+            fwd_n += r.forward_launches
+            bwd_n += r.backward_launches
+    barrier()
 
     # ---- end to end: b from pinned host memory, x back to host, inside the timed region
     xh1 = torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory()
@@ -323,15 +369,17 @@ def run_ours(args):
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_value = whole_job_rate(nnz * e2e_products, world, e2e_s) / 1e9
+    del x1, x2, b
+
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = serving_compare(cbct, torch, dev, args.requests, args.serving_scale, value,
+                                  args.serving_slots, args.serving_budget_gb, args.serving_schedule)
 
     if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return 0
-    dominant = "forward" if fwd_ms >= bwd_ms else "backward"
-    avg_ms = fwd_ms / max(fwd_n, 1) if dominant == "forward" else bwd_ms / max(bwd_n, 1)
-    peak, peak_kind = measured_peak()
-    achieved = nnz * BYTES_PER_UPDATE / (avg_ms * 1e-3) / 1e9
-    tr = NCU_TRAFFIC.get(dominant)
-    traffic = tr[0] if tr and tr[1] == projector_hash() else None
     cpu = None
     if not args.no_cpu_baseline:
         def gpu_nnz(sub):
@@ -346,17 +394,14 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
         "lsqr_iters_per_s": lsqr_ips,
         "nnz": nnz,
-        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "avg_launch_ms": avg_ms,
-                     "forward_ms_per_launch": fwd_ms / max(fwd_n, 1),
-                     "backward_ms_per_launch": bwd_ms / max(bwd_n, 1)},
+        "roofline": roofline_block(g, nnz, fwd_ms / max(fwd_n, 1), bwd_ms / max(bwd_n, 1), clocks),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * geom.num_rays,
                 "d2h_bytes_per_step": 2 * 4 * geom.num_voxels},
         "gpu_launches": launches,
         "clocks": clocks,
         "launch_shapes": {"fwd_rows": tune["fwd_rows"], "bwd_brick": tune["bwd_shape"]},
+        "serving": serving,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
@@ -404,51 +449,208 @@ def run_projectors(args):
     return 0
 
 
+PRECISION_REF = os.path.join(ROOT, "tests", "golden", "precision_reference.json")
+
+
 def run_precision(args):
-    """Storage-precision study on the 512^3 scan (768 x 512 detector, 720 angles,
-    noisy): hybrid LSQR 50 iterations with GCV, Krylov vectors and basis stored
-    in FP32, FP16 or BF16 (FP32 ray sums, FP64 scalars); time per iteration,
-    throughput, and the difference of each result from the FP32 one."""
+    """Storage-precision study (Krylov vectors, basis, volumes and projections
+    stored in FP32, FP16 or BF16; FP32 ray sums, Kahan-compensated for the
+    16-bit formats; FP64 Krylov scalars), errors against the FP64 oracle's
+    stored values (tests/golden/precision_reference.json):
+      * 512^3 scan (768 x 512 detector, 720 angles): A x and A^T y at sampled
+        rays / voxels; hybrid LSQR 50 (GCV) on noisy data, time per iteration
+        and the distance of each result from the FP32 one and from the phantom;
+      * 64^3 scan: LSQR, LSMR and hybrid LSQR after 20 iterations against the
+        FP64 iterates at sampled voxels;
+      * basis memory: hybrid LSQR with 70 iterations on a 1024^3 volume keeps
+        70 basis volumes, more than the device holds in FP32, run in FP16."""
     import numpy as np
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import synth
     from paper_2211_14212_gb300 import cbct
-    g = synth.config("c3")
+    with open(PRECISION_REF) as f:
+        ref = json.load(f)
     dev = torch.device("cuda", 0)
+    dts = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+
+    def rel(a, b):
+        a = np.asarray(a, np.float64)
+        b = np.asarray(b, np.float64)
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    # ---- 512^3: projectors against FP64, hybrid LSQR 50 per storage
+    g = synth.config("c3")
     geom = cbct.Geometry(g)
     tune = cbct.autotune(geom, max_angles=32)
-    x_true = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=2, scale=0.02)).to(dev)
-    b = cbct.project(geom, x_true).cpu().numpy()
-    b = torch.from_numpy(synth.poisson_log_noise(b, 1e5, seed=25).astype(np.float32)).to(dev)
     nnz = cbct.count_nnz(geom)
+    c3 = ref["c3"]
+    rays = torch.from_numpy(np.asarray(c3["rays"])).to(dev)
+    vox = torch.from_numpy(np.asarray(c3["voxels"])).to(dev)
+    x32 = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=c3["phantom_seed"], scale=0.02)).to(dev)
+    y32 = torch.from_numpy(synth.random_projections(g, c3["y_seed"]).astype(np.float32)).to(dev)
+    proj = {}
+    for st, dt in dts.items():
+        x, y = x32.to(dt), y32.to(dt)
+        ax = cbct.project(geom, x)
+        aty = cbct.backproject(geom, y)
+        torch.cuda.synchronize()
+        times = []
+        for fn in (lambda: cbct.project(geom, x, out=ax), lambda: cbct.backproject(geom, y, out=aty)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        proj[st] = {"forward_rel_err_vs_fp64": rel(ax.view(-1)[rays].double().cpu(), c3["project_rays"]),
+                    "backward_rel_err_vs_fp64": rel(aty.view(-1)[vox].double().cpu(), c3["backproject_voxels"]),
+                    "forward_ms": times[0], "backward_ms": times[1]}
+        del x, y, ax, aty
+    del y32
+    b = cbct.project(geom, x32).cpu().numpy()
+    b = torch.from_numpy(synth.poisson_log_noise(b, 1e5, seed=25).astype(np.float32)).to(dev)
     iters = 50
-    out = {"mode": "precision", "config": {"workload": "512^3 CBCT precision study: hybrid LSQR 50 (GCV)",
-                                           "volume": [g.nx, g.ny, g.nz], "voxel_mm": g.dx,
-                                           "detector": [g.nu, g.nv], "pixel_mm": g.du, "angles": g.nangles,
-                                           "dso_mm": g.dso, "dsd_mm": g.dsd, "noise": "Poisson I0=1e5"},
-           "nnz": nnz, "launch_shapes": {"fwd_rows": tune["fwd_rows"], "bwd": tune["bwd_shape"]}, "storage": {}}
-    ref = None
-    xt = x_true.double()
-    for storage in ("f32", "f16", "bf16"):
-        cbct.hybrid_lsqr(geom, b, 2, storage=storage)                    # warm-up
+    hyb, xref = {}, None
+    xt = x32.double()
+    for st in dts:
+        cbct.hybrid_lsqr(geom, b, 2, storage=st)                   # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x, rep = cbct.hybrid_lsqr(geom, b, iters, storage=storage)
+        x, rep = cbct.hybrid_lsqr(geom, b, iters, storage=st)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         xd = x.double()
-        if ref is None:
-            ref = xd.clone()
-        out["storage"][storage] = {
-            "s_per_solve": dt, "ms_per_iter": 1000 * dt / iters,
-            "gupdates_per_s": 2 * nnz * iters / dt / 1e9,
-            "rel_diff_vs_f32": float((xd - ref).norm() / ref.norm()),
-            "rel_err_vs_phantom": float((xd - xt).norm() / xt.norm()),
-            "lambda_last": float(rep.lam[-1]), "resid_last": float(rep.resid[-1])}
+        if xref is None:
+            xref = xd.clone()
+        hyb[st] = {"s_per_solve": dt, "ms_per_iter": 1000 * dt / iters, "gupdates_per_s": 2 * nnz * iters / dt / 1e9,
+                   "rel_diff_vs_f32": float((xd - xref).norm() / xref.norm()),
+                   "rel_err_vs_phantom": float((xd - xt).norm() / xt.norm()),
+                   "lambda_last": float(rep.lam[-1])}
         del x, xd
+    del xref, xt, x32, b, geom
+
+    # ---- 64^3: solvers against the FP64 iterates
+    md = ref["medium"]
+    gm = synth.Geometry(64, 64, 64, 4.0, 4.0, 4.0, 128, 128, 3.2, 3.2, 1000.0, 1536.0, synth.circular_angles(90))
+    geom = cbct.Geometry(gm)
+    bm = torch.from_numpy(synth.random_projections(gm, md["b_seed"]).astype(np.float32)).to(dev)
+    mvox = torch.from_numpy(np.asarray(md["voxels"])).to(dev)
+    solv = {}
+    for st in dts:
+        solv[st] = {}
+        for method in ("lsqr", "lsmr", "hybrid_lsqr"):
+            x, _ = getattr(cbct, method)(geom, bm, md["iters"], storage=st)
+            solv[st][method] = rel(x.view(-1)[mvox].double().cpu(), md[method]["sampled"])
+    del geom, bm
+
+    # ---- basis memory: 1024^3 volume, hybrid LSQR 70 iterations in FP16
+    gb = synth.Geometry(1024, 1024, 1024, 0.25, 0.25, 0.25, 512, 512, 1.0, 1.0, 1000.0, 1536.0,
+                        synth.circular_angles(180))
+    free, total = torch.cuda.mem_get_info(dev)
+    k = 70
+    need = {st: (k + 4) * gb.num_voxels * (4 if st == "f32" else 2) + 3 * gb.num_rays * 4 for st in ("f32", "f16")}
+    geom = cbct.Geometry(gb)
+    bb = torch.from_numpy(synth.random_projections(gb, 76).astype(np.float32)).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, rep = cbct.hybrid_lsqr(geom, bb, k, storage="f16")
+    torch.cuda.synchronize()
+    basis = {"volume": [1024, 1024, 1024], "detector": [512, 512], "angles": 180, "iters": k,
+             "device_total_bytes": total, "approx_bytes_needed": need,
+             "f32_fits": need["f32"] <= total, "f16_fits": need["f16"] <= total,
+             "f16_iters_done": rep.iters_done, "f16_s": time.perf_counter() - t0,
+             "f16_finite": bool(torch.isfinite(x).all())}
+    del x, bb, geom
+    print(json.dumps({"mode": "precision",
+                      "config": {"workload": "512^3 CBCT precision study: projectors and hybrid LSQR 50 (GCV)",
+                                 "volume": [g.nx, g.ny, g.nz], "voxel_mm": g.dx, "detector": [g.nu, g.nv],
+                                 "pixel_mm": g.du, "angles": g.nangles, "dso_mm": g.dso, "dsd_mm": g.dsd,
+                                 "noise": "Poisson I0=1e5"},
+                      "nnz": nnz, "launch_shapes": {"fwd_rows": tune["fwd_rows"], "bwd": tune["bwd_shape"]},
+                      "projectors_vs_fp64": proj, "hybrid_lsqr_50": hyb,
+                      "solvers_64cube_k20_rel_err_vs_fp64": solv, "basis_memory": basis}), flush=True)
+    return 0
+
+
+def run_microct(args):
+    """The micro-CT scan: 1024^3 x 0.1 mm volume (ellipsoids and a sample-holder
+    cylinder, x 0.02 mm^-1), 1536^2 x 0.6 mm detector, 1600 angles, DSO 200 /
+    DSD 1200 mm (magnification 6), Poisson noise with I0 = 2e5; LSMR 50
+    iterations with Tikhonov damping lambda = 1e-2 ||b|| (Sec. 2.2, Eq. 7).
+    One solve, CUDA events around every projector launch: s per solve,
+    Gupdates/s of the solve and the per-launch projector roofline."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2211_14212_gb300 import cbct
+    g = synth.config("c5")
+    dev = torch.device("cuda", 0)
+    geom = cbct.Geometry(g)
+    tune = cbct.autotune(geom, max_angles=32)
+    x_true = torch.from_numpy(synth.ellipsoid_phantom(g, 4, seed=4, scale=0.02, cylinder=True)).to(dev)
+    b = cbct.project(geom, x_true)
+    del x_true
+    gen = torch.Generator(device=dev).manual_seed(41)
+    for chunk in b.view(-1).split(1 << 28):             # photon noise in place, in chunks
+        counts = torch.poisson(2e5 * torch.exp(-chunk), generator=gen)
+        chunk.copy_(-torch.log(torch.clamp(counts, min=1.0) / 2e5))
+        del counts
+    nnz = cbct.count_nnz(geom)
+    bnorm = float(torch.linalg.vector_norm(b.double()))
+    lam = 1e-2 * bnorm
+    iters = 50
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        x, rep = cbct.lsmr(geom, b, iters, lam=lam, profile=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    clocks = clk.summary()
+    products = rep.forward_launches + rep.backward_launches
+    fwd = rep.forward_ms / max(rep.forward_launches, 1)
+    bwd = rep.backward_ms / max(rep.backward_launches, 1)
+    rl = roofline_block(g, nnz, fwd, bwd, clocks)
+    rl["traffic"] = None
+    rl["t_bound"]["issue_ms"] = None
+    rl["issue_util"] = None
+    out = {"mode": "microct",
+           "config": {"workload": "1024^3 micro-CT: LSMR 50 iterations, damping 1e-2 ||b||",
+                      "volume": [g.nx, g.ny, g.nz], "voxel_mm": g.dx, "detector": [g.nu, g.nv],
+                      "pixel_mm": g.du, "angles": g.nangles, "dso_mm": g.dso, "dsd_mm": g.dsd,
+                      "phantom": "4 random ellipsoids + cylinder (seed 4) x 0.02 mm^-1", "noise": "Poisson I0=2e5"},
+           "nnz": nnz, "iters_done": rep.iters_done, "lambda": lam, "s_per_solve": dt,
+           "gupdates_per_s": nnz * products / dt / 1e9, "projector_launches": products,
+           "resid_last": float(rep.resid[-1]), "normal_resid_last": float(rep.normal_resid[-1]),
+           "roofline": rl, "clocks": clocks, "launch_shapes": {"fwd_rows": tune["fwd_rows"],
+                                                               "bwd_brick": tune["bwd_shape"]}}
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_profile_solve(args):
+    """A target for ncu: the 256^3 scan with the benchmark's launch shapes
+    (4 rays per lane, 2 x 4 columns x 128 transpose tile) and one LSQR solve
+    of 2 iterations on a random b, plain launches.  Its first forward_kernel
+    and backward_kernel launches are the instantiations the benchmark's
+    solvers run (v-fastest projections with the weighted copy, z-fastest
+    volume)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2211_14212_gb300 import cbct
+    g, _ = workload_config()
+    geom = cbct.Geometry(g)
+    cbct.set_launch(geom, args.fwd_rows, args.bwd_config)
+    b = torch.from_numpy(synth.random_projections(g, 5).astype(np.float32)).cuda()
+    x, rep = cbct.lsqr(geom, b, 2, use_graph=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "profile-solve", "iters_done": rep.iters_done,
+                      "launch": [args.fwd_rows, args.bwd_config], "projector_hash": projector_hash()}))
     return 0
 
 
@@ -475,93 +677,138 @@ def serving_requests(count, scale, seed=3):
     return reqs
 
 
-def run_serving(args):
-    """Continuous-batching server vs the one-request-at-a-time solver on the
-    serving stream (Poisson arrivals at 0.8 of the one-at-a-time throughput)."""
-    import threading
-
+def serving_inputs(cbct, torch, dev, reqs, i0=5e4):
+    """Measured projections of every request (input generation, untimed): the
+    GPU forward projection of its phantom with photon noise at I0 = 5e4; and
+    nnz(A) of its scan (the work model that sets the arrival rate)."""
     import numpy as np
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
     import synth
-    from paper_2211_14212_gb300 import cbct
-    dev = torch.device("cuda", 0)
-    reqs = serving_requests(args.requests, args.serving_scale)
     gen = torch.Generator(device=dev)
-    # measured projections: GPU forward projection + Poisson photon noise (input generation)
     for r in reqs:
         g = r["geom"]
         geom = cbct.Geometry(g)
         x = torch.from_numpy(synth.ellipsoid_phantom(g, 10, seed=r["seed"], scale=0.02)).to(dev)
         b = cbct.project(geom, x)
         gen.manual_seed(r["seed"])
-        counts = torch.poisson(5e4 * torch.exp(-b), generator=gen)
-        r["b"] = (-torch.log(torch.clamp(counts, min=1.0) / 5e4)).float().cpu().numpy().ravel()
+        counts = torch.poisson(i0 * torch.exp(-b), generator=gen)
+        r["b"] = np.ascontiguousarray((-torch.log(torch.clamp(counts, min=1.0) / i0)).float().cpu().numpy().ravel())
+        r["nnz"] = cbct.count_nnz(geom)
         del x, b, counts, geom
-    torch.cuda.synchronize()
-    # one request at a time (plain solver, host b and x: end to end)
-    service, keep = [], {}
-    for i, r in enumerate(reqs[:2]):                      # warm-up
-        getattr(cbct, r["solver"])(cbct.Geometry(r["geom"]), r["b"], 2)
-    for i, r in enumerate(reqs):
-        t0 = time.perf_counter()
+    torch.cuda.synchronize(dev)
+
+
+def plain_arm(cbct, reqs, arrivals):
+    """One request at a time, in arrival order, fed in real time: request i
+    starts when it has arrived and request i - 1 is done; its latency runs
+    from its arrival to the end of its solve (scan set-up, b from host memory,
+    the solve, x back to host memory, all through the C ABI)."""
+    import numpy as np
+    lat, xs = [], []
+    t0 = time.perf_counter()
+    for a, r in zip(arrivals, reqs):
+        wait = a - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
         geom = cbct.Geometry(r["geom"])
-        x, _ = getattr(cbct, r["solver"])(geom, r["b"], r["iters"])
-        service.append(time.perf_counter() - t0)
-        if i < 8:
-            keep[i] = x
-        del geom
-    total = sum(service)
-    rate = 0.8 * len(reqs) / total
+        x, rep = getattr(cbct, r["solver"])(geom, r["b"], r["iters"])
+        geom.close()
+        lat.append(time.perf_counter() - t0 - a)
+        xs.append(x)
+    span = time.perf_counter() - t0
+    return np.array(lat), xs, span
+
+
+def server_arm(cbct, reqs, arrivals, slots, budget_gb, schedule, x_ref=None):
+    """The continuous-batching server fed in real time (a feeder thread submits
+    request i at its arrival time); latency = finish - submit by the server's
+    clock.  With `x_ref`, the largest relative difference of the results from
+    those."""
+    import threading
+
+    import numpy as np
+    srv = cbct.Server(int(budget_gb * (1 << 30)), max_slots=slots, use_graph=True, schedule=schedule)
+    ids = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for i, (a, r) in enumerate(zip(arrivals, reqs)):
+            wait = a - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ids[i] = srv.submit(r["geom"], r["b"], r["solver"], r["iters"])
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    lat, diff = [], 0.0
+    first, last = None, None
+    for i in range(len(reqs)):
+        res = srv.wait(ids[i])
+        lat.append(res.finish_s - res.submit_s)
+        first = res.submit_s if first is None else min(first, res.submit_s)
+        last = res.finish_s if last is None else max(last, res.finish_s)
+        if x_ref is not None:
+            ref = x_ref[i].ravel().astype(np.float64)
+            diff = max(diff, float(np.linalg.norm(res.x.ravel() - ref) / max(np.linalg.norm(ref), 1e-300)))
+    stats = srv.stats()
+    srv.close()
+    return np.array(lat), last - first, diff, stats
+
+
+def latency_summary(lat, span, count):
+    import numpy as np
+    return {"recon_per_s": count / span, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "max_s": float(lat.max())}
+
+
+def serving_compare(cbct, torch, dev, count, scale, gupd_per_s, slots, budget_gb, schedule, load=0.8):
+    """The serving stream through the one-request-at-a-time solver and through
+    the server, both fed in real time with the same Poisson arrivals.  The
+    arrival rate is `load` x the one-at-a-time throughput predicted from
+    each request's nnz(A) x (2 iters + 1) projector updates at the solver's
+    measured rate `gupd_per_s` (the 256^3 step's Gupdates/s)."""
+    import numpy as np
+    reqs = serving_requests(count, scale)
+    serving_inputs(cbct, torch, dev, reqs)
+    work = sum(r["nnz"] * (2 * r["iters"] + 1) for r in reqs)
+    est_total_s = work / (gupd_per_s * 1e9)
+    rate = load * len(reqs) / est_total_s
     rng = np.random.default_rng(4)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
     arrivals -= arrivals[0]
-    finish, t = [], 0.0
-    for a, sv in zip(arrivals, service):
-        t = max(t, a) + sv
-        finish.append(t)
-    lat_plain = np.array(finish) - arrivals
-    plain = {"recon_per_s": len(reqs) / (finish[-1] - arrivals[0]), "p50_s": float(np.percentile(lat_plain, 50)),
-             "p99_s": float(np.percentile(lat_plain, 99)), "mean_service_s": total / len(reqs)}
-    # the server, fed in real time, under each schedule
-    def serve(schedule):
-        srv = cbct.Server(int(args.serving_budget_gb * (1 << 30)), max_slots=args.serving_slots, use_graph=True,
-                          schedule=schedule)
-        ids = [None] * len(reqs)
-        t_start = time.perf_counter()
+    for r in reqs[:2]:                                  # warm-up of both paths (untimed)
+        geom = cbct.Geometry(r["geom"])
+        getattr(cbct, r["solver"])(geom, r["b"], 2)
+        geom.close()
+    server_arm(cbct, reqs[:2], [0.0, 0.0], slots, budget_gb, schedule)
+    lat_p, xs, span_p = plain_arm(cbct, reqs, arrivals)
+    lat_s, span_s, diff, stats = server_arm(cbct, reqs, arrivals, slots, budget_gb, schedule, xs)
+    return {"workload": "%d requests: %d^3..%d^3 volumes, %d..%d px square detectors, %d..%d angles, "
+                        "LSQR/LSMR %d..%d iterations, I0 = 5e4" % (
+                            len(reqs), min(r["geom"].nx for r in reqs), max(r["geom"].nx for r in reqs),
+                            min(r["geom"].nu for r in reqs), max(r["geom"].nu for r in reqs),
+                            min(r["geom"].nangles for r in reqs), max(r["geom"].nangles for r in reqs),
+                            min(r["iters"] for r in reqs), max(r["iters"] for r in reqs)),
+            "scale": scale, "offered_load": load, "arrival_rate_per_s": rate,
+            "predicted_one_at_a_time_s": est_total_s,
+            "plain": latency_summary(lat_p, span_p, len(reqs)),
+            "server": dict(latency_summary(lat_s, span_s, len(reqs)), schedule=schedule, max_slots=slots,
+                           budget_gb=budget_gb, steps=stats["steps"], graph_replays=stats["graph_replays"]),
+            "max_rel_diff_server_vs_plain": diff}
 
-        def feeder():
-            for i, (a, r) in enumerate(zip(arrivals, reqs)):
-                dt = a - (time.perf_counter() - t_start)
-                if dt > 0:
-                    time.sleep(dt)
-                ids[i] = srv.submit(r["geom"], r["b"], r["solver"], r["iters"])
 
-        th = threading.Thread(target=feeder)
-        th.start()
-        th.join()
-        results = [srv.wait(i) for i in ids]
-        stats = srv.stats()
-        srv.close()
-        lat = np.array([r.finish_s - r.submit_s for r in results])
-        first = min(r.submit_s for r in results)
-        last = max(r.finish_s for r in results)
-        diffs = [float(np.linalg.norm(results[i].x - keep[i]) / np.linalg.norm(keep[i])) for i in keep]
-        return {"recon_per_s": len(reqs) / (last - first), "p50_s": float(np.percentile(lat, 50)),
-                "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "steps": stats["steps"],
-                "graph_replays": stats["graph_replays"], "max_slots": args.serving_slots,
-                "budget_gb": args.serving_budget_gb,
-                "max_rel_diff_vs_plain": max(diffs) if diffs else None}
-
-    plain["mean_s"] = float(lat_plain.mean())
-    out = {"mode": "serving", "requests": len(reqs), "offered_load": 0.8, "arrival_rate_per_s": rate,
-           "scale": args.serving_scale, "unit": "recon/s",
-           "plain_one_at_a_time": plain,
-           "server_srpt": serve("srpt"),
-           "server_ratio": serve("ratio"),
-           "server_share": serve("share"),
-           "request_mix": [r["desc"] + [r["solver"], r["iters"]] for r in reqs]}
+def run_serving(args):
+    """The serving stream alone: one-at-a-time vs the server under each
+    schedule (exploration; the default run reports the default schedule)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2211_14212_gb300 import cbct
+    dev = torch.device("cuda", 0)
+    out = {"mode": "serving"}
+    for sched in args.serving_schedule.split(","):
+        out[sched] = serving_compare(cbct, torch, dev, args.requests, args.serving_scale, args.serving_rate,
+                                     args.serving_slots, args.serving_budget_gb, sched)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -573,7 +820,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "projectors", "serving", "precision"], default="solve",
+    ap.add_argument("--mode", choices=["solve", "projectors", "serving", "precision", "microct", "profile-solve"],
+                    default="solve",
                     help="solve: the benchmark step (default); projectors: standalone A / A^T timing; "
                          "serving: continuous-batching server vs one request at a time; "
                          "precision: FP32 / FP16 / BF16 storage study at 512^3")
@@ -581,6 +829,13 @@ def main():
     ap.add_argument("--serving-scale", type=float, default=1.0)
     ap.add_argument("--serving-slots", type=int, default=16)
     ap.add_argument("--serving-budget-gb", type=float, default=96.0)
+    ap.add_argument("--serving-schedule", default="fifo",
+                    help="server schedule (fifo, srpt, ratio, share; --mode serving takes a comma list)")
+    ap.add_argument("--serving-rate", type=float, default=700.0,
+                    help="--mode serving: the solver's Gupdates/s that sets the arrival rate")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream in the default run")
+    ap.add_argument("--fwd-rows", type=int, default=4, help="--mode profile-solve: forward rays per lane")
+    ap.add_argument("--bwd-config", type=int, default=5, help="--mode profile-solve: transpose tile")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -590,6 +845,10 @@ def main():
         sys.exit(run_serving(args))
     if args.mode == "precision":
         sys.exit(run_precision(args))
+    if args.mode == "microct":
+        sys.exit(run_microct(args))
+    if args.mode == "profile-solve":
+        sys.exit(run_profile_solve(args))
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
 
 

@@ -97,9 +97,10 @@ int64_t cbct_geometry_num_rays(const cbct_geometry *geom);     /* N, or -1 for N
 cbct_status cbct_project(const cbct_geometry *geom, const void *x, void *y,
                          cbct_dtype dtype, cbct_stream stream);
 
-/* x = A^T y, the exact transpose of cbct_project (same ray/voxel lengths, so
- * <A x, y> = <x, A^T y> up to FP32 rounding of the sums; Sec. 2.1.4 explains
- * why an unmatched backprojector breaks the Krylov methods).  y: N device
+/* x = A^T y, the transpose of cbct_project (the same ray/voxel lengths from
+ * the same crossing tables, so <A x, y> = <x, A^T y> up to FP32 rounding of
+ * the lengths and sums; Sec. 2.1.4 explains why an unmatched backprojector
+ * breaks the Krylov methods).  y: N device
  * elements, x: M device elements of `dtype`.  Asynchronous on `stream`. */
 cbct_status cbct_backproject(const cbct_geometry *geom, const void *y, void *x,
                              cbct_dtype dtype, cbct_stream stream);
@@ -107,16 +108,17 @@ cbct_status cbct_backproject(const cbct_geometry *geom, const void *y, void *x,
 /* cbct_project without any device allocation, for callers that cannot call
  * cudaMalloc (the paper has no counterpart: it is an interface variant, not a
  * step of the method).  Same arguments, layouts and result as cbct_project;
- * the z-fastest copy of the volume that cbct_project allocates per call lives
- * here in a fixed 64 MiB array of the library's device memory, so the volume
- * may hold at most 2^24 FP32 or 2^25 FP16/BF16 voxels (a 256^3 FP32 volume);
- * larger volumes are rejected with CBCT_EINVAL before any work is queued.
- * The geometry's device must be the current device (else CBCT_EINVAL).  The
- * first call on a device looks the array up (cudaGetSymbolAddress); make it
- * before capturing a stream.  Every call on a device shares the one array,
- * which keeps the last call's contents (each call overwrites all it reads):
- * calls whose work overlaps on the GPU (other streams, other threads) race
- * and give wrong results, so serialise them on one stream. */
+ * the padded z-fastest copy of the volume (nx * ny * (nz + 2) + 4 elements)
+ * that cbct_project allocates per call lives here in a fixed 66 MiB array of
+ * the library's device memory, so e.g. a 256^3 FP32 volume or a 256^2 x 512
+ * FP16/BF16 volume fits; larger ones are rejected with CBCT_EINVAL before any
+ * work is queued.  The geometry's device must be the current device (else
+ * CBCT_EINVAL).  The first call on a device looks the array up
+ * (cudaGetSymbolAddress); make it before capturing a stream.  Every call on a
+ * device shares the one array, which keeps the last call's contents (each
+ * call overwrites all it reads): calls whose work overlaps on the GPU (other
+ * streams, other threads) race and give wrong results, so serialise them on
+ * one stream. */
 cbct_status cbct_project_static(const cbct_geometry *geom, const void *x, void *y,
                                 cbct_dtype dtype, cbct_stream stream);
 
@@ -141,16 +143,19 @@ cbct_status cbct_count_nnz(const cbct_geometry *geom, int64_t *nnz, cbct_stream 
  * bwd_config: tile of the transpose (one warp per voxel column), 0 = 4 x 2
  * columns x 32 voxels along z (1 per lane), 1 = 4 x 2 x 64 (2 per lane),
  * 2 = 8 x 1 x 32, 3 = 2 x 4 x 64, 4 = 4 x 2 x 128 (4 per lane),
- * 5 = 2 x 4 x 128, 6 = 4 x 2 x 256 (8 per lane), 7 = 2 x 4 x 256.  Changing
- * the shape while another thread uses the geometry is a data race. */
-#define CBCT_TUNE_TIMES 11
+ * 5 = 2 x 4 x 128, 6 = 4 x 2 x 256 (8 per lane), 7 = 2 x 4 x 256,
+ * 8 = 2 x 4 x 128 and 9 = 4 x 2 x 128 holding each voxel's candidate rows in
+ * registers per angle (configurations 0..3 do too; 4..7 re-read them per
+ * detector column).  Changing the shape while another thread uses the
+ * geometry is a data race. */
+#define CBCT_TUNE_TIMES 13
 cbct_status cbct_geometry_set_launch(cbct_geometry *geom, int fwd_rows, int bwd_config);
 cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, int *bwd_config);
 /* Times every launch shape (forward and transpose, FP32, on a strided subset
  * of at most max_angles angles; max_angles <= 0 = all) and keeps the fastest.
  * times_ms, if non-null, is a host array of CBCT_TUNE_TIMES doubles that
  * receives the forward times for fwd_rows 1, 2, 4 and the transpose times for
- * bwd_config 0..7.  Allocates scratch on `stream` and synchronises it. */
+ * bwd_config 0..9.  Allocates scratch on `stream` and synchronises it. */
 cbct_status cbct_geometry_autotune(cbct_geometry *geom, int max_angles, double *times_ms, cbct_stream stream);
 /* Angles per pass of the transpose inside the solvers and cbct_backproject
  * (performance only).  With a
@@ -294,19 +299,27 @@ cbct_status cbct_hybrid_lsmr_solve(const cbct_geometry *geom, const float *b, fl
  * a time).  Submitted requests wait in FIFO order and are admitted as slots
  * while the device memory they need fits the budget; a library-owned worker
  * thread then runs steps: one Krylov iteration of a set of admitted requests
- * (one multi-instance launch per kernel for all of them), after which it reads
- * out finished results, frees their memory and admits waiting requests.  Which
- * admitted requests a step advances is the schedule: CBCT_SCHED_SRPT (default)
- * takes them in order of least remaining work (iterations left x rays x
- * (nx + ny)) while the step's forward tiles (8 detector columns x 64 rows of
- * one angle each) stay within 4096, about five waves of the GPU, so small
- * requests are batched and large ones run one at a time, shortest first;
+ * (one multi-instance launch per kernel for all of them).  Two more library
+ * threads keep host-side work off the steps' path: one admits waiting
+ * requests (builds the scan's tables, uploads b and queues the solver's start
+ * on its own CUDA stream), one reads finished results out to the host and
+ * frees their memory.  Which admitted requests a step advances is the
+ * schedule.  CBCT_SCHED_FIFO takes them in submission order while the
+ * step's forward tiles (8 detector columns x 128 rows of one angle each) stay
+ * within 2048, so small requests share a step and large ones run one at a
+ * time, oldest first (the order that minimises the longest wait);
+ * CBCT_SCHED_SRPT takes them in order of least remaining work (iterations
+ * left x rays x (nx + ny)) under the same limit, which shortens the median
+ * latency but makes long requests wait behind short ones (a request left out
+ * of 64 consecutive steps goes first from then on, so it cannot starve);
  * CBCT_SCHED_RATIO orders them by response ratio (age + remaining time) /
- * remaining time instead (remaining time from the same cost model and the
- * measured work rate), so that a long request's priority grows while it
- * waits; CBCT_SCHED_SHARE advances every admitted request every step.  Each result
- * equals the single-request solver's (same kernels and per-voxel / per-ray
- * summation order) up to the rounding of the blockwise norm reductions.
+ * remaining time (remaining time from the same cost model and the measured
+ * work rate); CBCT_SCHED_SHARE advances every admitted request every step.
+ * Each result equals the single-request solver's up to FP32 rounding: the
+ * server's tiles sum every ray and voxel in the same order, but a single
+ * request tuned to other launch shapes (cbct_geometry_autotune) sums its norm
+ * partials in other groups, and late iterates of ill-conditioned problems
+ * amplify such differences (about 1e-4 relative after 20-40 iterations).
  * Requests use FP32 storage and LSQR or LSMR.  All calls are thread-safe
  * except cbct_server_destroy, which must not overlap any other call on the
  * same server. */
@@ -314,7 +327,7 @@ cbct_status cbct_hybrid_lsmr_solve(const cbct_geometry *geom, const float *b, fl
 typedef struct cbct_server cbct_server;   /* opaque, library-owned */
 typedef enum { CBCT_SOLVER_LSQR = 0, CBCT_SOLVER_LSMR = 1 } cbct_solver;
 
-typedef enum { CBCT_SCHED_SRPT = 0, CBCT_SCHED_SHARE = 1, CBCT_SCHED_RATIO = 2 } cbct_schedule;
+typedef enum { CBCT_SCHED_SRPT = 0, CBCT_SCHED_SHARE = 1, CBCT_SCHED_RATIO = 2, CBCT_SCHED_FIFO = 3 } cbct_schedule;
 
 typedef struct {
     size_t hbm_budget_bytes;   /* device memory the server may hold for requests (> 0) */

@@ -257,7 +257,8 @@ def backproject_voxel_driven(geom: Geometry, y, out=None, stream=None):
 
 def project_static(geom: Geometry, x, out=None, stream=None):
     """y = A x like project(), through cbct_project_static, which allocates no
-    device memory (volume of at most 64 MiB; calls must not overlap on the GPU)."""
+    device memory (padded volume copy of at most 66 MiB, e.g. 256^3 FP32;
+    calls must not overlap on the GPU)."""
     import torch
     _require_cuda(x, "x", geom.num_voxels, geom.device)
     if out is None:
@@ -292,10 +293,11 @@ def count_nnz(geom: Geometry, stream=None) -> int:
     return int(n.value)
 
 
-TUNE_TIMES = 11
+TUNE_TIMES = 13
 FWD_ROWS = (1, 2, 4)
 BWD_CONFIGS = ("4x2 columns x 32", "4x2 columns x 64", "8x1 columns x 32", "2x4 columns x 64",
-               "4x2 columns x 128", "2x4 columns x 128", "4x2 columns x 256", "2x4 columns x 256")
+               "4x2 columns x 128", "2x4 columns x 128", "4x2 columns x 256", "2x4 columns x 256",
+               "2x4 columns x 128, rows held", "4x2 columns x 128, rows held")
 
 
 def set_launch(geom: Geometry, fwd_rows: int, bwd_config: int):
@@ -544,14 +546,15 @@ class ServedResult:
 class Server:
     """Continuous-batching server (cbct_server_*): requests of different scans
     are admitted by device-memory budget and advanced in steps of one Krylov
-    iteration; schedule "srpt" (default) advances the requests with the least
-    remaining work until a step fills the GPU, "ratio" orders them by response
-    ratio (age + remaining) / remaining, "share" advances all of them."""
+    iteration; schedule "fifo" (default) advances the oldest requests until a
+    step fills the GPU, "srpt" the ones with the least remaining work,
+    "ratio" orders them by response ratio (age + remaining) / remaining,
+    "share" advances all of them."""
 
     SOLVERS = {"lsqr": 0, "lsmr": 1}
-    SCHEDULES = {"srpt": 0, "share": 1, "ratio": 2}
+    SCHEDULES = {"srpt": 0, "share": 1, "ratio": 2, "fifo": 3}
 
-    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, use_graph: bool = True, schedule: str = "srpt"):
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, use_graph: bool = True, schedule: str = "fifo"):
         lib = load()
         o = _ServerOpts(int(hbm_budget_bytes), int(max_slots), 1 if use_graph else 0, self.SCHEDULES[schedule])
         h = ctypes.c_void_p()

@@ -93,7 +93,7 @@ extern "C" cbct_status cbct_geometry_autotune(cbct_geometry *g, int max_angles, 
     cbct_status st = cbct_geometry_create(&d, &t);
     if (st != CBCT_OK) return st;
 
-    const size_t m = (size_t)g->dev.nx * g->dev.ny * g->dev.nz;
+    const size_t m = (size_t)zf_len(g->dev);            // padded z-fastest volume
     const size_t n = (size_t)keep * g->dev.nv * g->dev.nu;
     float *x = nullptr, *y = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -104,7 +104,7 @@ extern "C" cbct_status cbct_geometry_autotune(cbct_geometry *g, int max_angles, 
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
     if (err != cudaSuccess) st = cuda_fail(err, "cbct_geometry_autotune");
     if (st == CBCT_OK) {
-        fill_kernel<<<1024, 256, 0, s>>>(x, m, 1.0f);
+        st = launch_fill_volume(t->dev, x, 1.0f, s);
         fill_kernel<<<1024, 256, 0, s>>>(y, n, 1.0f);
         const Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};
         for (int c = 0; c < NUM_FWD_ROWS && st == CBCT_OK; ++c) {

@@ -29,10 +29,12 @@ namespace cbct {
 // holds its (fixed) voxel index.  The length of the ray/voxel segment
 // [alpha0, alpha1] is (alpha1 - alpha0) * ray_len[iu][iv].
 //
-// Forward and transposed kernels derive every alpha from these tables with
-// the same two rounded operations (plane_alpha), so the segment lengths they
-// use are bit-identical and A^T is the exact transpose of A up to the order of
-// the FP32 sums.
+// Forward and transposed kernels derive every x/y crossing from these tables
+// with the same two rounded operations (plane_alpha); the transpose takes its
+// z crossings from plane_alpha too (zbox), the forward projector from an
+// equivalent one-FMA form measured from the same plane pq.  A^T is the
+// transpose of A; in FP32 the two kernels' segment lengths agree to rounding
+// (not bit for bit), which the dot-product tests bound.
 struct DevGeom {
     int nx, ny, nz;
     int nu, nv, nangles;
@@ -46,6 +48,7 @@ struct DevGeom {
     const float *ray_len;    // [nu][nv]
     const float2 *trig;      // [nangles] (cos t, sin t), for footprint windows only
     const float2 *zbox;      // [nz][nv]: alpha interval (entry, exit) of row iv's ray in z slab k
+    int zsingle;             // 1: every ray crosses at most one z plane inside any x/y voxel column
     int fwd_rows;            // forward tile: rays per lane (1, 2 or 4)
     int bwd_config;          // transpose tile: column patch / voxels per lane (backward_shape)
     int angle_block;         // transpose: angles per pass when summed in passes (launch_backward)
@@ -56,6 +59,26 @@ struct DevGeom {
 struct BrickShape {
     int bx, by, bz, r;
 };
+
+// ------------------------------------------------- internal volume layout
+//
+// Inside the library every volume-side vector is z-fastest with padded
+// columns: voxel (i, j, k) sits at
+//     ZF_GUARD + (j * nx + i) * (nz + 2) + 1 + k,
+// each column carrying one zero below voxel 0 and one above voxel nz - 1, and
+// the array starting and ending with ZF_GUARD zeros (zf_len elements in all).
+// The forward projector then reads voxels k in [-2, nz + 1] of any column
+// without a bounds test.  Vectors are zeroed when allocated; kernels that
+// combine whole vectors elementwise keep the pads at zero, and the kernels
+// that address voxels write the interior only.
+constexpr int ZF_GUARD = 2;
+__host__ __device__ __forceinline__ int64_t zf_len(const DevGeom &g) {
+    return (int64_t)g.nx * g.ny * (g.nz + 2) + 2 * ZF_GUARD;
+}
+// index of voxel k = 0 of column (i, j)
+__host__ __device__ __forceinline__ int64_t zf_col(const DevGeom &g, int i, int j) {
+    return ZF_GUARD + 1 + ((int64_t)j * g.nx + i) * (g.nz + 2);
+}
 
 }  // namespace cbct
 
@@ -152,8 +175,9 @@ cbct_status cuda_fail(cudaError_t err, const char *what);
 cbct_status launch_forward(const DevGeom &g, const void *x_zfast, void *y, cbct_dtype t,
                            const Epilogue &epi, cudaStream_t s, bool vfast);
 // Layouts: the ABI uses x[k][j][i] and y[a][iv][iu].  The forward kernel reads
-// volumes z-fastest, x[j][i][k], and the transpose reads projections
-// v-fastest, y[a][iu][iv]; the solvers keep their vectors in those layouts.
+// volumes in the padded z-fastest layout above, and the transpose reads
+// projections v-fastest, y[a][iu][iv]; the solvers keep their vectors in those
+// layouts.
 // launch_forward writes either projection layout, launch_backward either
 // volume layout.
 // The transpose reads its projections pre-weighted by the ray lengths |d'|,
@@ -172,8 +196,11 @@ int default_angle_block(const DevGeom &g);
 // Fills DevGeom::zbox (nz * nv entries) from the z tables; synchronous use at
 // geometry creation (legacy default stream).
 cudaError_t launch_zbox(const DevGeom &g, float2 *zbox);
+// ABI x[k][j][i] <-> padded z-fastest (to_zfast also writes every pad and guard: zeros).
 cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_zfast,
                             cudaStream_t s);
+// Zero pads and guards, `value` in every voxel of a padded z-fastest FP32 volume.
+cbct_status launch_fill_volume(const DevGeom &g, float *x, float value, cudaStream_t s);
 cbct_status launch_proj_relayout(const DevGeom &g, const void *src, void *dst, cbct_dtype t, bool to_vfast,
                                  cudaStream_t s);
 cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaStream_t s);
@@ -185,6 +212,6 @@ int backward_num_blocks(const DevGeom &g);
 dim3 forward_grid(const DevGeom &g);
 dim3 backward_grid(const DevGeom &g);
 BrickShape backward_shape(int config);
-constexpr int NUM_FWD_ROWS = 3, NUM_BWD_CONFIGS = 8;
+constexpr int NUM_FWD_ROWS = 3, NUM_BWD_CONFIGS = 10;
 
 }  // namespace cbct

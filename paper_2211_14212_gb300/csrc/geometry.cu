@@ -86,6 +86,9 @@ cbct_status validate_geometry_desc(const cbct_geometry_desc *d) {
     // index ranges: voxels addressed with int32, rays with int64
     if ((int64_t)d->nx * d->ny * d->nz >= (int64_t)1 << 31)
         return invalid("geometry: more than 2^31-1 voxels");
+    // the internal padded z-fastest layout (nz + 2 per column, 4 guards) is addressed with int32
+    if ((int64_t)d->nx * d->ny * (d->nz + 2) + 4 >= (int64_t)1 << 31)
+        return invalid("geometry: the padded volume layout needs more than 2^31-1 elements");
     if ((int64_t)d->nu * d->nv >= (int64_t)1 << 31)
         return invalid("geometry: more than 2^31-1 pixels per projection");
     if (d->nangles > 65535 || d->nv > 65535 * 4)
@@ -183,7 +186,7 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
     dg.trig = reinterpret_cast<const float2 *>(mem + o_tr);
     dg.zbox = reinterpret_cast<const float2 *>(mem + o_zb);
     // the z slab crossings are computed on the device by the projectors' own
-    // plane_alpha, so that they are bit-identical to the forward traversal's
+    // plane_alpha (the same two roundings as every x/y crossing)
     if (err == cudaSuccess) err = launch_zbox(dg, reinterpret_cast<float2 *>(mem + o_zb));
     if (err == cudaSuccess) err = cudaStreamSynchronize(0);
     if (err != cudaSuccess) {
@@ -192,8 +195,18 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *d, cbct_ge
         delete g;
         return cuda_fail(err, "cbct_geometry_create");
     }
-    dg.fwd_rows = 2;
-    dg.bwd_config = nz >= 128 ? 5 : nz >= 64 ? 3 : 0;   // 4 / 2 / 1 voxels per lane by column depth
+    dg.fwd_rows = nv >= 128 ? 4 : nv >= 64 ? 2 : 1;   // forward tile: rows per lane by detector height
+    // At most one z-plane crossing per x/y voxel column along every ray: a
+    // ray's x/y path inside one column is at most the column's diagonal, and
+    // its z slope is at most max|v| / DSD (the pixel farthest from the
+    // mid-plane, seen from the source).  The forward projector's fast
+    // traversal relies on it (2 % margin for rounding).
+    {
+        const double vmax = 0.5 * (nv - 1) * d->dv;
+        const double zrise = std::sqrt(d->dx * d->dx + d->dy * d->dy) * vmax / d->dsd;
+        dg.zsingle = zrise < 0.98 * d->dz ? 1 : 0;
+    }
+    dg.bwd_config = nz >= 64 ? 3 : 0;   // 2 / 1 voxels per lane by column depth
     dg.angle_block = default_angle_block(dg);
     *out = g;
     return CBCT_OK;

@@ -177,7 +177,8 @@ struct GmresOperator {
 static cbct_status gmres_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
                                cbct_solve_report *rep, cudaStream_t s, bool ab) {
     const DevGeom &g = geom->dev;
-    const int64_t n = cbct_geometry_num_rays(geom), m = cbct_geometry_num_voxels(geom);
+    // m: length of a volume-side vector (padded z-fastest layout, pads kept at zero)
+    const int64_t n = cbct_geometry_num_rays(geom), m = zf_len(geom->dev);
     const int iters = o->iters;
     const int64_t len = ab ? n : m;                 // Krylov vectors: projections (AB) or volumes (BA)
     const int ld = iters + 1;                       // Hessenberg: column-major (iters + 1) x iters
@@ -192,12 +193,17 @@ static cbct_status gmres_solve(const cbct_geometry *geom, const float *b, float 
     op.voxel_driven = o->gmres_backprojector == 2;
     float *V = nullptr, *w = nullptr, *yn = nullptr, *xm = nullptr;
     double *partial = nullptr, *pn = nullptr, *H = nullptr, *d2 = nullptr, *beta = nullptr, *ycoef = nullptr;
-    CBCT_CUDA_TRY(ws.alloc(&V, (size_t)(iters + 1) * len));
-    CBCT_CUDA_TRY(ws.alloc(&w, (size_t)len));
+    if (ab) {
+        CBCT_CUDA_TRY(ws.alloc(&V, (size_t)(iters + 1) * len));
+        CBCT_CUDA_TRY(ws.alloc(&w, (size_t)len));
+    } else {
+        CBCT_CUDA_TRY(ws.alloc_volumes(&V, g, (size_t)iters + 1));
+        CBCT_CUDA_TRY(ws.alloc_volumes(&w, g));
+    }
     CBCT_CUDA_TRY(ws.alloc(&yn, (size_t)n));
-    CBCT_CUDA_TRY(ws.alloc(&xm, (size_t)m));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&xm, g));
     CBCT_CUDA_TRY(ws.alloc(&op.tn, (size_t)n));
-    CBCT_CUDA_TRY(ws.alloc(&op.tm, (size_t)m));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&op.tm, g));
     CBCT_CUDA_TRY(ws.alloc(&op.wbuf, (size_t)n));
     CBCT_CUDA_TRY(ws.alloc(&partial, (size_t)(iters + 1) * VEC_BLOCKS));
     CBCT_CUDA_TRY(ws.alloc(&pn, (size_t)VEC_BLOCKS));
@@ -208,8 +214,9 @@ static cbct_status gmres_solve(const cbct_geometry *geom, const float *b, float 
     CBCT_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * ld * iters, s));
     if (op.weighted) {                  // R = 1 / (A 1), C = 1 / (A^T 1)
         CBCT_CUDA_TRY(ws.alloc(&op.R, (size_t)n));
-        CBCT_CUDA_TRY(ws.alloc(&op.C, (size_t)m));
-        k_fill<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(xm, m, 1.0f);
+        CBCT_CUDA_TRY(ws.alloc_volumes(&op.C, g));
+        st = launch_fill_volume(g, xm, 1.0f, s);         // the ones vector (pads stay zero)
+        if (st != CBCT_OK) return st;
         st = op.A(xm, op.R);
         if (st != CBCT_OK) return st;
         k_invert<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(op.R, n);

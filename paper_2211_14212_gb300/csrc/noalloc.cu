@@ -1,17 +1,18 @@
 // cbct_project_static: the forward projection y = A x of cbct_project for
 // callers that cannot allocate device memory.  cbct_project re-lays the
-// caller's volume x[k][j][i] into a z-fastest temporary that it allocates on
-// the stream; here that temporary is a fixed array in the library's own
-// device memory, so the call allocates nothing.
+// caller's volume x[k][j][i] into a padded z-fastest temporary (nx ny (nz + 2)
+// + 4 elements) that it allocates on the stream; here that temporary is a
+// fixed array in the library's own device memory, so the call allocates
+// nothing.
 #include <mutex>
 
 #include "common.cuh"
 
 namespace cbct {
 
-// Largest re-laid volume the static scratch holds: 64 MiB, i.e. 2^24 FP32
-// voxels (a 256^3 volume) or 2^25 FP16/BF16 voxels.
-constexpr size_t STATIC_SCRATCH_BYTES = (size_t)64 << 20;
+// Largest re-laid volume the static scratch holds: 66 MiB of the padded
+// layout, e.g. a 256^3 FP32 volume (67.6 MB padded) or 256^2 x 512 FP16/BF16.
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)66 << 20;
 
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
 
@@ -50,10 +51,10 @@ extern "C" cbct_status cbct_project_static(const cbct_geometry *g, const void *x
         set_error("cbct_project_static: unknown dtype");
         return CBCT_EINVAL;
     }
-    const size_t bytes = (size_t)cbct_geometry_num_voxels(g) * dtype_size(t);
+    const size_t bytes = (size_t)zf_len(g->dev) * dtype_size(t);
     if (bytes > STATIC_SCRATCH_BYTES) {
-        set_error("cbct_project_static: volume needs more than the 64 MiB of static scratch "
-                  "(at most 2^24 FP32 or 2^25 FP16/BF16 voxels)");
+        set_error("cbct_project_static: the volume's padded copy (nx ny (nz + 2) + 4 elements) needs more "
+                  "than the 66 MiB of static scratch (a 256^3 FP32 volume fits)");
         return CBCT_EINVAL;
     }
     cbct_status st0 = require_geometry_device(g, "cbct_project_static");
@@ -62,9 +63,9 @@ extern "C" cbct_status cbct_project_static(const cbct_geometry *g, const void *x
     cbct_status st = scratch_for_current_device(&scratch);
     if (st != CBCT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // The re-layout writes every one of the M scratch values before the forward
-    // kernel reads any, so nothing left by an earlier call is used and nothing
-    // has to be cleared.
+    // The re-layout writes every voxel, pad and guard of the padded copy before
+    // the forward kernel reads any, so nothing left by an earlier call is used
+    // and nothing has to be cleared.
     st = launch_relayout(g->dev, x, scratch, t, true, s);
     if (st != CBCT_OK) return st;
     const Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};

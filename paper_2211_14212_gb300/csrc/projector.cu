@@ -17,8 +17,9 @@ namespace cbct {
 
 // ------------------------------------------------------------- forward A x
 
+// 4 rays per lane hold 80 registers (3 CTAs per SM); fewer fit in 64.
 template <typename T, bool COMP, int R, bool VF>
-__global__ void __launch_bounds__(FWD_THREADS, 4)
+__global__ void __launch_bounds__(FWD_THREADS, R >= 4 ? 3 : 4)
 forward_kernel(DevGeom g, const T *__restrict__ vol, T *__restrict__ proj, Epilogue epi) {
     __shared__ double red[FWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
@@ -106,20 +107,24 @@ cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaSt
 
 // ---------------------------------------------------------- transpose A^T y
 
-template <typename T, bool ZFAST, int CX, int K>
-__global__ void __launch_bounds__(BWD_THREADS, K >= 8 ? 3 : 4)
+template <typename T, bool ZFAST, int CX, int K, bool HOIST>
+__global__ void __launch_bounds__(BWD_THREADS, (K >= 8 || (HOIST && K >= 4)) ? 3 : 4)
 backward_kernel(DevGeom g, const float *__restrict__ proj, T *__restrict__ vol, Epilogue epi, int a_begin, int a_end,
                 const float *acc_in, float *acc_out) {
     __shared__ double red[BWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    backward_tile<T, ZFAST, CX, K>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z, a_begin, a_end, acc_in,
+    backward_tile<T, ZFAST, CX, K, HOIST>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z, a_begin, a_end, acc_in,
                                    acc_out, epi.partial ? epi.partial + b : nullptr, red);
 }
 
-// Transpose tile shapes: column patch CX x (8 / CX), 32 K voxels along z.
+// Transpose tile shapes: column patch CX x (8 / CX), 32 K voxels along z;
+// configurations 0..3 and 8, 9 keep the slab intervals of their candidate
+// rows in registers per angle (8, 9: 4 voxels per lane, 3 CTAs per SM).
 BrickShape backward_shape(int config) {
     switch (config) {
+    case 8: return BrickShape{2, 4, 128, 4};
+    case 9: return BrickShape{4, 2, 128, 4};
     case 1: return BrickShape{4, 2, 64, 2};
     case 2: return BrickShape{8, 1, 32, 1};
     case 3: return BrickShape{2, 4, 64, 2};
@@ -148,14 +153,16 @@ static void launch_backward_t(const DevGeom &g, const float *y, void *x, const E
     const float *yy = y;
     T *xx = (T *)x;
     switch (g.bwd_config) {
-    case 1: backward_kernel<T, ZF, 4, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 2: backward_kernel<T, ZF, 8, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 3: backward_kernel<T, ZF, 2, 2><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 4: backward_kernel<T, ZF, 4, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 5: backward_kernel<T, ZF, 2, 4><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 6: backward_kernel<T, ZF, 4, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 7: backward_kernel<T, ZF, 2, 8><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    default: backward_kernel<T, ZF, 4, 1><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 1: backward_kernel<T, ZF, 4, 2, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 2: backward_kernel<T, ZF, 8, 1, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 3: backward_kernel<T, ZF, 2, 2, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 4: backward_kernel<T, ZF, 4, 4, false><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 5: backward_kernel<T, ZF, 2, 4, false><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 6: backward_kernel<T, ZF, 4, 8, false><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 7: backward_kernel<T, ZF, 2, 8, false><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 8: backward_kernel<T, ZF, 2, 4, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    case 9: backward_kernel<T, ZF, 4, 4, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
+    default: backward_kernel<T, ZF, 4, 1, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
     }
 }
 
@@ -344,31 +351,43 @@ cbct_status launch_proj_relayout(const DevGeom &g, const void *src, void *dst, c
 
 // ------------------------------------------------------- volume re-layout
 //
-// Standard x[k][j][i] <-> z-fastest x[j][i][k]: for each j a (k, i) plane is
-// transposed through a 32 x 33 shared tile (coalesced on both sides).
+// Standard x[k][j][i] <-> padded z-fastest (zf_col(i, j) + k): for each j a
+// (k, i) plane is transposed through a 32 x 33 shared tile (coalesced on both
+// sides).  Towards the padded layout the kernel also writes the zero pads of
+// every column it covers and (block (0, 0, 0)) the guards at both ends.
 
 template <typename T, bool TO_ZFAST>
-__global__ void __launch_bounds__(256) relayout_kernel(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
-                                                       int nz) {
+__global__ void __launch_bounds__(256) relayout_kernel(DevGeom g, const T *__restrict__ src, T *__restrict__ dst) {
     __shared__ T tile[32][33];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int j = blockIdx.z;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    if (TO_ZFAST) {                 // src [k][j][i] -> dst [j][i][k]
+    if (TO_ZFAST) {                 // src [k][j][i] -> dst padded [j][i][k]
         const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
         for (int r = ty; r < 32; r += 8) {
             const int k = k0 + r, i = i0 + tx;
             if (k < nz && i < nx) tile[r][tx] = src[((size_t)k * ny + j) * nx + i];
         }
         __syncthreads();
+        const T zero = T(0.0f);
         for (int r = ty; r < 32; r += 8) {
             const int i = i0 + r, k = k0 + tx;
-            if (i < nx && k < nz) dst[((size_t)j * nx + i) * nz + k] = tile[tx][r];
+            if (i < nx && k < nz) {
+                const size_t c = (size_t)zf_col(g, i, j);
+                dst[c + k] = tile[tx][r];
+                if (k == 0) dst[c - 1] = zero;
+                if (k == nz - 1) dst[c + nz] = zero;
+            }
         }
-    } else {                        // src [j][i][k] -> dst [k][j][i]
+        if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < ZF_GUARD) {
+            dst[threadIdx.x] = zero;
+            dst[zf_len(g) - 1 - threadIdx.x] = zero;
+        }
+    } else {                        // src padded [j][i][k] -> dst [k][j][i]
         const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
         for (int r = ty; r < 32; r += 8) {
             const int i = i0 + r, k = k0 + tx;
-            if (i < nx && k < nz) tile[r][tx] = src[((size_t)j * nx + i) * nz + k];
+            if (i < nx && k < nz) tile[r][tx] = src[(size_t)zf_col(g, i, j) + k];
         }
         __syncthreads();
         for (int r = ty; r < 32; r += 8) {
@@ -382,10 +401,10 @@ template <typename T>
 static void launch_relayout_t(const DevGeom &g, const void *src, void *dst, bool to_zfast, cudaStream_t s) {
     if (to_zfast) {
         const dim3 grid((g.nx + 31) / 32, (g.nz + 31) / 32, g.ny);
-        relayout_kernel<T, true><<<grid, 256, 0, s>>>((const T *)src, (T *)dst, g.nx, g.ny, g.nz);
+        relayout_kernel<T, true><<<grid, 256, 0, s>>>(g, (const T *)src, (T *)dst);
     } else {
         const dim3 grid((g.nz + 31) / 32, (g.nx + 31) / 32, g.ny);
-        relayout_kernel<T, false><<<grid, 256, 0, s>>>((const T *)src, (T *)dst, g.nx, g.ny, g.nz);
+        relayout_kernel<T, false><<<grid, 256, 0, s>>>(g, (const T *)src, (T *)dst);
     }
 }
 
@@ -396,6 +415,24 @@ cbct_status launch_relayout(const DevGeom &g, const void *src, void *dst, cbct_d
     case CBCT_F16: launch_relayout_t<__half>(g, src, dst, to_zfast, s); break;
     case CBCT_BF16: launch_relayout_t<__nv_bfloat16>(g, src, dst, to_zfast, s); break;
     }
+    CBCT_CUDA_TRY(cudaGetLastError());
+    return CBCT_OK;
+}
+
+// x = value in every voxel, 0 in every pad and guard (padded z-fastest, FP32).
+__global__ void __launch_bounds__(256) fill_volume_kernel(DevGeom g, float *__restrict__ x, float value) {
+    const int64_t n = zf_len(g);
+    const int nzp = g.nz + 2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e - ZF_GUARD;
+        const int64_t k = c % nzp - 1;          // -1 and nz: pads
+        const bool voxel = c >= 0 && c < n - 2 * ZF_GUARD && k >= 0 && k < g.nz;
+        x[e] = voxel ? value : 0.0f;
+    }
+}
+
+cbct_status launch_fill_volume(const DevGeom &g, float *x, float value, cudaStream_t s) {
+    fill_volume_kernel<<<1024, 256, 0, s>>>(g, x, value);
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;
 }
@@ -415,9 +452,9 @@ extern "C" cbct_status cbct_project(const cbct_geometry *g, const void *x, void 
     cbct_status st = check_pair(g, x, y, t, "cbct_project");
     if (st != CBCT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // the forward kernel reads the z-fastest layout: re-lay the caller's volume first
+    // the forward kernel reads the padded z-fastest layout: re-lay the caller's volume first
     void *tmp = nullptr;
-    CBCT_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)cbct_geometry_num_voxels(g) * dtype_size(t), s));
+    CBCT_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)zf_len(g->dev) * dtype_size(t), s));
     st = launch_relayout(g->dev, x, tmp, t, true, s);
     if (st == CBCT_OK) {
         Epilogue epi{nullptr, nullptr, 1.0, 0.0, nullptr, nullptr, nullptr};

@@ -15,10 +15,11 @@
 // k of one voxel column, gather one contiguous run.
 //
 // Both projectors take every plane crossing from the per-ray tables of
-// DevGeom through plane_alpha, so a ray/voxel segment has the same FP32 length
-// in both: the backprojector is the transpose of the forward projector, not an
+// DevGeom (the x/y crossings through plane_alpha in both), so the
+// backprojector is the transpose of the forward projector, not an
 // approximation of it (the paper traces Krylov instabilities to unmatched
-// backprojectors, Sec. 2.1.4 and Sec. 4).
+// backprojectors, Sec. 2.1.4 and Sec. 4); in FP32 their segment lengths agree
+// to rounding.
 #pragma once
 
 #include <cfloat>
@@ -222,10 +223,177 @@ __device__ __forceinline__ void load_rays(const DevGeom &g, int a, int iu, int i
     }
 }
 
+// ------------------------------------------- z index from alpha (forward)
+//
+// Along a ray the z voxel coordinate is linear in alpha: measured from the
+// plane pq nearest to the ray origin, zeta(alpha) - pq = alpha / (dz I) -
+// f / dz.  Its floor, the voxel index k, comes from one FMA and one add of
+// 1.5 * 2^23 + pq (the add rounds to an integer, and the float's bits are
+// then k + MAGIC_BITS); k - pq comes back exactly by subtracting the same
+// constant.  The alpha at which the ray leaves voxel k through a z plane is
+// (k - pq) (dz I) + c, both terms small (no cancellation).  alpha is clamped to
+// the ray's range inside [0, nz) along z, so every segment outside the volume
+// has zero length and k stays in [-1, nz].
+constexpr float ZMAGIC = 12582912.0f;        // 1.5 * 2^23
+constexpr int ZMAGIC_BITS = 0x4B400000;
+
+struct RayZ {
+    float a, b;          // (zeta - pq) - 0.5 = a * alpha + b (voxel units)
+    float m;             // ZMAGIC + pq
+    float inva, c;       // exit-plane alpha of voxel k: (k - pq) * inva + c
+    float lo, hi;        // alpha range inside the slab [0, nz)
+    int soff;            // +1 / -1 / 0: neighbour voxel across the exit plane
+};
+
+__device__ __forceinline__ RayZ make_rayz(const RayAxis &rz, float dz, int nz) {
+    RayZ r;
+    r.m = ZMAGIC + rz.pq;
+    if (rz.I == 0.0f) {                          // parallel to the z planes: fixed voxel pq
+        const bool in = rz.pq >= 0.0f && rz.pq < (float)nz;
+        r.a = r.b = r.inva = 0.0f;
+        r.c = FLT_MAX;
+        r.lo = in ? -FLT_MAX : 0.0f;
+        r.hi = in ? FLT_MAX : 0.0f;
+        r.soff = 0;
+        return r;
+    }
+    const float a0 = plane_alpha(0.0f - rz.pq, dz, rz), a1 = plane_alpha((float)nz - rz.pq, dz, rz);
+    r.lo = fminf(a0, a1);
+    r.hi = fmaxf(a0, a1);
+    r.inva = dz * rz.I;
+    r.a = 1.0f / r.inva;
+    r.b = -rz.f / dz - 0.5f;
+    const bool up = rz.I > 0.0f;                 // alpha grows with the plane index
+    r.c = up ? (dz + rz.f) * rz.I : rz.f * rz.I; // exit plane of voxel k: k + 1 (up) or k (down)
+    r.soff = up ? 1 : -1;
+    return r;
+}
+
+// Forward traversal of R rays of one detector column through the padded
+// z-fastest volume, for geometries with at most one z-plane crossing per xy
+// cell (DevGeom::zsingle).  At every xy cell boundary e each ray adds
+//     (e - e_prev) v + max(e - ze, 0) (vn - v),
+// v and vn the voxel it occupied on entering the cell and its neighbour across
+// the next z plane (crossed at ze if ze < e): both are loaded for every cell,
+// so no lane branches.  The next cell's voxel index comes from zeta(e).  Ray
+// pairs use packed FP32x2 arithmetic unless COMP (Kahan-compensated sums, for
+// 16-bit storage).  Returns the ray sums in acc (alpha units).
+template <typename T, bool COMP, int R>
+__device__ __forceinline__ void trace_rays_zsingle(const DevGeom &g, const T *__restrict__ vol, const RayAxis &rx,
+                                                   const RayAxis &ry, const RayAxis (&rzax)[R], float (&acc)[R]) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    float amin = -FLT_MAX, amax = FLT_MAX;
+    bool miss = false;
+    clip_slab(rx, g.dx, 0, nx, amin, amax, miss);
+    clip_slab(ry, g.dy, 0, ny, amin, amax, miss);
+    if (miss || !(amin < amax)) return;
+    Axis ax = axis_start(rx, g.dx, amin, 0, nx);
+    Axis ay = axis_start(ry, g.dy, amin, 0, ny);
+    const int sx = nz + 2, sy = nx * (nz + 2);
+    // index of voxel k of the current column is base + bits(k + ZMAGIC)
+    int base = (int)zf_col(g, ax.i, ay.i) - ZMAGIC_BITS;
+    RayZ z[R];
+    float kf[R], v[R], vn[R], ep[R], comp[R];
+    auto ld = [&](int idx) { return Storage<T>::load(vol + idx); };
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        z[r] = make_rayz(rzax[r], g.dz, nz);
+        ep[r] = fminf(fmaxf(amin, z[r].lo), z[r].hi);
+        const float kb = __fadd_rn(__fmaf_rn(ep[r], z[r].a, z[r].b), z[r].m);
+        kf[r] = __fadd_rn(kb, -z[r].m);
+        const int idx = base + __float_as_int(kb);
+        v[r] = ld(idx);
+        vn[r] = ld(idx + z[r].soff);
+        comp[r] = 0.0f;
+    }
+    auto kahan = [&](int r, float term) {
+        const float yk = term - comp[r];
+        const float t = acc[r] + yk;
+        comp[r] = (t - acc[r]) - yk;
+        acc[r] = t;
+    };
+    const int dcx = ax.s * sx, dcy = ay.s * sy;
+    const int maxsteps = nx + ny + 1;
+#pragma unroll 1
+    for (int n = 0; n < maxsteps; ++n) {
+        const float e = fminf(ax.e, ay.e);
+        float kbn[R];
+        if (!COMP && R % 2 == 0) {
+#pragma unroll
+            for (int p = 0; p < R / 2; ++p) {
+                const int r0 = 2 * p, r1 = r0 + 1;
+                const float2 ec = make_float2(fminf(fmaxf(e, z[r0].lo), z[r0].hi), fminf(fmaxf(e, z[r1].lo), z[r1].hi));
+                const float2 len = __fadd2_rn(ec, make_float2(-ep[r0], -ep[r1]));
+                float2 a2 = __ffma2_rn(len, make_float2(v[r0], v[r1]), make_float2(acc[r0], acc[r1]));
+                const float2 ze = __ffma2_rn(make_float2(kf[r0], kf[r1]), make_float2(z[r0].inva, z[r1].inva),
+                                             make_float2(z[r0].c, z[r1].c));
+                const float2 d = __fadd2_rn(ec, make_float2(-ze.x, -ze.y));
+                const float2 w = make_float2(fmaxf(d.x, 0.0f), fmaxf(d.y, 0.0f));
+                const float2 dv = __fadd2_rn(make_float2(vn[r0], vn[r1]), make_float2(-v[r0], -v[r1]));
+                a2 = __ffma2_rn(w, dv, a2);
+                acc[r0] = a2.x;
+                acc[r1] = a2.y;
+                const float2 t = __ffma2_rn(ec, make_float2(z[r0].a, z[r1].a), make_float2(z[r0].b, z[r1].b));
+                const float2 kb = __fadd2_rn(t, make_float2(z[r0].m, z[r1].m));
+                const float2 kn = __fadd2_rn(kb, make_float2(-z[r0].m, -z[r1].m));
+                kbn[r0] = kb.x;
+                kbn[r1] = kb.y;
+                kf[r0] = kn.x;
+                kf[r1] = kn.y;
+                ep[r0] = ec.x;
+                ep[r1] = ec.y;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float ec = fminf(fmaxf(e, z[r].lo), z[r].hi);
+                const float ze = __fmaf_rn(kf[r], z[r].inva, z[r].c);
+                const float w = fmaxf(ec - ze, 0.0f);
+                if (COMP) {
+                    kahan(r, (ec - ep[r]) * v[r]);
+                    kahan(r, w * (vn[r] - v[r]));
+                } else {
+                    acc[r] = __fmaf_rn(ec - ep[r], v[r], acc[r]);
+                    acc[r] = __fmaf_rn(w, vn[r] - v[r], acc[r]);
+                }
+                const float kb = __fadd_rn(__fmaf_rn(ec, z[r].a, z[r].b), z[r].m);
+                kf[r] = __fadd_rn(kb, -z[r].m);
+                kbn[r] = kb;
+                ep[r] = ec;
+            }
+        }
+        bool done;
+        if (e == ax.e) {
+            ax.i += ax.s;
+            done = (unsigned)ax.i >= (unsigned)nx;
+            if (!done) {
+                base += dcx;
+                ax.r += (float)ax.s;
+                ax.e = plane_alpha(ax.r, g.dx, rx);
+            }
+        } else {
+            ay.i += ay.s;
+            done = (unsigned)ay.i >= (unsigned)ny;
+            if (!done) {
+                base += dcy;
+                ay.r += (float)ay.s;
+                ay.e = plane_alpha(ay.r, g.dy, ry);
+            }
+        }
+        if (done) break;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int idx = base + __float_as_int(kbn[r]);
+            v[r] = ld(idx);
+            vn[r] = ld(idx + z[r].soff);
+        }
+    }
+}
+
 // ------------------------------------------------------------- forward A x
 //
 // One tile = 8 warps = 8 adjacent detector columns (iu) x 32 R detector rows
-// (iv) of one angle.  The volume is read z-fastest: vol[(j * nx + i) * nz + k].
+// (iv) of one angle.  The volume is read in the padded z-fastest layout.
 // Epilogue: proj = a * (A vol) + b * old (either projection layout), and one
 // FP64 sum of squares of the stored values into *partial (when non-null).
 
@@ -239,26 +407,35 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
     const int iu = tx * FWD_COLS + warp;
     const int iv0 = ty * 32 * R;
     const bool col_ok = iu < g.nu;            // uniform across the warp
-    float acc[R], comp[R];
+    float acc[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = comp[r] = 0.0f;
+    for (int r = 0; r < R; ++r) acc[r] = 0.0f;
     if (col_ok) {
         RayAxis rx, ry, rz[R];
         load_rays<R>(g, a, iu, iv0, g.nv, rx, ry, rz);
-        auto fetch = [&](int idx) { return Storage<T>::load(vol + idx); };
-        auto seg = [&](int r, float len, float value) {
-            const float term = len * value;
-            if (COMP) {          // Kahan-compensated running sum
-                const float yk = term - comp[r];
-                const float t = acc[r] + yk;
-                comp[r] = (t - acc[r]) - yk;
-                acc[r] = t;
-            } else {
-                acc[r] += term;
-            }
-        };
-        // z-fastest volume: voxel (i, j, k) at (j * nx + i) * nz + k
-        trace_columns<R>(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, 0, g.nz, g.nx * g.nz, fetch, seg);
+        if (g.zsingle) {
+            trace_rays_zsingle<T, COMP, R>(g, vol, rx, ry, rz, acc);
+        } else {
+            // several z crossings per xy cell are possible: the exact
+            // crossing-by-crossing traversal
+            float comp[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) comp[r] = 0.0f;
+            auto fetch = [&](int idx) { return Storage<T>::load(vol + idx); };
+            auto seg = [&](int r, float len, float value) {
+                const float term = len * value;
+                if (COMP) {          // Kahan-compensated running sum
+                    const float yk = term - comp[r];
+                    const float t = acc[r] + yk;
+                    comp[r] = (t - acc[r]) - yk;
+                    acc[r] = t;
+                } else {
+                    acc[r] += term;
+                }
+            };
+            trace_columns<R>(g, rx, ry, rz, 0, g.nx, 0, g.ny, 0, g.nz, (int)zf_col(g, 0, 0), g.nz + 2,
+                             g.nx * (g.nz + 2), fetch, seg);
+        }
     }
     double sq = 0.0;
     const double acoef = epi_a(epi), bcoef = epi_b(epi);
@@ -303,8 +480,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
 //     [max(ain, z entry), min(aout, z exit)].
 // The z entry/exit of a row's ray in slab k does not depend on the angle
 // (circular orbit), so it is read from the table DevGeom::zbox, which
-// plane_alpha filled at geometry creation: every length is bit-identical to
-// the forward projector's, and A^T is the exact transpose.
+// plane_alpha filled at geometry creation.
 // Projections are read v-fastest and pre-weighted by the ray length:
 // w[a][iu][iv] = |d'| * y.
 
@@ -315,15 +491,19 @@ constexpr int BWD_SHORT_ROWS = 3;
 // do not fit in L2 is summed in passes over blocks of angles (launch_backward):
 // `acc_in` (if not null) holds the FP32 sums of the earlier passes and
 // `acc_out` (if not null) receives the running sums instead of the volume, so
-// only the last pass applies the epilogue.  Both are z-fastest, indexed like
-// the internal volume; they may be the same buffer (each lane reads and writes
-// only its own voxels).
-template <typename T, bool ZFAST, int CX, int K>
+// only the last pass applies the epilogue.  Both are indexed
+// ((j * nx + i) * nz + k) (unpadded); they may be the same buffer (each lane
+// reads and writes only its own voxels).  ZFAST output goes to the padded
+// z-fastest layout, else to the ABI layout x[k][j][i].
+template <typename T, bool ZFAST, int CX, int K, bool HOIST>
 __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__restrict__ wproj, T *__restrict__ vol,
                                               const Epilogue &epi, int tx, int ty, int tz, int a_begin, int a_end,
                                               const float *acc_in, float *acc_out, double *partial,
                                               double *red) {
     constexpr int CY = 8 / CX;
+    // HOIST: the slab intervals of the candidate rows are loaded once per
+    // angle and kept in registers (3 x 2 per voxel of the lane); otherwise
+    // they are loaded for every detector column.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = tx * CX + (warp % CX), j = ty * CY + (warp / CX);
     const int k0 = tz * 32 * K;
@@ -344,6 +524,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
         // the 0.05-pixel margins.
         const float inv_du = 1.0f / g.du, inv_dv = 1.0f / g.dv;
         const size_t nuv = (size_t)g.nu * g.nv;
+        const int rlast = g.nv - BWD_SHORT_ROWS;     // first row of the last full short window
         for (int a = a_begin; a < a_end; ++a) {
             const float2 cs = g.trig[a];
             float umin = FLT_MAX, umax = -FLT_MAX, magmin = FLT_MAX, magmax = 0.0f;
@@ -366,53 +547,98 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
             // extreme at a corner).  The window holds for every detector
             // column below; a row that misses the voxel for one of them adds
             // an exact zero.
-            int r0[K], r1[K];
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
+            auto window = [&](int kk, int &lo, int &hi) {
                 const int k = k0 + kk * 32 + lane;
                 const float zlo = (g.bz0 + k * g.dz) * inv_dv, zhi = (g.bz0 + (k + 1) * g.dz) * inv_dv;
                 const float vmin = fminf(zlo * magmin, zlo * magmax);
                 const float vmax = fmaxf(zhi * magmin, zhi * magmax);
-                r0[kk] = max(0, (int)ceilf(vmin + (cv - 0.05f)));
-                r1[kk] = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
-            }
+                lo = max(0, (int)ceilf(vmin + (cv - 0.05f)));
+                hi = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
+            };
             // Windows of at most BWD_SHORT_ROWS rows in every lane (the usual
-            // case: a slab spans dz * mag / dv rows) take a fixed, predicated
-            // sequence instead of a loop; the same rows are summed in the same
-            // order either way.
-            bool short_rows = true;
+            // case: a slab spans dz * mag / dv rows) take a fixed sequence of
+            // BWD_SHORT_ROWS rows starting at r0 (moved down to fit the
+            // detector) instead of a loop; rows outside the window meet the
+            // voxel nowhere and add exact zeros, so the same nonzero terms are
+            // summed in the same order either way.
+            int r0[K];
+            bool short_rows = !HOIST || rlast >= 0;
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) short_rows = short_rows && r1[kk] - r0[kk] < BWD_SHORT_ROWS;
+            for (int kk = 0; kk < K; ++kk) {
+                int hi;
+                window(kk, r0[kk], hi);
+                short_rows = short_rows && hi - r0[kk] < BWD_SHORT_ROWS;
+            }
             short_rows = __all_sync(0xffffffffu, short_rows);
             const float *pa = wproj + (size_t)a * nuv;
-            for (int iu = iu0; iu <= iu1; ++iu) {
-                const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
-                const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
-                float ain = -FLT_MAX, aout = FLT_MAX;
-                bool miss = false;
-                clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
-                clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
-                if (miss || !(ain < aout)) continue;
-                const float *wcol = pa + (size_t)iu * g.nv;
-                if (short_rows) {
+            if (short_rows) {
+                // HOIST: the fixed sequence starts at r0 moved down to fit the
+                // detector and the three rows' slab intervals are loaded once
+                // per angle (a row outside the window meets the voxel nowhere:
+                // exact zero); otherwise the rows past the window are skipped,
+                // their intervals read per detector column.
+                float2 zb[HOIST ? K : 1][BWD_SHORT_ROWS];
+                int r1[HOIST ? 1 : K];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    if (HOIST) {
+                        r0[kk] = min(r0[kk], rlast);
+                        const float2 *zr = g.zbox + (size_t)min(k0 + kk * 32 + lane, g.nz - 1) * g.nv + r0[kk];
+#pragma unroll
+                        for (int t = 0; t < BWD_SHORT_ROWS; ++t) zb[HOIST ? kk : 0][t] = zr[t];
+                    } else {
+                        int lo;
+                        window(kk, lo, r1[HOIST ? 0 : kk]);
+                    }
+                }
+                for (int iu = iu0; iu <= iu1; ++iu) {
+                    const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
+                    const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
+                    float ain = -FLT_MAX, aout = FLT_MAX;
+                    bool miss = false;
+                    clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
+                    clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
+                    if (miss || !(ain < aout)) continue;
+                    const float *wcol = pa + (size_t)iu * g.nv;
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) {
-                        const float2 *zb = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv;
+                        const float *wr = wcol + r0[kk];
+                        if (HOIST) {
 #pragma unroll
-                        for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
-                            const int iv = r0[kk] + t;
-                            if (iv <= r1[kk]) {
-                                const float2 e = zb[iv];
+                            for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
+                                const float2 e = zb[HOIST ? kk : 0][t];
                                 const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
-                                acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
+                                acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wr + t), acc[kk]);
+                            }
+                        } else {
+                            const float2 *zb2 = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv + r0[kk];
+#pragma unroll
+                            for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
+                                if (r0[kk] + t <= r1[HOIST ? 0 : kk]) {
+                                    const float2 e = zb2[t];
+                                    const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
+                                    acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wr + t), acc[kk]);
+                                }
                             }
                         }
                     }
-                } else {
+                }
+            } else {
+                for (int iu = iu0; iu <= iu1; ++iu) {
+                    const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
+                    const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
+                    float ain = -FLT_MAX, aout = FLT_MAX;
+                    bool miss = false;
+                    clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
+                    clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
+                    if (miss || !(ain < aout)) continue;
+                    const float *wcol = pa + (size_t)iu * g.nv;
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) {
-                        const float2 *zb = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv;
-                        for (int iv = r0[kk]; iv <= r1[kk]; ++iv) {
+                        const float2 *zb = g.zbox + (size_t)min(k0 + kk * 32 + lane, g.nz - 1) * g.nv;
+                        int rlo, rhi;
+                        window(kk, rlo, rhi);
+                        for (int iv = rlo; iv <= rhi; ++iv) {
                             const float2 e = zb[iv];         // row iv's alpha interval in slab k
                             const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
                             // a miss adds exactly zero: the same sum as skipping it
@@ -437,7 +663,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
     for (int kk = 0; kk < K; ++kk) {
         const int k = k0 + kk * 32 + lane;
         if (!col_ok || k >= g.nz) continue;
-        const size_t v = ZFAST ? ((size_t)j * g.nx + i) * g.nz + k : ((size_t)k * g.ny + j) * g.nx + i;
+        const size_t v = ZFAST ? (size_t)(zf_col(g, i, j) + k) : ((size_t)k * g.ny + j) * g.nx + i;
         double out = acoef * (double)acc[kk];
         if (bcoef != 0.0) {
             const T *oldp = epi.old ? (const T *)epi.old : (const T *)vol;

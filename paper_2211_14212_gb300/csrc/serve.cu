@@ -7,10 +7,11 @@
 // forward launch walks the forward tiles of all slots in the step, one
 // transpose launch walks all their tiles, one launch per scalar step handles
 // all of them (one block each) and one launch updates all their vectors.  The
-// schedule picks the set: shortest remaining work first until the step's
-// forward tiles fill the GPU (SRPT, the default), or every slot (SHARE).  A
-// slot finishes, its result is copied out and its memory is freed while the
-// others continue; waiting requests are admitted between steps.  The launch
+// schedule picks the set: the oldest slots until the step's forward tiles
+// fill the GPU (FIFO), the shortest remaining work first (SRPT), the highest
+// response ratio (RATIO), or every slot (SHARE).  Admission (tables, upload
+// of b, the solver's start) and read-out (x to the host, freeing) run on
+// their own threads and streams while the steps go on.  The launch
 // topology of a step does not depend on the set (fixed persistent grids, a
 // device slot table), so one captured CUDA graph is replayed for every step.
 //
@@ -37,10 +38,11 @@
 namespace cbct {
 
 constexpr int SRV_MAX_SLOTS = 64;
-constexpr int SRV_FWD_ROWS = 2;                       // forward tile: 2 rays per lane
-constexpr int64_t SRV_SAT_TILES = 4096;                // SRPT: forward tiles that fill a step (~5 waves)
-constexpr int SRV_CX = 2, SRV_BK = 4;                  // transpose tile: 2 x 4 columns x 128 (configuration 5)
-constexpr int SRV_BWD_CONFIG = 5;
+constexpr int SRV_FWD_ROWS = 4;                       // forward tile: 4 rays per lane
+constexpr int64_t SRV_SAT_TILES = 2048;                // forward tiles (8 columns x 128 rows) that fill a step
+constexpr int SRV_SRPT_AGE_CAP = 64;                   // SRPT: steps a slot may be passed over before it goes first
+constexpr int SRV_CX = 2, SRV_BK = 2;                  // transpose tile: 2 x 4 columns x 64 (configuration 3)
+constexpr int SRV_BWD_CONFIG = 3;
 
 struct SlotDev {
     DevGeom g;
@@ -50,7 +52,7 @@ struct SlotDev {
     int method, cap;
     int fgx, fgy;          // forward tile grid (x: columns / 8, y: row groups); z: angles
     int bgx, bgy;          // brick grid (x, y); z: bricks along z
-    int64_t m;             // voxels
+    int64_t m;             // length of a volume-side vector (padded z-fastest layout)
 };
 
 struct SlotTable {
@@ -75,12 +77,24 @@ __device__ __forceinline__ int find_slot(const int *start, int n, int item) {
     return lo;
 }
 
+// Tiles are claimed one at a time from a counter (reset at the start of every
+// step), so that blocks that drew cheap tiles (columns that miss the volume,
+// voxel columns near the corners) take more: a persistent grid walking a fixed
+// stride leaves SMs idle at the end of each kernel.
+__device__ __forceinline__ int claim_tile(unsigned *counter, int *slot_sh) {
+    __syncthreads();                       // every thread is done with the previous tile
+    if (threadIdx.x == 0) *slot_sh = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    return *slot_sh;
+}
+
 // U <- fa * A V + fb * U for every slot (forward tiles of all slots).
-__global__ void __launch_bounds__(FWD_THREADS) srv_forward(const SlotTable *tab) {
+__global__ void __launch_bounds__(FWD_THREADS, 3) srv_forward(const SlotTable *tab, unsigned *counter) {
     __shared__ double red[FWD_THREADS / 32];
+    __shared__ int item_sh;
     const int n = tab->n;
     const int total = tab->fwd_start[n];
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    for (int item = claim_tile(counter, &item_sh); item < total; item = claim_tile(counter, &item_sh)) {
         const int s = find_slot(tab->fwd_start, n, item);
         const SlotDev &sd = tab->s[s];
         if (sd.st->stop) continue;
@@ -92,18 +106,19 @@ __global__ void __launch_bounds__(FWD_THREADS) srv_forward(const SlotTable *tab)
 }
 
 // V <- ba * A^T U + bb * V for every slot (transpose tiles of all slots, z-fastest volumes).
-__global__ void __launch_bounds__(BWD_THREADS) srv_backward(const SlotTable *tab) {
+__global__ void __launch_bounds__(BWD_THREADS, 4) srv_backward(const SlotTable *tab, unsigned *counter) {
     __shared__ double red[BWD_THREADS / 32];
+    __shared__ int item_sh;
     const int n = tab->n;
     const int total = tab->bwd_start[n];
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    for (int item = claim_tile(counter, &item_sh); item < total; item = claim_tile(counter, &item_sh)) {
         const int s = find_slot(tab->bwd_start, n, item);
         const SlotDev &sd = tab->s[s];
         if (sd.st->stop) continue;
         const int local = item - tab->bwd_start[s];
         const int tbx = local % sd.bgx, tby = (local / sd.bgx) % sd.bgy, tbz = local / (sd.bgx * sd.bgy);
         const Epilogue epi{&sd.st->ba, &sd.st->bb, 0.0, 0.0, nullptr, nullptr, nullptr};
-        backward_tile<float, true, SRV_CX, SRV_BK>(sd.g, sd.Uw, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
+        backward_tile<float, true, SRV_CX, SRV_BK, true>(sd.g, sd.Uw, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
                                                    nullptr, sd.pb + local, red);
     }
 }
@@ -188,7 +203,10 @@ struct Slot {
     GkState *st = nullptr;
     double *pf = nullptr, *pb = nullptr, *hist = nullptr;
     int nf = 0, nb = 0, steps = 0;
+    int passed_over = 0;              // consecutive steps this slot was left out of (SRPT aging)
+    bool aged = false;                // passed over SRV_SRPT_AGE_CAP steps in a row: first until it finishes
     double work_iter = 0.0;           // cost model of one iteration: rays x (nx + ny)
+    cudaEvent_t ready = nullptr;      // recorded on the admission stream once the set-up is queued
 };
 
 // Forward tiles and bricks of a scan under the server's launch shapes.
@@ -204,7 +222,8 @@ void grids(const cbct_geometry_desc &d, int &fgx, int &fgy, int &bgx, int &bgy, 
 // staging of b, partial sums, state and histories), rounded up per buffer.
 size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
     auto al = [](size_t b) { return (b + 1023) & ~(size_t)1023; };
-    const size_t n = (size_t)d.nangles * d.nv * d.nu, m = (size_t)d.nx * d.ny * d.nz;
+    // m: a volume-side vector in the padded z-fastest layout
+    const size_t n = (size_t)d.nangles * d.nv * d.nu, m = (size_t)d.nx * d.ny * (d.nz + 2) + 2 * ZF_GUARD;
     int fgx, fgy, bgx, bgy, bgz;
     grids(d, fgx, fgy, bgx, bgy, bgz);
     const size_t nf = (size_t)fgx * fgy * d.nangles, nb = (size_t)bgx * bgy * bgz;
@@ -219,22 +238,42 @@ size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
 
 }  // namespace
 
+// Three library threads share the work of a server, so that the steps never
+// wait for host-side work:
+//   admission   takes waiting requests in submission order while the budget
+//               and the slot count allow, builds the scan's tables, uploads b
+//               and queues the solver's start (b / ||b||, the first A^T) on
+//               its own stream, then hands the slot to the step thread with
+//               an event that orders the step stream after the set-up;
+//   steps       advances the admitted slots one Krylov iteration per step
+//               (one captured graph replayed) and hands finished slots on;
+//   read-out    copies each finished result to the host on its own stream,
+//               frees the slot's memory and wakes the waiters.
+// Geometries of finished slots are destroyed only while no slot is active
+// (their tables are a few MB), because freeing device memory waits for the
+// whole device.
 struct ServerImpl {
     size_t budget = 0, in_use = 0;
-    int max_slots = 1, use_graph = 1, device = 0, schedule = CBCT_SCHED_SRPT;
+    int max_slots = 1, use_graph = 1, device = 0, schedule = CBCT_SCHED_FIFO;
     double work_rate = 0.0;           // cost-model units per second, running estimate from timed steps
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_admit, cv_ready, cv_finish, cv_done;
     std::deque<std::shared_ptr<Request>> pending;
     std::map<uint64_t, std::shared_ptr<Request>> requests;
+    std::vector<Slot> ready;          // set up, not yet stepped (guarded by mu)
+    std::deque<Slot> finishing;       // stepped to the end, not yet read out (guarded by mu)
+    std::vector<cbct_geometry *> graveyard;   // geometries of read-out slots (guarded by mu)
+    int in_flight = 0;                // admitted and not yet finished stepping (guarded by mu)
+    int active_slots = 0;             // slots the step thread holds (guarded by mu)
     uint64_t next_id = 1;
-    bool stopping = false;
-    std::thread worker;
-    // worker-owned
-    cudaStream_t s = nullptr;
+    bool stopping = false, steps_stopped = false;
+    std::thread admitter, worker, reader;
+    cudaStream_t s = nullptr, s_admit = nullptr, s_read = nullptr;
+    // step-thread owned
     SlotTable *tab_host = nullptr, *tab_dev = nullptr;
     SlotStatus *stat_host = nullptr, *stat_dev = nullptr;
+    unsigned *counters = nullptr;     // tile counters of the forward and transpose kernels
     std::vector<Slot> slots;
     std::vector<int> step_slots;      // slots advanced by the current step, in slot-table order
     bool table_dirty = true;
@@ -242,17 +281,20 @@ struct ServerImpl {
     int fwd_grid = 0, bwd_grid = 0, vec_grid = 0;
     int64_t steps_run = 0, graph_replays = 0;
 
-    void run();
+    void run_admission();
+    void run_steps();
+    void run_readout();
     std::vector<int> pick_step_slots() const;
     cbct_status setup_slot(Slot &sl);
-    void release_slot(Slot &sl);
+    void release_slot(Slot &sl, cudaStream_t st, bool keep_geometry);
     cbct_status finish_slot(Slot &sl);
     cbct_status enqueue_step();
-    void fail_all(cbct_status st, const std::string &msg);
+    void complete(const std::shared_ptr<Request> &r, cbct_status st, const std::string &msg);
 };
 
 // -------------------------------------------------------------- slot life
 
+// On the admission thread and stream.
 cbct_status ServerImpl::setup_slot(Slot &sl) {
     Request &r = *sl.req;
     r.desc.angles_rad = r.angles.data();
@@ -261,12 +303,14 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     sl.geom->dev.fwd_rows = SRV_FWD_ROWS;
     sl.geom->dev.bwd_config = SRV_BWD_CONFIG;
     const DevGeom &g = sl.geom->dev;
-    const int64_t n = cbct_geometry_num_rays(sl.geom), m = cbct_geometry_num_voxels(sl.geom);
+    // m: a volume-side vector in the padded z-fastest layout (pads zeroed below)
+    const int64_t n = cbct_geometry_num_rays(sl.geom), m = zf_len(g);
     sl.nf = forward_num_blocks(g);
     sl.nb = backward_num_blocks(g);
     sl.work_iter = (double)n * (g.nx + g.ny);
+    cudaStream_t sa = s_admit;
     auto A = [&](auto **p, size_t cnt) {
-        return cudaMallocAsync((void **)p, cnt * sizeof(**p) + 16, s);
+        return cudaMallocAsync((void **)p, cnt * sizeof(**p) + 16, sa);
     };
     cudaError_t e = A(&sl.U, (size_t)n);
     if (e == cudaSuccess) e = A(&sl.Uw, (size_t)n);
@@ -279,71 +323,88 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     if (e == cudaSuccess) e = A(&sl.pb, (size_t)sl.nb);
     if (e == cudaSuccess) e = A(&sl.st, (size_t)1);
     if (e == cudaSuccess) e = A(&sl.hist, (size_t)2 * r.iters);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.b, r.b.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sl.x, 0, sizeof(float) * m, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sl.hist, 0, sizeof(double) * 2 * r.iters, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.b, r.b.data(), sizeof(float) * n, cudaMemcpyHostToDevice, sa);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl.x, 0, sizeof(float) * m, sa);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl.V, 0, sizeof(float) * m, sa);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl.w, 0, sizeof(float) * m, sa);
+    if (e == cudaSuccess && sl.h2) e = cudaMemsetAsync(sl.h2, 0, sizeof(float) * m, sa);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl.hist, 0, sizeof(double) * 2 * r.iters, sa);
     GkState init;
     std::memset(&init, 0, sizeof init);
     init.damp = r.damp;
     init.sqrt_n = std::sqrt((double)n);
-    init.sqrt_m = std::sqrt((double)m);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.st, &init, sizeof init, cudaMemcpyHostToDevice, s);
+    init.sqrt_m = std::sqrt((double)cbct_geometry_num_voxels(sl.geom));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.st, &init, sizeof init, cudaMemcpyHostToDevice, sa);
     if (e != cudaSuccess) return cuda_fail(e, "server: slot allocation");
     // beta_1 u_1 = b, alpha_1 v_1 = A^T u_1: the same start as the single-request solver
-    k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.b, n, sl.pf);
-    gk_begin<<<1, RED_THREADS, 0, s>>>(sl.st, sl.pf, VEC_BLOCKS);
+    k_sumsq<float><<<VEC_BLOCKS, VEC_THREADS, 0, sa>>>(sl.b, n, sl.pf);
+    gk_begin<<<1, RED_THREADS, 0, sa>>>(sl.st, sl.pf, VEC_BLOCKS);
     // U = su * b, v-fastest
-    st = launch_proj_relayout(g, sl.b, sl.U, CBCT_F32, true, s);
+    st = launch_proj_relayout(g, sl.b, sl.U, CBCT_F32, true, sa);
     if (st != CBCT_OK) return st;
-    k_scale_inplace<<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.U, n, &sl.st->c0, &sl.st->stop);
-    st = launch_weight(g, sl.U, CBCT_F32, sl.Uw, s);
+    k_scale_inplace<<<VEC_BLOCKS, VEC_THREADS, 0, sa>>>(sl.U, n, &sl.st->c0, &sl.st->stop);
+    st = launch_weight(g, sl.U, CBCT_F32, sl.Uw, sa);
     if (st != CBCT_OK) return st;
     Epilogue eb{&sl.st->ba, &sl.st->bb, 0.0, 0.0, sl.pb, &sl.st->stop, nullptr};
-    st = launch_backward(g, sl.Uw, sl.V, CBCT_F32, eb, s, true, nullptr);
+    st = launch_backward(g, sl.Uw, sl.V, CBCT_F32, eb, sa, true, nullptr);
     if (st != CBCT_OK) return st;
-    gk_begin2<<<1, RED_THREADS, 0, s>>>(sl.st, sl.pb, sl.nb, r.method);
-    k_start_dirs<float><<<VEC_BLOCKS, VEC_THREADS, 0, s>>>(sl.V, sl.w, r.method == M_LSMR ? sl.h2 : nullptr, nullptr,
-                                                           m, sl.st);
+    gk_begin2<<<1, RED_THREADS, 0, sa>>>(sl.st, sl.pb, sl.nb, r.method);
+    k_start_dirs<float><<<VEC_BLOCKS, VEC_THREADS, 0, sa>>>(sl.V, sl.w, r.method == M_LSMR ? sl.h2 : nullptr, nullptr,
+                                                            m, sl.st);
     CBCT_CUDA_TRY(cudaGetLastError());
-    CBCT_CUDA_TRY(cudaFreeAsync(sl.b, s));
+    CBCT_CUDA_TRY(cudaFreeAsync(sl.b, sa));
     sl.b = nullptr;
+    CBCT_CUDA_TRY(cudaEventCreateWithFlags(&sl.ready, cudaEventDisableTiming));
+    CBCT_CUDA_TRY(cudaEventRecord(sl.ready, sa));
     return CBCT_OK;
 }
 
-void ServerImpl::release_slot(Slot &sl) {
+// Frees the slot's buffers on stream `st`; the geometry is destroyed at once
+// or (keep_geometry) left in the graveyard for a quiet moment.
+void ServerImpl::release_slot(Slot &sl, cudaStream_t st, bool keep_geometry) {
     for (void *p : {(void *)sl.U, (void *)sl.Uw, (void *)sl.b, (void *)sl.V, (void *)sl.w, (void *)sl.x, (void *)sl.h2,
                     (void *)sl.pf, (void *)sl.pb, (void *)sl.st, (void *)sl.hist})
-        if (p) cudaFreeAsync(p, s);
+        if (p) cudaFreeAsync(p, st);
     sl.U = sl.Uw = sl.b = sl.V = sl.w = sl.x = sl.h2 = nullptr;
     sl.pf = sl.pb = sl.hist = nullptr;
     sl.st = nullptr;
+    if (sl.ready) {
+        cudaEventDestroy(sl.ready);
+        sl.ready = nullptr;
+    }
     if (sl.geom) {
-        cudaStreamSynchronize(s);
-        cbct_geometry_destroy(sl.geom);
+        cudaStreamSynchronize(st);
+        if (keep_geometry) {
+            std::lock_guard<std::mutex> lk(mu);
+            graveyard.push_back(sl.geom);
+        } else {
+            cbct_geometry_destroy(sl.geom);
+        }
         sl.geom = nullptr;
     }
 }
 
-// Read out a finished slot: x (caller layout), histories and final state.
+// On the read-out thread and stream: x (caller layout), histories and final state.
 cbct_status ServerImpl::finish_slot(Slot &sl) {
     Request &r = *sl.req;
     const int64_t m = cbct_geometry_num_voxels(sl.geom);
+    cudaStream_t sr = s_read;
     float *tmp = nullptr;
-    CBCT_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(float) * m, s));
-    cbct_status st = launch_relayout(sl.geom->dev, sl.x, tmp, CBCT_F32, false, s);
+    CBCT_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(float) * m, sr));
+    cbct_status st = launch_relayout(sl.geom->dev, sl.x, tmp, CBCT_F32, false, sr);
     r.x.assign((size_t)m, 0.0f);
     r.hist_r.assign((size_t)r.iters, 0.0);
     r.hist_n.assign((size_t)r.iters, 0.0);
     GkState fin;
     cudaError_t e = cudaSuccess;
-    if (st == CBCT_OK) e = cudaMemcpyAsync(r.x.data(), tmp, sizeof(float) * m, cudaMemcpyDeviceToHost, s);
+    if (st == CBCT_OK) e = cudaMemcpyAsync(r.x.data(), tmp, sizeof(float) * m, cudaMemcpyDeviceToHost, sr);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(r.hist_r.data(), sl.hist, sizeof(double) * r.iters, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(r.hist_r.data(), sl.hist, sizeof(double) * r.iters, cudaMemcpyDeviceToHost, sr);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(r.hist_n.data(), sl.hist + r.iters, sizeof(double) * r.iters, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&fin, sl.st, sizeof fin, cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(tmp, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        e = cudaMemcpyAsync(r.hist_n.data(), sl.hist + r.iters, sizeof(double) * r.iters, cudaMemcpyDeviceToHost, sr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&fin, sl.st, sizeof fin, cudaMemcpyDeviceToHost, sr);
+    cudaFreeAsync(tmp, sr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sr);
     if (st != CBCT_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "server: read-out");
     r.iters_done = fin.iter;
@@ -352,12 +413,28 @@ cbct_status ServerImpl::finish_slot(Slot &sl) {
     return CBCT_OK;
 }
 
+// Marks a request done (its memory already released) and wakes waiters and admission.
+void ServerImpl::complete(const std::shared_ptr<Request> &r, cbct_status st, const std::string &msg) {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (st != CBCT_OK) r->status = st;
+        if (!msg.empty()) r->error = msg;
+        r->done = true;
+        r->t_finish = now_s(t0);
+        in_use -= r->bytes;
+    }
+    cv_done.notify_all();
+    cv_admit.notify_one();
+}
+
 // One Krylov iteration of every slot, then the per-slot status to the host.
 cbct_status ServerImpl::enqueue_step() {
     auto launch_all = [&]() -> cudaError_t {
-        srv_forward<<<fwd_grid, FWD_THREADS, 0, s>>>(tab_dev);
+        cudaError_t e0 = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned), s);
+        if (e0 != cudaSuccess) return e0;
+        srv_forward<<<fwd_grid, FWD_THREADS, 0, s>>>(tab_dev, counters);
         srv_after_forward<<<SRV_MAX_SLOTS, RED_THREADS, 0, s>>>(tab_dev);
-        srv_backward<<<bwd_grid, BWD_THREADS, 0, s>>>(tab_dev);
+        srv_backward<<<bwd_grid, BWD_THREADS, 0, s>>>(tab_dev, counters + 1);
         srv_after_backward<<<SRV_MAX_SLOTS, RED_THREADS, 0, s>>>(tab_dev);
         srv_update<<<vec_grid, VEC_THREADS, 0, s>>>(tab_dev);
         srv_status<<<1, SRV_MAX_SLOTS, 0, s>>>(tab_dev, stat_dev);
@@ -391,31 +468,16 @@ cbct_status ServerImpl::enqueue_step() {
     return CBCT_OK;
 }
 
-void ServerImpl::fail_all(cbct_status st, const std::string &msg) {
-    std::vector<Slot> dead;
-    dead.swap(slots);
-    step_slots.clear();
-    for (Slot &sl : dead) release_slot(sl);
-    std::lock_guard<std::mutex> lk(mu);
-    for (Slot &sl : dead) {
-        sl.req->status = st;
-        sl.req->error = msg;
-        sl.req->done = true;
-        sl.req->t_finish = now_s(t0);
-        in_use -= sl.req->bytes;
-    }
-    table_dirty = true;
-    cv_done.notify_all();
-}
+// ---------------------------------------------------------------- schedules
 
-// ------------------------------------------------------------------ worker
-
-// SRPT: the slots with the least remaining work (iterations left x cost of
-// one), ties by request id; RATIO: the slots with the highest response ratio
-// (time since submission + remaining time) / remaining time, the remaining
-// time estimated from the cost model and the measured work rate, so that
-// short requests go first but a waiting request's priority grows with its
-// age.  Both take slots in that order as long as the step's forward tiles stay
+// FIFO: the slots in submission order; SRPT: the least remaining work
+// (iterations left x cost of one), ties by request id, except that slots
+// passed over for SRV_SRPT_AGE_CAP consecutive steps go first from then on
+// (oldest first), so a long request cannot wait for ever behind a stream of
+// short ones; RATIO: the highest
+// response ratio (time since submission + remaining time) / remaining time,
+// the remaining time from the cost model and the measured work rate.  All
+// three take slots in that order as long as the step's forward tiles stay
 // within SRV_SAT_TILES (the first slot always runs).  SHARE: every slot.
 // Returned in increasing slot index.
 std::vector<int> ServerImpl::pick_step_slots() const {
@@ -427,7 +489,11 @@ std::vector<int> ServerImpl::pick_step_slots() const {
     const double now = now_s(t0);
     for (size_t i = 0; i < slots.size(); ++i) {
         const double rem = remaining((int)i);
-        if (schedule == CBCT_SCHED_RATIO && work_rate > 0.0) {
+        if (schedule == CBCT_SCHED_FIFO) {
+            key[i] = (double)slots[i].req->id;
+        } else if (schedule == CBCT_SCHED_SRPT && slots[i].aged) {
+            key[i] = -1e300 + (double)slots[i].req->id;        // aged: ahead of every fresh slot, oldest first
+        } else if (schedule == CBCT_SCHED_RATIO && work_rate > 0.0) {
             const double rem_s = std::max(rem / work_rate, 1e-6);
             key[i] = -(now - slots[i].req->t_submit + rem_s) / rem_s;       // higher ratio first
         } else {
@@ -440,8 +506,8 @@ std::vector<int> ServerImpl::pick_step_slots() const {
     std::vector<int> pick;
     int64_t tiles = 0;
     for (int i : all) {
-        // a step's duration is its total work: never let a larger request join
-        // (and slow down) a step that smaller ones already fill
+        // a step's duration is its total work: never let a request join (and
+        // slow down) a step that the ones before it in the order already fill
         if (!pick.empty() && tiles + slots[i].nf > SRV_SAT_TILES) break;
         pick.push_back(i);
         tiles += slots[i].nf;
@@ -450,49 +516,75 @@ std::vector<int> ServerImpl::pick_step_slots() const {
     return pick;
 }
 
-void ServerImpl::run() {
+// ------------------------------------------------------------------ threads
+
+void ServerImpl::run_admission() {
     cudaSetDevice(device);
     for (;;) {
-        std::vector<std::shared_ptr<Request>> admit;
+        std::shared_ptr<Request> r;
         {
             std::unique_lock<std::mutex> lk(mu);
+            cv_admit.wait(lk, [&] {
+                return stopping || (!pending.empty() && in_flight < max_slots &&
+                                    in_use + pending.front()->bytes <= budget);
+            });
             if (stopping) break;
-            while (!pending.empty() && (int)(slots.size() + admit.size()) < max_slots &&
-                   in_use + pending.front()->bytes <= budget) {
-                std::shared_ptr<Request> r = pending.front();
-                pending.pop_front();
-                in_use += r->bytes;
-                r->t_admit = now_s(t0);
-                r->admitted = true;
-                admit.push_back(r);
-            }
-            if (slots.empty() && admit.empty()) {
-                cv_work.wait_for(lk, std::chrono::milliseconds(50));
-                continue;
-            }
+            r = pending.front();
+            pending.pop_front();
+            in_use += r->bytes;
+            ++in_flight;
+            r->t_admit = now_s(t0);
+            r->admitted = true;
         }
-        for (std::shared_ptr<Request> &r : admit) {
-            Slot sl;
-            sl.req = r;
-            cbct_status st = setup_slot(sl);
-            if (st != CBCT_OK) {
-                const std::string msg = cbct_last_error();
-                release_slot(sl);
+        Slot sl;
+        sl.req = r;
+        cbct_status st = setup_slot(sl);
+        if (st != CBCT_OK) {
+            const std::string msg = cbct_last_error();
+            release_slot(sl, s_admit, false);
+            {
                 std::lock_guard<std::mutex> lk(mu);
-                r->status = st;
-                r->error = msg;
-                r->done = true;
-                r->t_finish = now_s(t0);
-                in_use -= r->bytes;
-                cv_done.notify_all();
-                continue;
+                --in_flight;
             }
+            complete(r, st, msg);
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            ready.push_back(sl);
+        }
+        cv_ready.notify_one();
+    }
+}
+
+void ServerImpl::run_steps() {
+    cudaSetDevice(device);
+    for (;;) {
+        std::vector<Slot> incoming;
+        std::vector<cbct_geometry *> dead;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (slots.empty()) cv_ready.wait(lk, [&] { return stopping || !ready.empty(); });
+            if (stopping) break;
+            incoming.swap(ready);
+            active_slots = (int)(slots.size() + incoming.size());
+            if (slots.empty() && finishing.empty()) dead.swap(graveyard);     // a quiet moment
+        }
+        for (cbct_geometry *g : dead) cbct_geometry_destroy(g);
+        for (Slot &sl : incoming) {
+            cudaStreamWaitEvent(s, sl.ready, 0);          // the step stream follows the slot's set-up
             slots.push_back(sl);
             table_dirty = true;
         }
         if (slots.empty()) continue;
         {
             std::vector<int> pick = pick_step_slots();
+            std::vector<char> in_step(slots.size(), 0);
+            for (int i : pick) in_step[i] = 1;
+            for (size_t i = 0; i < slots.size(); ++i) {
+                slots[i].passed_over = in_step[i] ? 0 : slots[i].passed_over + 1;
+                if (slots[i].passed_over >= SRV_SRPT_AGE_CAP) slots[i].aged = true;
+            }
             if (pick != step_slots) {
                 step_slots.swap(pick);
                 table_dirty = true;
@@ -514,18 +606,15 @@ void ServerImpl::run() {
                 d.cap = sl.req->iters;
                 const dim3 fg = forward_grid(d.g), bg = backward_grid(d.g);
                 d.fgx = fg.x; d.fgy = fg.y; d.bgx = bg.x; d.bgy = bg.y;
-                d.m = cbct_geometry_num_voxels(sl.geom);
+                d.m = zf_len(d.g);
                 t.fwd_start[i + 1] = t.fwd_start[i] + sl.nf;
                 t.bwd_start[i + 1] = t.bwd_start[i] + sl.nb;
             }
-            if (cudaMemcpyAsync(tab_dev, tab_host, sizeof(SlotTable), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-                fail_all(cuda_fail(cudaGetLastError(), "server: slot table"), cbct_last_error());
-                continue;
-            }
-            table_dirty = false;
+            cudaError_t e = cudaMemcpyAsync(tab_dev, tab_host, sizeof(SlotTable), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) table_dirty = false;
         }
         const double t_step = now_s(t0);
-        cbct_status st = enqueue_step();
+        cbct_status st = table_dirty ? cuda_fail(cudaGetLastError(), "server: slot table") : enqueue_step();
         cudaError_t e = cudaStreamSynchronize(s);
         {   // running estimate of the work rate (cost-model units per second)
             double w = 0.0;
@@ -535,38 +624,73 @@ void ServerImpl::run() {
         }
         if (st != CBCT_OK || e != cudaSuccess) {
             if (e != cudaSuccess) st = cuda_fail(e, "server: step");
-            fail_all(st, cbct_last_error());
+            const std::string msg = cbct_last_error();
+            std::vector<Slot> failed;
+            failed.swap(slots);
+            step_slots.clear();
+            table_dirty = true;
+            for (Slot &sl : failed) {
+                std::shared_ptr<Request> r = sl.req;
+                release_slot(sl, s, false);
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    --in_flight;
+                }
+                complete(r, st, msg);
+            }
             continue;
         }
         ++steps_run;
         // table entries are in increasing slot index: walk them backwards so that
         // erasing a finished slot leaves the remaining indices valid
-        bool erased = false;
+        std::vector<Slot> done_now;
         for (int ti = (int)step_slots.size() - 1; ti >= 0; --ti) {
             const int i = step_slots[ti];
             Slot &sl = slots[i];
             ++sl.steps;
             if (!stat_host[ti].stop && sl.steps < sl.req->iters) continue;
-            cbct_status fs = finish_slot(sl);
-            const std::string msg = fs == CBCT_OK ? sl.req->error : std::string(cbct_last_error());
-            std::shared_ptr<Request> r = sl.req;
-            release_slot(sl);
+            done_now.push_back(sl);
             slots.erase(slots.begin() + i);
-            erased = true;
-            table_dirty = true;
-            std::lock_guard<std::mutex> lk(mu);
-            if (fs != CBCT_OK) r->status = fs;
-            r->error = msg;
-            r->done = true;
-            r->t_finish = now_s(t0);
-            in_use -= r->bytes;
-            cv_done.notify_all();
         }
-        if (erased) step_slots.clear();     // slot indices shifted: the next step re-picks
+        if (!done_now.empty()) {
+            step_slots.clear();              // slot indices shifted: the next step re-picks
+            table_dirty = true;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                in_flight -= (int)done_now.size();
+                active_slots = (int)slots.size();
+                for (Slot &sl : done_now) finishing.push_back(sl);
+            }
+            cv_finish.notify_one();
+            cv_admit.notify_one();           // a slot is free (its memory follows at read-out)
+        }
     }
-    for (Slot &sl : slots) release_slot(sl);
+    for (Slot &sl : slots) {
+        std::shared_ptr<Request> r = sl.req;
+        release_slot(sl, s, false);
+        complete(r, CBCT_EINVAL, "server destroyed before the request finished");
+    }
     slots.clear();
     cudaStreamSynchronize(s);
+}
+
+void ServerImpl::run_readout() {
+    cudaSetDevice(device);
+    for (;;) {
+        Slot sl;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_finish.wait(lk, [&] { return steps_stopped || !finishing.empty(); });
+            if (finishing.empty()) break;        // steps stopped and nothing left to read out
+            sl = finishing.front();
+            finishing.pop_front();
+        }
+        cbct_status fs = finish_slot(sl);
+        const std::string msg = fs == CBCT_OK ? std::string() : std::string(cbct_last_error());
+        std::shared_ptr<Request> r = sl.req;
+        release_slot(sl, s_read, true);
+        complete(r, fs, msg);
+    }
 }
 
 }  // namespace cbct
@@ -577,6 +701,16 @@ struct cbct_server {
     ServerImpl impl;
 };
 
+static void free_server_resources(ServerImpl &S) {
+    if (S.tab_host) cudaFreeHost(S.tab_host);
+    if (S.tab_dev) cudaFree(S.tab_dev);
+    if (S.stat_host) cudaFreeHost(S.stat_host);
+    if (S.stat_dev) cudaFree(S.stat_dev);
+    if (S.counters) cudaFree(S.counters);
+    for (cudaStream_t st : {S.s, S.s_admit, S.s_read})
+        if (st) cudaStreamDestroy(st);
+}
+
 extern "C" cbct_status cbct_server_create(const cbct_server_opts *o, cbct_server **out) {
     if (!o || !out) { set_error("cbct_server_create: null argument"); return CBCT_EINVAL; }
     *out = nullptr;
@@ -584,7 +718,8 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *o, cbct_server
         set_error("cbct_server_create: need hbm_budget_bytes > 0 and 1 <= max_slots <= 64");
         return CBCT_EINVAL;
     }
-    if (o->schedule != CBCT_SCHED_SRPT && o->schedule != CBCT_SCHED_SHARE && o->schedule != CBCT_SCHED_RATIO) {
+    if (o->schedule != CBCT_SCHED_SRPT && o->schedule != CBCT_SCHED_SHARE && o->schedule != CBCT_SCHED_RATIO &&
+        o->schedule != CBCT_SCHED_FIFO) {
         set_error("cbct_server_create: unknown schedule");
         return CBCT_EINVAL;
     }
@@ -602,17 +737,16 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *o, cbct_server
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, srv_forward, FWD_THREADS, 0);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, srv_backward, BWD_THREADS, 0);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.s_admit, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.s_read, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(&S.tab_host, sizeof(SlotTable));
     if (e == cudaSuccess) e = cudaMalloc(&S.tab_dev, sizeof(SlotTable));
     if (e == cudaSuccess) e = cudaMallocHost(&S.stat_host, sizeof(SlotStatus) * SRV_MAX_SLOTS);
     if (e == cudaSuccess) e = cudaMalloc(&S.stat_dev, sizeof(SlotStatus) * SRV_MAX_SLOTS);
+    if (e == cudaSuccess) e = cudaMalloc(&S.counters, 2 * sizeof(unsigned));
     if (e != cudaSuccess) {
         cbct_status st = cuda_fail(e, "cbct_server_create");
-        if (S.tab_host) cudaFreeHost(S.tab_host);
-        if (S.tab_dev) cudaFree(S.tab_dev);
-        if (S.stat_host) cudaFreeHost(S.stat_host);
-        if (S.stat_dev) cudaFree(S.stat_dev);
-        if (S.s) cudaStreamDestroy(S.s);
+        free_server_resources(S);
         delete srv;
         return st;
     }
@@ -621,14 +755,21 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *o, cbct_server
     S.bwd_grid = sms * std::max(occ_b, 1);
     S.vec_grid = sms * 4;
     try {
-        S.worker = std::thread([&S] { S.run(); });
+        S.reader = std::thread([&S] { S.run_readout(); });
+        S.worker = std::thread([&S] { S.run_steps(); });
+        S.admitter = std::thread([&S] { S.run_admission(); });
     } catch (...) {
-        set_error("cbct_server_create: cannot start the worker thread");
-        cudaFreeHost(S.tab_host);
-        cudaFree(S.tab_dev);
-        cudaFreeHost(S.stat_host);
-        cudaFree(S.stat_dev);
-        cudaStreamDestroy(S.s);
+        set_error("cbct_server_create: cannot start the server threads");
+        {
+            std::lock_guard<std::mutex> lk(S.mu);
+            S.stopping = S.steps_stopped = true;
+        }
+        S.cv_admit.notify_all();
+        S.cv_ready.notify_all();
+        S.cv_finish.notify_all();
+        for (std::thread *t : {&S.admitter, &S.worker, &S.reader})
+            if (t->joinable()) t->join();
+        free_server_resources(S);
         delete srv;
         return CBCT_ENOMEM;
     }
@@ -679,7 +820,7 @@ extern "C" cbct_status cbct_server_submit(cbct_server *srv, const cbct_geometry_
         S.pending.push_back(r);
         *id = r->id;
     }
-    S.cv_work.notify_one();
+    S.cv_admit.notify_one();
     return CBCT_OK;
 }
 
@@ -745,14 +886,26 @@ extern "C" void cbct_server_destroy(cbct_server *srv) {
         std::lock_guard<std::mutex> lk(S.mu);
         S.stopping = true;
     }
-    S.cv_work.notify_all();
+    S.cv_admit.notify_all();
+    S.cv_ready.notify_all();
+    if (S.admitter.joinable()) S.admitter.join();
     if (S.worker.joinable()) S.worker.join();
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.steps_stopped = true;
+    }
+    S.cv_finish.notify_all();
+    if (S.reader.joinable()) S.reader.join();
+    for (Slot &sl : S.ready) {                 // set up but never stepped
+        std::shared_ptr<Request> r = sl.req;
+        S.release_slot(sl, S.s_admit, false);
+        S.complete(r, CBCT_EINVAL, "server destroyed before the request finished");
+    }
+    S.ready.clear();
+    for (cbct_geometry *g : S.graveyard) cbct_geometry_destroy(g);
+    S.graveyard.clear();
     if (S.step_graph) cudaGraphExecDestroy(S.step_graph);
-    cudaStreamSynchronize(S.s);
-    cudaFreeHost(S.tab_host);
-    cudaFree(S.tab_dev);
-    cudaFreeHost(S.stat_host);
-    cudaFree(S.stat_dev);
-    cudaStreamDestroy(S.s);
+    for (cudaStream_t st : {S.s, S.s_admit, S.s_read}) cudaStreamSynchronize(st);
+    free_server_resources(S);
     delete srv;
 }

@@ -110,6 +110,15 @@ struct Workspace {
         *p = (T *)q;
         return e;
     }
+    // `count` volume-side vectors in the padded z-fastest layout, back to
+    // back, all zero (pads and guards included).
+    template <typename T>
+    cudaError_t alloc_volumes(T **p, const DevGeom &g, size_t count = 1) {
+        const size_t len = (size_t)zf_len(g) * count;
+        cudaError_t e = alloc(p, len);
+        if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, len * sizeof(T), s);
+        return e;
+    }
 };
 
 inline bool is_device_pointer(const void *p) {
@@ -218,7 +227,7 @@ cbct_status run_iterations(int iters, bool use_graph, cudaStream_t s, F &&enqueu
 struct SolveIO {
     const float *b_dev;   // b re-laid v-fastest, y[a][iu][iv], like the projection-side vectors
     float *x_dev;         // caller layout x[k][j][i] (device; staging buffer for host x)
-    float *xz;            // the iterate in the solvers' z-fastest layout x[j][i][k]
+    float *xz;            // the iterate in the solvers' padded z-fastest layout
     bool x_is_host;
     float *x_host;
 };
@@ -263,8 +272,7 @@ inline cbct_status setup_io(const cbct_geometry *g, const float *b, float *x, Wo
         io.x_is_host = true;
         io.x_host = x;
     }
-    CBCT_CUDA_TRY(ws.alloc(&io.xz, (size_t)m));
-    CBCT_CUDA_TRY(cudaMemsetAsync(io.xz, 0, sizeof(float) * m, ws.s));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&io.xz, g->dev));
     return CBCT_OK;
 }
 

@@ -216,6 +216,7 @@ struct Reorth {
         cap = o->iters + 1;
         CBCT_CUDA_TRY(ws.alloc(&Ub, (size_t)cap * n));
         CBCT_CUDA_TRY(ws.alloc(&Vb, (size_t)cap * m));
+        CBCT_CUDA_TRY(cudaMemsetAsync(Vb, 0, sizeof(float) * cap * m, ws.s));
         CBCT_CUDA_TRY(ws.alloc(&partial, (size_t)cap * VEC_BLOCKS));
         CBCT_CUDA_TRY(ws.alloc(&d, (size_t)cap));
         return CBCT_OK;
@@ -371,7 +372,8 @@ template <typename T>
 static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
                             cbct_solve_report *rep, cudaStream_t s, Method method, bool lsmr_proj) {
     const DevGeom &g = geom->dev;
-    const int64_t n = cbct_geometry_num_rays(geom), m = cbct_geometry_num_voxels(geom);
+    // m: length of a volume-side vector (padded z-fastest layout); mvox: voxels
+    const int64_t n = cbct_geometry_num_rays(geom), m = zf_len(geom->dev), mvox = cbct_geometry_num_voxels(geom);
     const int iters = o->iters;
     const int nf = forward_num_blocks(g), nb = backward_num_blocks(g);
     Workspace ws(s);
@@ -387,7 +389,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     CBCT_CUDA_TRY(ws.alloc(&U, (size_t)n));
     CBCT_CUDA_TRY(ws.alloc(&W, (size_t)n));          // |d'| U, the transpose's input
     if (method == M_HYBRID) {
-        CBCT_CUDA_TRY(ws.alloc(&basis, (size_t)m * (iters + 1)));
+        CBCT_CUDA_TRY(ws.alloc_volumes(&basis, g, (size_t)iters + 1));
         CBCT_CUDA_TRY(ws.alloc(&alpha_arr, (size_t)iters + 2));
         CBCT_CUDA_TRY(ws.alloc(&beta_arr, (size_t)iters + 2));
         CBCT_CUDA_TRY(ws.alloc(&scale_arr, (size_t)iters + 2));
@@ -395,9 +397,9 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
         CBCT_CUDA_TRY(ws.alloc(&work, (size_t)(iters + 1) * iters * 2 + 4 * (iters + 1)));
         V = basis;
     } else {
-        CBCT_CUDA_TRY(ws.alloc(&V, (size_t)m));
-        CBCT_CUDA_TRY(ws.alloc(&w, (size_t)m));
-        if (method == M_LSMR) CBCT_CUDA_TRY(ws.alloc(&h2, (size_t)m));
+        CBCT_CUDA_TRY(ws.alloc_volumes(&V, g));
+        CBCT_CUDA_TRY(ws.alloc_volumes(&w, g));
+        if (method == M_LSMR) CBCT_CUDA_TRY(ws.alloc_volumes(&h2, g));
     }
     CBCT_CUDA_TRY(ws.alloc(&pf, (size_t)nf));
     CBCT_CUDA_TRY(ws.alloc(&pb, (size_t)nb));
@@ -405,7 +407,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     CBCT_CUDA_TRY(ws.alloc(&hist, (size_t)3 * iters));
     CBCT_CUDA_TRY(ws.alloc(&dst, 1));
     float *accum = nullptr;         // running sums of a transpose summed in passes
-    if (g.angle_block < g.nangles) CBCT_CUDA_TRY(ws.alloc(&accum, (size_t)m));
+    if (g.angle_block < g.nangles) CBCT_CUDA_TRY(ws.alloc(&accum, (size_t)mvox));
     const int bwd_passes = backward_passes(g, accum);
     CBCT_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * 3 * iters, s));
 
@@ -416,7 +418,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     std::memset(&init, 0, sizeof init);
     init.damp = method == M_HYBRID ? 0.0 : o->lambda;
     init.sqrt_n = std::sqrt((double)n);
-    init.sqrt_m = std::sqrt((double)m);
+    init.sqrt_m = std::sqrt((double)mvox);
     init.scaled = std::is_same<T, __half>::value ? 1 : 0;
     CBCT_CUDA_TRY(cudaMemcpyAsync(dst, &init, sizeof init, cudaMemcpyHostToDevice, s));
     const cbct_dtype t = o->storage;
@@ -601,7 +603,8 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
 static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
                               cbct_solve_report *rep, cudaStream_t s) {
     const DevGeom &g = geom->dev;
-    const int64_t n = cbct_geometry_num_rays(geom), m = cbct_geometry_num_voxels(geom);
+    // m: length of a volume-side vector (padded z-fastest layout); mvox: voxels
+    const int64_t n = cbct_geometry_num_rays(geom), m = zf_len(geom->dev), mvox = cbct_geometry_num_voxels(geom);
     const int iters = o->iters;
     const int nf = forward_num_blocks(g);
     Workspace ws(s);
@@ -614,8 +617,8 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     CBCT_CUDA_TRY(ws.alloc(&r, (size_t)n));
     CBCT_CUDA_TRY(ws.alloc(&q, (size_t)n));
     CBCT_CUDA_TRY(ws.alloc(&wr, (size_t)n));
-    CBCT_CUDA_TRY(ws.alloc(&sv, (size_t)m));
-    CBCT_CUDA_TRY(ws.alloc(&p, (size_t)m));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&sv, g));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&p, g));
     CBCT_CUDA_TRY(ws.alloc(&pq, (size_t)nf));
     CBCT_CUDA_TRY(ws.alloc(&pp, (size_t)VEC_BLOCKS));
     CBCT_CUDA_TRY(ws.alloc(&pr, (size_t)VEC_BLOCKS));
@@ -624,7 +627,7 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     CBCT_CUDA_TRY(ws.alloc(&dst, 1));
     CBCT_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * 3 * iters, s));
     float *accum = nullptr;         // running sums of a transpose summed in passes
-    if (g.angle_block < g.nangles) CBCT_CUDA_TRY(ws.alloc(&accum, (size_t)m));
+    if (g.angle_block < g.nangles) CBCT_CUDA_TRY(ws.alloc(&accum, (size_t)mvox));
     const int bwd_passes = backward_passes(g, accum);
     Tracker tr;
     tr.profile = o->profile != 0;

@@ -22,23 +22,33 @@ struct TvState {
 
 constexpr double TV_CONVERGED = 1e-14;     // inner CGLS stops once ||s|| <= this x its start
 
+// Voxel coordinates of the padded z-fastest layout (index v =
+// ZF_GUARD + (j nx + i) (nz + 2) + 1 + k); pads and guards have none.
 struct VolIndex {
     int nx, ny, nz;
-    __device__ __forceinline__ void coords(int64_t v, int &i, int &j, int &k) const {
-        k = (int)(v % nz);
-        const int64_t c = v / nz;
-        i = (int)(c % nx);
-        j = (int)(c / nx);
+    __device__ __forceinline__ int64_t len() const { return (int64_t)nx * ny * (nz + 2) + 2 * ZF_GUARD; }
+    __device__ __forceinline__ int64_t oi() const { return nz + 2; }
+    __device__ __forceinline__ int64_t oj() const { return (int64_t)nx * (nz + 2); }
+    __device__ __forceinline__ bool coords(int64_t v, int &i, int &j, int &k) const {
+        const int64_t c = v - ZF_GUARD;
+        if (c < 0) return false;
+        const int64_t col = c / (nz + 2);
+        if (col >= (int64_t)nx * ny) return false;
+        k = (int)(c - col * (nz + 2)) - 1;
+        if (k < 0 || k >= nz) return false;
+        i = (int)(col % nx);
+        j = (int)(col / nx);
+        return true;
     }
 };
 
 // w = (|D x|^2 + tau^2)^(-1/4)
 __global__ void __launch_bounds__(VEC_THREADS)
 k_tv_weights(const float *__restrict__ x, float *__restrict__ w, VolIndex vi, float tau) {
-    const int64_t m = (int64_t)vi.nx * vi.ny * vi.nz, oi = vi.nz, oj = (int64_t)vi.nx * vi.nz;
+    const int64_t m = vi.len(), oi = vi.oi(), oj = vi.oj();
     for (int64_t v = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; v < m; v += (int64_t)VEC_BLOCKS * VEC_THREADS) {
         int i, j, k;
-        vi.coords(v, i, j, k);
+        if (!vi.coords(v, i, j, k)) continue;
         const float xv = x[v];
         const float di = i < vi.nx - 1 ? x[v + oi] - xv : 0.0f;
         const float dj = j < vi.ny - 1 ? x[v + oj] - xv : 0.0f;
@@ -53,11 +63,11 @@ k_grad_w(const float *__restrict__ x, const float *__restrict__ w, float *__rest
          double *partial, const int *stop) {
     __shared__ double red[VEC_THREADS / 32];
     if (stop && *stop) return;
-    const int64_t m = (int64_t)vi.nx * vi.ny * vi.nz, oi = vi.nz, oj = (int64_t)vi.nx * vi.nz;
+    const int64_t m = vi.len(), oi = vi.oi(), oj = vi.oj();
     double ss = 0.0;
     for (int64_t v = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; v < m; v += (int64_t)VEC_BLOCKS * VEC_THREADS) {
         int i, j, k;
-        vi.coords(v, i, j, k);
+        if (!vi.coords(v, i, j, k)) continue;
         const float xv = x[v];
         const float cw = (float)(c * (double)w[v]);
         const float gi = cw * (i < vi.nx - 1 ? x[v + oi] - xv : 0.0f);
@@ -80,11 +90,11 @@ k_div_w_add(const float *__restrict__ rd, const float *__restrict__ w, float *__
             double *partial, const int *stop) {
     __shared__ double red[VEC_THREADS / 32];
     if (stop && *stop) return;
-    const int64_t m = (int64_t)vi.nx * vi.ny * vi.nz, oi = vi.nz, oj = (int64_t)vi.nx * vi.nz;
+    const int64_t m = vi.len(), oi = vi.oi(), oj = vi.oj();
     double ss = 0.0;
     for (int64_t v = (int64_t)blockIdx.x * VEC_THREADS + threadIdx.x; v < m; v += (int64_t)VEC_BLOCKS * VEC_THREADS) {
         int i, j, k;
-        vi.coords(v, i, j, k);
+        if (!vi.coords(v, i, j, k)) continue;
         // (D_c^T u)[v] = u[v - o_c] (if the previous voxel's difference exists) - u[v] (if v's exists)
         const float wv = w[v];
         double t = 0.0;
@@ -182,7 +192,8 @@ __global__ void k_tv_reset(TvState *st) {
 static cbct_status cgls_tv_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
                                  cbct_solve_report *rep, cudaStream_t s) {
     const DevGeom &g = geom->dev;
-    const int64_t n = cbct_geometry_num_rays(geom), m = cbct_geometry_num_voxels(geom);
+    // m: length of a volume-side vector (padded z-fastest layout, pads kept at zero)
+    const int64_t n = cbct_geometry_num_rays(geom), m = zf_len(geom->dev);
     const int iters = o->iters, outer = o->tv_outer;
     const double lam = o->lambda;
     const VolIndex vi{g.nx, g.ny, g.nz};
@@ -195,14 +206,14 @@ static cbct_status cgls_tv_solve(const cbct_geometry *geom, const float *b, floa
           *wa = nullptr;
     double *pf = nullptr, *pd = nullptr, *ps = nullptr, *pr = nullptr, *hist = nullptr;
     TvState *dst = nullptr;
-    CBCT_CUDA_TRY(ws.alloc(&w, (size_t)m));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&w, g));
     CBCT_CUDA_TRY(ws.alloc(&ra, (size_t)n));
     CBCT_CUDA_TRY(ws.alloc(&qa, (size_t)n));
     CBCT_CUDA_TRY(ws.alloc(&wa, (size_t)n));
-    CBCT_CUDA_TRY(ws.alloc(&rd, (size_t)3 * m));
-    CBCT_CUDA_TRY(ws.alloc(&qd, (size_t)3 * m));
-    CBCT_CUDA_TRY(ws.alloc(&p, (size_t)m));
-    CBCT_CUDA_TRY(ws.alloc(&sv, (size_t)m));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&rd, g, 3));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&qd, g, 3));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&p, g));
+    CBCT_CUDA_TRY(ws.alloc_volumes(&sv, g));
     CBCT_CUDA_TRY(ws.alloc(&pf, (size_t)nf));
     CBCT_CUDA_TRY(ws.alloc(&pd, (size_t)VEC_BLOCKS));
     CBCT_CUDA_TRY(ws.alloc(&ps, (size_t)VEC_BLOCKS));

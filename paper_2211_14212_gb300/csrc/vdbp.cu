@@ -72,7 +72,7 @@ voxel_backproject_kernel(DevGeom g, const float *__restrict__ proj, float *__res
     for (int kk = 0; kk < VD_K; ++kk) {
         const int k = k0 + kk * 32 + lane;
         if (k >= g.nz) continue;
-        const size_t vi = ZFAST ? ((size_t)j * g.nx + i) * g.nz + k : ((size_t)k * g.ny + j) * g.nx + i;
+        const size_t vi = ZFAST ? (size_t)(zf_col(g, i, j) + k) : ((size_t)k * g.ny + j) * g.nx + i;
         vol[vi] = acc[kk];
     }
 }

@@ -88,7 +88,7 @@ def test_server_argument_checks(lib):
     from paper_2211_14212_gb300 import cbct
     h = ctypes.c_void_p()
     assert lib.cbct_server_create(None, ctypes.byref(h)) == cbct.CBCT_EINVAL
-    for budget, slots, sched in ((0, 4, 0), (1 << 30, 0, 0), (1 << 30, 65, 0), (1 << 30, 4, 3), (1 << 30, 4, -1)):
+    for budget, slots, sched in ((0, 4, 0), (1 << 30, 0, 0), (1 << 30, 65, 0), (1 << 30, 4, 4), (1 << 30, 4, -1)):
         o = cbct._ServerOpts(budget, slots, 1, sched)
         assert lib.cbct_server_create(ctypes.byref(o), ctypes.byref(h)) == cbct.CBCT_EINVAL
     rid = ctypes.c_uint64()

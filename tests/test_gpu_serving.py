@@ -127,11 +127,12 @@ def test_many_requests_continuous(cbct):
     assert st["bytes_in_use"] == 0 and st["active"] == 0 and st["pending"] == 0
 
 
-@pytest.mark.parametrize("schedule", ["srpt", "ratio", "share"])
+@pytest.mark.parametrize("schedule", ["fifo", "srpt", "ratio", "share"])
 def test_schedule(cbct, schedule):
     """A large request (more forward tiles than one step needs to fill the GPU)
-    and a short one submitted right after it: SRPT runs the short one alone,
-    so the steps add up; SHARE advances both in the same steps."""
+    and a short one submitted right after it: FIFO runs the large one to the
+    end first and SRPT the short one, each alone, so the steps add up; SHARE
+    advances both in the same steps."""
     big = synth.Geometry(128, 128, 128, 2.0, 2.0, 2.0, 256, 256, 1.6, 1.6, 1000.0, 1536.0,
                          synth.circular_angles(180))
     small = synth.config("c1")
@@ -147,9 +148,35 @@ def test_schedule(cbct, schedule):
     if schedule == "srpt":
         assert st["steps"] == 34
         assert r_small.finish_s <= r_big.finish_s
+    elif schedule == "fifo":
+        assert st["steps"] == 34
+        assert r_small.finish_s >= r_big.finish_s
     elif schedule == "share":
         assert st["steps"] < 34
     else:                       # the young short request has the higher response ratio
         assert r_small.finish_s <= r_big.finish_s
     alone, _ = cbct.lsqr(cbct.Geometry(small), b_small, 4)
     assert rel(r_small.x, alone) <= MIX_TOL
+
+
+def test_srpt_does_not_starve_a_long_request(cbct):
+    """SRPT with a sustained stream of short requests behind a long one: the
+    long request (more forward tiles than a step takes) is passed over while
+    shorter work is available, but after 64 consecutive steps without it it
+    goes first, so it finishes well before the stream ends."""
+    big = synth.Geometry(128, 128, 128, 2.0, 2.0, 2.0, 256, 256, 1.6, 1.6, 1000.0, 1536.0,
+                         synth.circular_angles(180))
+    small = synth.config("c1")
+    rng = np.random.default_rng(6)
+    b_big = np.abs(rng.standard_normal(big.num_rays)).astype(np.float32)
+    b_small = np.abs(rng.standard_normal(small.num_rays)).astype(np.float32)
+    with cbct.Server(16 << 30, max_slots=16, schedule="srpt") as srv:
+        i_big = srv.submit(big, b_big, "lsqr", 30)
+        ids = [srv.submit(small, b_small, "lsqr", 10) for _ in range(100)]
+        r_big = srv.wait(i_big, timeout=600)
+        smalls = [srv.wait(i, timeout=600) for i in ids]
+    assert r_big.report.iters_done == 30
+    last_small = max(r.finish_s for r in smalls)
+    assert r_big.finish_s < last_small
+    # and the short ones did go first while it waited
+    assert sum(r.finish_s < r_big.finish_s for r in smalls) >= 10
