@@ -93,3 +93,24 @@ def test_precision_reference_values():
     sub = np.asarray(ref["voxels"][::40])
     y = synth.random_projections(g, ref["y_seed"]).astype(np.float32).astype(np.float64)
     np.testing.assert_allclose(oracle.backproject_voxels(g, y, sub), ref["backproject_voxels"][::40], rtol=RTOL)
+
+
+def test_c2_anchor_first_iterate_is_along_the_backprojected_data():
+    """The stored 256^3 anchor (tests/golden/make_golden_c2_solvers.py) against
+    a property of its first iterates: LSQR's and LSMR's x_1 are multiples of
+    A^T b (Sec. 2.1.2-2.1.3: x_1 lies in span{A^T b}).  A^T b is recomputed at
+    60 of the stored voxels by the oracle's voxel-by-voxel route, independent
+    of the scatter the stored run used."""
+    path = os.path.join(os.path.dirname(GOLDEN), "c2_solver_anchor.json")
+    with open(path) as f:
+        anchor = json.load(f)
+    g = synth.config(anchor["geometry"])
+    b = synth.random_projections(g, anchor["b"]["seed"]).astype(np.float32).astype(np.float64)
+    pick = np.arange(0, len(anchor["voxels"]), len(anchor["voxels"]) // 60)[:60]
+    vox = np.asarray(anchor["voxels"])[pick]
+    atb = oracle.backproject_voxels(g, b, vox)
+    for method in ("lsqr", "lsmr"):
+        x1 = np.asarray(anchor[method]["iterates"][0])[pick]
+        ratio = x1 / atb
+        np.testing.assert_allclose(ratio, ratio[0], rtol=1e-9)
+        assert ratio[0] > 0
