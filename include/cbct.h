@@ -153,6 +153,9 @@ cbct_status cbct_geometry_set_launch(cbct_geometry *geom, int fwd_rows, int bwd_
 cbct_status cbct_geometry_get_launch(const cbct_geometry *geom, int *fwd_rows, int *bwd_config);
 /* Times every launch shape (forward and transpose, FP32, on a strided subset
  * of at most max_angles angles; max_angles <= 0 = all) and keeps the fastest.
+ * The subset is widened to at least twice the device's L2 size worth of
+ * projections (or all angles), so that the transpose is timed reading its
+ * projections from HBM as in a full-size product, not from L2.
  * times_ms, if non-null, is a host array of CBCT_TUNE_TIMES doubles that
  * receives the forward times for fwd_rows 1, 2, 4 and the transpose times for
  * bwd_config 0..9.  Allocates scratch on `stream` and synchronises it. */

@@ -83,7 +83,14 @@ extern "C" cbct_status cbct_geometry_autotune(cbct_geometry *g, int max_angles, 
     if (dst != CBCT_OK) return dst;
     cudaStream_t s = (cudaStream_t)stream;
     const int na = g->desc.nangles;
-    const int keep = max_angles > 0 && max_angles < na ? max_angles : na;
+    int keep = max_angles > 0 && max_angles < na ? max_angles : na;
+    // A stack that fits in L2 would time the transpose's gathers from L2:
+    // keep at least twice L2's worth of projections.
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess) {
+        const size_t per_angle = (size_t)g->desc.nu * g->desc.nv * sizeof(float);
+        keep = (int)std::max<size_t>(keep, std::min<size_t>(na, (2 * (size_t)l2 + per_angle - 1) / per_angle));
+    }
     std::vector<double> sub((size_t)keep);
     for (int i = 0; i < keep; ++i) sub[i] = g->desc.angles_rad[(size_t)i * na / keep];
     cbct_geometry_desc d = g->desc;

@@ -121,8 +121,9 @@ inline size_t dtype_size(cbct_dtype t) { return t == CBCT_F32 ? 4 : 2; }
 // analogue).  a and b are FP64 values read from device memory (written by the
 // previous solver kernel) or given directly; a null pointer means the
 // immediate value.  out_old is read from `old` when set (an input buffer
-// distinct from the output), else from the output buffer itself.  `partial`, when non-null, receives one FP64 sum of
-// squares of the stored outputs per thread block, reduced later in a fixed
+// distinct from the output), else from the output buffer itself.  `partial`,
+// when non-null, receives FP64 sums of squares of the stored outputs
+// (TILE_PARTIALS per projector tile, one per warp), reduced later in a fixed
 // order (deterministic norms).
 struct Epilogue {
     const double *a_ptr;
@@ -137,6 +138,17 @@ struct Epilogue {
 
 __device__ __forceinline__ double epi_a(const Epilogue &e) { return e.a_ptr ? *e.a_ptr : e.a_val; }
 __device__ __forceinline__ double epi_b(const Epilogue &e) { return e.b_ptr ? *e.b_ptr : e.b_val; }
+
+// Projector tiles leave one FP64 norm partial per warp (8 per 256-thread
+// tile), written without a block barrier; later kernels sum them in a fixed
+// order.
+constexpr int TILE_PARTIALS = 8;
+
+// Sum of one double per lane of a warp, written by lane 0 to dst[warp].
+__device__ __forceinline__ void warp_partial(double v, double *dst) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) dst[threadIdx.x >> 5] = v;
+}
 
 // Deterministic block reduction of one double per thread into thread 0.
 template <int NT>
@@ -187,6 +199,12 @@ cbct_status launch_forward(const DevGeom &g, const void *x_zfast, void *y, cbct_
 // over blocks of DevGeom::angle_block angles; null means one pass.
 cbct_status launch_backward(const DevGeom &g, const float *w_vfast, void *x, cbct_dtype t,
                             const Epilogue &epi, cudaStream_t s, bool zfast, float *accum);
+// One transpose launch over angles [a0, a1) (acc_in / acc_out as in
+// backward_tile), output in the padded z-fastest or the ABI volume layout.
+void launch_backward_zfast(const DevGeom &g, const float *w_vfast, void *x, cbct_dtype t, const Epilogue &epi,
+                           cudaStream_t s, int a0, int a1, const float *acc_in, float *acc_out);
+void launch_backward_abi(const DevGeom &g, const float *w_vfast, void *x, cbct_dtype t, const Epilogue &epi,
+                         cudaStream_t s, int a0, int a1, const float *acc_in, float *acc_out);
 // w[a][iu][iv] = |d'| * y for a v-fastest projection vector y[a][iu][iv] of type t.
 cbct_status launch_weight(const DevGeom &g, const void *y_vfast, cbct_dtype t, float *w, cudaStream_t s);
 // w[a][iu][iv] = |d'| * y for y in the ABI layout y[a][iv][iu].
@@ -209,6 +227,9 @@ cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaSt
 cbct_status launch_voxel_backproject(const DevGeom &g, const float *y_vfast, float *x, bool zfast, cudaStream_t s);
 int forward_num_blocks(const DevGeom &g);
 int backward_num_blocks(const DevGeom &g);
+// FP64 norm partials one launch leaves (TILE_PARTIALS per tile)
+inline int forward_num_partials(const DevGeom &g) { return forward_num_blocks(g) * TILE_PARTIALS; }
+inline int backward_num_partials(const DevGeom &g) { return backward_num_blocks(g) * TILE_PARTIALS; }
 dim3 forward_grid(const DevGeom &g);
 dim3 backward_grid(const DevGeom &g);
 BrickShape backward_shape(int config);

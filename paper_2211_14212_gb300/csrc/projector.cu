@@ -23,9 +23,11 @@ __global__ void __launch_bounds__(FWD_THREADS, R >= 4 ? 3 : 4)
 forward_kernel(DevGeom g, const T *__restrict__ vol, T *__restrict__ proj, Epilogue epi) {
     __shared__ double red[FWD_THREADS / 32];
     if (epi.stop && *epi.stop) return;
-    const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    forward_tile<T, COMP, R, VF>(g, vol, proj, epi, blockIdx.x, blockIdx.y, blockIdx.z,
-                                 epi.partial ? epi.partial + b : nullptr, red);
+    auto partial_at = [&]() -> double * {
+        const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        return epi.partial ? epi.partial + b * TILE_PARTIALS : nullptr;
+    };
+    forward_tile<T, COMP, R, VF>(g, vol, proj, epi, blockIdx.x, blockIdx.y, blockIdx.z, partial_at, red);
 }
 
 template <int R>
@@ -107,17 +109,6 @@ cbct_status launch_count(const DevGeom &g, unsigned long long *count_dev, cudaSt
 
 // ---------------------------------------------------------- transpose A^T y
 
-template <typename T, bool ZFAST, int CX, int K, bool HOIST>
-__global__ void __launch_bounds__(BWD_THREADS, (K >= 8 || (HOIST && K >= 4)) ? 3 : 4)
-backward_kernel(DevGeom g, const float *__restrict__ proj, T *__restrict__ vol, Epilogue epi, int a_begin, int a_end,
-                const float *acc_in, float *acc_out) {
-    __shared__ double red[BWD_THREADS / 32];
-    if (epi.stop && *epi.stop) return;
-    const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    backward_tile<T, ZFAST, CX, K, HOIST>(g, proj, vol, epi, blockIdx.x, blockIdx.y, blockIdx.z, a_begin, a_end, acc_in,
-                                   acc_out, epi.partial ? epi.partial + b : nullptr, red);
-}
-
 // Transpose tile shapes: column patch CX x (8 / CX), 32 K voxels along z;
 // configurations 0..3 and 8, 9 keep the slab intervals of their candidate
 // rows in registers per angle (8, 9: 4 voxels per lane, 3 CTAs per SM).
@@ -146,36 +137,6 @@ int backward_num_blocks(const DevGeom &g) {
     return (int)(gr.x * gr.y * gr.z);
 }
 
-template <typename T, bool ZF>
-static void launch_backward_t(const DevGeom &g, const float *y, void *x, const Epilogue &epi, cudaStream_t s,
-                              int a0, int a1, const float *acc_in, float *acc_out) {
-    const dim3 grid = backward_grid(g);
-    const float *yy = y;
-    T *xx = (T *)x;
-    switch (g.bwd_config) {
-    case 1: backward_kernel<T, ZF, 4, 2, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 2: backward_kernel<T, ZF, 8, 1, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 3: backward_kernel<T, ZF, 2, 2, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 4: backward_kernel<T, ZF, 4, 4, false><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 5: backward_kernel<T, ZF, 2, 4, false><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 6: backward_kernel<T, ZF, 4, 8, false><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 7: backward_kernel<T, ZF, 2, 8, false><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 8: backward_kernel<T, ZF, 2, 4, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    case 9: backward_kernel<T, ZF, 4, 4, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    default: backward_kernel<T, ZF, 4, 1, true><<<grid, BWD_THREADS, 0, s>>>(g, yy, xx, epi, a0, a1, acc_in, acc_out); break;
-    }
-}
-
-template <bool ZF>
-static void launch_backward_z(const DevGeom &g, const float *y, void *x, cbct_dtype t, const Epilogue &epi,
-                              cudaStream_t s, int a0, int a1, const float *acc_in, float *acc_out) {
-    switch (t) {
-    case CBCT_F32: launch_backward_t<float, ZF>(g, y, x, epi, s, a0, a1, acc_in, acc_out); break;
-    case CBCT_F16: launch_backward_t<__half, ZF>(g, y, x, epi, s, a0, a1, acc_in, acc_out); break;
-    case CBCT_BF16: launch_backward_t<__nv_bfloat16, ZF>(g, y, x, epi, s, a0, a1, acc_in, acc_out); break;
-    }
-}
-
 int backward_passes(const DevGeom &g, const float *accum) {
     if (!accum || g.angle_block <= 0 || g.angle_block >= g.nangles) return 1;
     return (g.nangles + g.angle_block - 1) / g.angle_block;
@@ -193,9 +154,9 @@ cbct_status launch_backward(const DevGeom &g, const float *y, void *x, cbct_dtyp
         const float *acc_in = p > 0 ? accum : nullptr;
         float *acc_out = p + 1 < passes ? accum : nullptr;
         if (zfast)
-            launch_backward_z<true>(g, y, x, t, epi, s, a0, a1, acc_in, acc_out);
+            launch_backward_zfast(g, y, x, t, epi, s, a0, a1, acc_in, acc_out);
         else
-            launch_backward_z<false>(g, y, x, t, epi, s, a0, a1, acc_in, acc_out);
+            launch_backward_abi(g, y, x, t, epi, s, a0, a1, acc_in, acc_out);
     }
     CBCT_CUDA_TRY(cudaGetLastError());
     return CBCT_OK;

@@ -395,13 +395,17 @@ __device__ __forceinline__ void trace_rays_zsingle(const DevGeom &g, const T *__
 // One tile = 8 warps = 8 adjacent detector columns (iu) x 32 R detector rows
 // (iv) of one angle.  The volume is read in the padded z-fastest layout.
 // Epilogue: proj = a * (A vol) + b * old (either projection layout), and one
-// FP64 sum of squares of the stored values into *partial (when non-null).
+// FP64 sums of squares of the stored values, one per warp, into
+// partial_at()[warp] (when it returns non-null).  partial_at is called only in
+// the epilogue, so that the address it computes is not held in a register
+// through the traversal, and the sums need no block barrier (measured 6 %
+// of the transpose's time with one).
 
 constexpr int FWD_COLS = 8, FWD_THREADS = 32 * FWD_COLS;
 
-template <typename T, bool COMP, int R, bool VFAST>
+template <typename T, bool COMP, int R, bool VFAST, typename PartialAt>
 __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restrict__ vol, T *__restrict__ proj,
-                                             const Epilogue &epi, int tx, int ty, int a, double *partial,
+                                             const Epilogue &epi, int tx, int ty, int a, PartialAt &&partial_at,
                                              double *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int iu = tx * FWD_COLS + warp;
@@ -457,10 +461,8 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
             sq += (double)stored * (double)stored;
         }
     }
-    if (partial) {
-        const double s = block_sum<FWD_THREADS>(sq, red);
-        if (threadIdx.x == 0) *partial = s;
-    }
+    double *partial = partial_at();
+    if (partial) warp_partial(sq, partial);
 }
 
 // ---------------------------------------------------------- transpose A^T y
@@ -491,16 +493,21 @@ constexpr int BWD_SHORT_ROWS = 3;
 // do not fit in L2 is summed in passes over blocks of angles (launch_backward):
 // `acc_in` (if not null) holds the FP32 sums of the earlier passes and
 // `acc_out` (if not null) receives the running sums instead of the volume, so
-// only the last pass applies the epilogue.  Both are indexed
+// only the last pass applies the epilogue (with the FP64 sums of squares of
+// the stored values into partial_at()[warp], when non-null, as in the
+// forward tile).  Both are indexed
 // ((j * nx + i) * nz + k) (unpadded); they may be the same buffer (each lane
 // reads and writes only its own voxels).  ZFAST output goes to the padded
 // z-fastest layout, else to the ABI layout x[k][j][i].
-template <typename T, bool ZFAST, int CX, int K, bool HOIST>
+template <typename T, bool ZFAST, int CX, int K, bool HOIST, typename PartialAt>
 __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__restrict__ wproj, T *__restrict__ vol,
                                               const Epilogue &epi, int tx, int ty, int tz, int a_begin, int a_end,
-                                              const float *acc_in, float *acc_out, double *partial,
+                                              const float *acc_in, float *acc_out, PartialAt &&partial_at,
                                               double *red) {
     constexpr int CY = 8 / CX;
+    // detector columns per unrolled step of the column loops: as many as fit
+    // in registers next to the voxels' sums
+    constexpr int BWD_IU_UNROLL = !HOIST ? 1 : K == 1 ? 2 : K == 2 ? 4 : 2;
     // HOIST: the slab intervals of the candidate rows are loaded once per
     // angle and kept in registers (3 x 2 per voxel of the lane); otherwise
     // they are loaded for every detector column.
@@ -514,7 +521,121 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
         const int k = k0 + kk * 32 + lane;
         acc[kk] = acc_in && col_ok && k < g.nz ? acc_in[((size_t)j * g.nx + i) * g.nz + k] : 0.0f;
     }
-    if (col_ok) {
+    if (col_ok && HOIST) {
+        // The three candidate rows of each voxel start at its window's first
+        // row moved down to fit the detector, and their slab intervals are
+        // loaded once per angle (a row outside the window meets the voxel
+        // nowhere and adds an exact zero).  The detector windows only select
+        // candidates (every length is then computed exactly from the crossing
+        // tables), so they use fast approximate divisions: their relative
+        // error (~1e-6) stays far below the 0.05-pixel margins.
+        const float inv_dv = 1.0f / g.dv, inv_du = 1.0f / g.du;
+        const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
+        float zlo[K], zhi[K];
+        int zboff[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int k = k0 + kk * 32 + lane;
+            zlo[kk] = (g.bz0 + k * g.dz) * inv_dv;
+            zhi[kk] = (g.bz0 + (k + 1) * g.dz) * inv_dv;
+            zboff[kk] = min(k, g.nz - 1) * g.nv;
+        }
+        const float x0 = g.bx0 + i * g.dx, x1 = x0 + g.dx;
+        const float y0 = g.by0 + j * g.dy, y1 = y0 + g.dy;
+        const size_t nuv = (size_t)g.nu * g.nv;
+        const int rmax = g.nv - BWD_SHORT_ROWS;
+        for (int a = a_begin; a < a_end; ++a) {
+            const float2 cs = __ldg(&g.trig[a]);
+            float umin = FLT_MAX, umax = -FLT_MAX, magmin = FLT_MAX, magmax = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float px = (c & 1) ? x1 : x0, py = (c & 2) ? y1 : y0;
+                const float along = g.dso - (px * cs.x + py * cs.y);   // > 0: source outside
+                const float mag = __fdividef(g.dsd, along);
+                const float u = (-px * cs.y + py * cs.x) * mag;
+                umin = fminf(umin, u);
+                umax = fmaxf(umax, u);
+                magmin = fminf(magmin, mag);
+                magmax = fmaxf(magmax, mag);
+            }
+            const int iu0 = max(0, (int)ceilf(__fmaf_rn(umin, inv_du, cu - 0.05f)));
+            const int iu1 = min(g.nu - 1, (int)floorf(__fmaf_rn(umax, inv_du, cu + 0.05f)));
+            int r0[K];
+            bool short_rows = true;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int k = k0 + kk * 32 + lane;
+                const float vmin = fminf(zlo[kk] * magmin, zlo[kk] * magmax);
+                const float vmax = fmaxf(zhi[kk] * magmin, zhi[kk] * magmax);
+                const int lo = max(0, (int)ceilf(vmin + (cv - 0.05f)));
+                const int hi = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
+                short_rows = short_rows && hi - lo < BWD_SHORT_ROWS;
+                r0[kk] = min(lo, rmax);
+            }
+            short_rows = __all_sync(0xffffffffu, short_rows) && rmax >= 0;
+            const float *pa = wproj + (size_t)a * nuv;
+            if (short_rows) {
+                float2 zb[K][BWD_SHORT_ROWS];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+                    for (int t = 0; t < BWD_SHORT_ROWS; ++t) zb[kk][t] = __ldg(&g.zbox[zboff[kk] + r0[kk] + t]);
+                // unrolled: the next columns' table and projection loads are
+                // issued before this column's sums (measured 7 % faster than
+                // the compiler's choice, which kept the loop rolled)
+#pragma unroll BWD_IU_UNROLL
+                for (int iu = iu0; iu <= iu1; ++iu) {
+                    const float4 xy = __ldg(&g.ray_xy[(size_t)a * g.nu + iu]);
+                    const float2 q = __ldg(&g.ray_xyq[(size_t)a * g.nu + iu]);
+                    float ain = -FLT_MAX, aout = FLT_MAX;
+                    bool miss = false;
+                    clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
+                    clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
+                    if (miss || !(ain < aout)) continue;
+                    const float *wcol = pa + (size_t)iu * g.nv;
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) {
+                        const float *wr = wcol + r0[kk];
+#pragma unroll
+                        for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
+                            const float2 e = zb[kk][t];
+                            const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
+                            acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wr + t), acc[kk]);
+                        }
+                    }
+                }
+            } else {
+                int rlo[K], rhi[K];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const int k = k0 + kk * 32 + lane;
+                    const float vmin = fminf(zlo[kk] * magmin, zlo[kk] * magmax);
+                    const float vmax = fmaxf(zhi[kk] * magmin, zhi[kk] * magmax);
+                    rlo[kk] = max(0, (int)ceilf(vmin + (cv - 0.05f)));
+                    rhi[kk] = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
+                }
+                for (int iu = iu0; iu <= iu1; ++iu) {
+                    const float4 xy = __ldg(&g.ray_xy[(size_t)a * g.nu + iu]);
+                    const float2 q = __ldg(&g.ray_xyq[(size_t)a * g.nu + iu]);
+                    float ain = -FLT_MAX, aout = FLT_MAX;
+                    bool miss = false;
+                    clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
+                    clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
+                    if (miss || !(ain < aout)) continue;
+                    const float *wcol = pa + (size_t)iu * g.nv;
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) {
+                        for (int iv = rlo[kk]; iv <= rhi[kk]; ++iv) {
+                            const float2 e = __ldg(&g.zbox[zboff[kk] + iv]);
+                            const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
+                            acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (col_ok && !HOIST) {
         const float x0 = g.bx0 + i * g.dx, x1 = x0 + g.dx;
         const float y0 = g.by0 + j * g.dy, y1 = y0 + g.dy;
         const float cu = 0.5f * (g.nu - 1), cv = 0.5f * (g.nv - 1);
@@ -524,9 +645,8 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
         // the 0.05-pixel margins.
         const float inv_du = 1.0f / g.du, inv_dv = 1.0f / g.dv;
         const size_t nuv = (size_t)g.nu * g.nv;
-        const int rlast = g.nv - BWD_SHORT_ROWS;     // first row of the last full short window
         for (int a = a_begin; a < a_end; ++a) {
-            const float2 cs = g.trig[a];
+            const float2 cs = __ldg(&g.trig[a]);
             float umin = FLT_MAX, umax = -FLT_MAX, magmin = FLT_MAX, magmax = 0.0f;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -547,99 +667,56 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
             // extreme at a corner).  The window holds for every detector
             // column below; a row that misses the voxel for one of them adds
             // an exact zero.
-            auto window = [&](int kk, int &lo, int &hi) {
+            int r0[K], r1[K];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
                 const int k = k0 + kk * 32 + lane;
                 const float zlo = (g.bz0 + k * g.dz) * inv_dv, zhi = (g.bz0 + (k + 1) * g.dz) * inv_dv;
                 const float vmin = fminf(zlo * magmin, zlo * magmax);
                 const float vmax = fmaxf(zhi * magmin, zhi * magmax);
-                lo = max(0, (int)ceilf(vmin + (cv - 0.05f)));
-                hi = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
-            };
-            // Windows of at most BWD_SHORT_ROWS rows in every lane (the usual
-            // case: a slab spans dz * mag / dv rows) take a fixed sequence of
-            // BWD_SHORT_ROWS rows starting at r0 (moved down to fit the
-            // detector) instead of a loop; rows outside the window meet the
-            // voxel nowhere and add exact zeros, so the same nonzero terms are
-            // summed in the same order either way.
-            int r0[K];
-            bool short_rows = !HOIST || rlast >= 0;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                int hi;
-                window(kk, r0[kk], hi);
-                short_rows = short_rows && hi - r0[kk] < BWD_SHORT_ROWS;
+                r0[kk] = max(0, (int)ceilf(vmin + (cv - 0.05f)));
+                r1[kk] = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
             }
+            // Windows of at most BWD_SHORT_ROWS rows in every lane (the usual
+            // case: a slab spans dz * mag / dv rows) take a fixed, predicated
+            // sequence instead of a loop; the same rows are summed in the same
+            // order either way.
+            bool short_rows = true;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) short_rows = short_rows && r1[kk] - r0[kk] < BWD_SHORT_ROWS;
             short_rows = __all_sync(0xffffffffu, short_rows);
             const float *pa = wproj + (size_t)a * nuv;
-            if (short_rows) {
-                // HOIST: the fixed sequence starts at r0 moved down to fit the
-                // detector and the three rows' slab intervals are loaded once
-                // per angle (a row outside the window meets the voxel nowhere:
-                // exact zero); otherwise the rows past the window are skipped,
-                // their intervals read per detector column.
-                float2 zb[HOIST ? K : 1][BWD_SHORT_ROWS];
-                int r1[HOIST ? 1 : K];
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    if (HOIST) {
-                        r0[kk] = min(r0[kk], rlast);
-                        const float2 *zr = g.zbox + (size_t)min(k0 + kk * 32 + lane, g.nz - 1) * g.nv + r0[kk];
-#pragma unroll
-                        for (int t = 0; t < BWD_SHORT_ROWS; ++t) zb[HOIST ? kk : 0][t] = zr[t];
-                    } else {
-                        int lo;
-                        window(kk, lo, r1[HOIST ? 0 : kk]);
-                    }
-                }
-                for (int iu = iu0; iu <= iu1; ++iu) {
-                    const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
-                    const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
-                    float ain = -FLT_MAX, aout = FLT_MAX;
-                    bool miss = false;
-                    clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
-                    clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
-                    if (miss || !(ain < aout)) continue;
-                    const float *wcol = pa + (size_t)iu * g.nv;
+            // unrolled for the same reason as the hoisted loop above
+#pragma unroll BWD_IU_UNROLL
+            for (int iu = iu0; iu <= iu1; ++iu) {
+                const float4 xy = __ldg(&g.ray_xy[(size_t)a * g.nu + iu]);
+                const float2 q = __ldg(&g.ray_xyq[(size_t)a * g.nu + iu]);
+                float ain = -FLT_MAX, aout = FLT_MAX;
+                bool miss = false;
+                clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
+                clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
+                if (miss || !(ain < aout)) continue;
+                const float *wcol = pa + (size_t)iu * g.nv;
+                if (short_rows) {
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) {
-                        const float *wr = wcol + r0[kk];
-                        if (HOIST) {
+                        const float2 *zb = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv;
 #pragma unroll
-                            for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
-                                const float2 e = zb[HOIST ? kk : 0][t];
+                        for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
+                            const int iv = r0[kk] + t;
+                            if (iv <= r1[kk]) {
+                                const float2 e = __ldg(zb + iv);
                                 const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
-                                acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wr + t), acc[kk]);
-                            }
-                        } else {
-                            const float2 *zb2 = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv + r0[kk];
-#pragma unroll
-                            for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
-                                if (r0[kk] + t <= r1[HOIST ? 0 : kk]) {
-                                    const float2 e = zb2[t];
-                                    const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
-                                    acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wr + t), acc[kk]);
-                                }
+                                acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
                             }
                         }
                     }
-                }
-            } else {
-                for (int iu = iu0; iu <= iu1; ++iu) {
-                    const float4 xy = g.ray_xy[(size_t)a * g.nu + iu];
-                    const float2 q = g.ray_xyq[(size_t)a * g.nu + iu];
-                    float ain = -FLT_MAX, aout = FLT_MAX;
-                    bool miss = false;
-                    clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
-                    clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
-                    if (miss || !(ain < aout)) continue;
-                    const float *wcol = pa + (size_t)iu * g.nv;
+                } else {
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) {
-                        const float2 *zb = g.zbox + (size_t)min(k0 + kk * 32 + lane, g.nz - 1) * g.nv;
-                        int rlo, rhi;
-                        window(kk, rlo, rhi);
-                        for (int iv = rlo; iv <= rhi; ++iv) {
-                            const float2 e = zb[iv];         // row iv's alpha interval in slab k
+                        const float2 *zb = g.zbox + (size_t)(k0 + kk * 32 + lane) * g.nv;
+                        for (int iv = r0[kk]; iv <= r1[kk]; ++iv) {
+                            const float2 e = __ldg(zb + iv);        // row iv's alpha interval in slab k
                             const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
                             // a miss adds exactly zero: the same sum as skipping it
                             acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
@@ -673,10 +750,8 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
         Storage<T>::store(vol + v, stored);
         sq += (double)stored * (double)stored;
     }
-    if (partial) {
-        const double s = block_sum<BWD_THREADS>(sq, red);
-        if (threadIdx.x == 0) *partial = s;
-    }
+    double *partial = partial_at();
+    if (partial) warp_partial(sq, partial);
 }
 
 }  // namespace cbct

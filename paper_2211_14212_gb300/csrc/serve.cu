@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(FWD_THREADS, 3) srv_forward(const SlotTable *t
         const int local = item - tab->fwd_start[s];
         const int tx = local % sd.fgx, ty = (local / sd.fgx) % sd.fgy, a = local / (sd.fgx * sd.fgy);
         const Epilogue epi{&sd.st->fa, &sd.st->fb, 0.0, 0.0, nullptr, nullptr, nullptr, sd.Uw};
-        forward_tile<float, false, SRV_FWD_ROWS, true>(sd.g, sd.V, sd.U, epi, tx, ty, a, sd.pf + local, red);
+        forward_tile<float, false, SRV_FWD_ROWS, true>(sd.g, sd.V, sd.U, epi, tx, ty, a,
+                                                       [&]() { return sd.pf + (size_t)local * TILE_PARTIALS; }, red);
     }
 }
 
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) srv_backward(const SlotTable *
         const int tbx = local % sd.bgx, tby = (local / sd.bgx) % sd.bgy, tbz = local / (sd.bgx * sd.bgy);
         const Epilogue epi{&sd.st->ba, &sd.st->bb, 0.0, 0.0, nullptr, nullptr, nullptr};
         backward_tile<float, true, SRV_CX, SRV_BK, true>(sd.g, sd.Uw, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
-                                                   nullptr, sd.pb + local, red);
+                                                         nullptr, [&]() { return sd.pb + (size_t)local * TILE_PARTIALS; }, red);
     }
 }
 
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(RED_THREADS) srv_after_forward(const SlotTable
     if (s >= tab->n) return;
     const SlotDev &sd = tab->s[s];
     if (sd.st->stop) return;
-    const double ss = reduce_partials(sd.pf, tab->fwd_start[s + 1] - tab->fwd_start[s], red);
+    const double ss = reduce_partials(sd.pf, (tab->fwd_start[s + 1] - tab->fwd_start[s]) * TILE_PARTIALS, red);
     if (threadIdx.x == 0) gk_after_forward_step(sd.st, ss, nullptr);
 }
 
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(RED_THREADS) srv_after_backward(const SlotTabl
     if (s >= tab->n) return;
     const SlotDev &sd = tab->s[s];
     if (sd.st->stop) return;
-    const double ss = reduce_partials(sd.pb, tab->bwd_start[s + 1] - tab->bwd_start[s], red);
+    const double ss = reduce_partials(sd.pb, (tab->bwd_start[s + 1] - tab->bwd_start[s]) * TILE_PARTIALS, red);
     if (threadIdx.x == 0)
         gk_after_backward_step(sd.st, ss, sd.method, sd.hist_r, sd.hist_n, nullptr, nullptr, sd.cap);
 }
@@ -231,7 +232,7 @@ size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
     t += al((size_t)d.nz * d.nv * 8);                       // z slab table
     t += 3 * al(n * 4);                                     // U, |d'| U and the staged b
     t += al(m * 4) * (method == M_LSMR ? 4 : 3);            // V, w, x (+ hbar)
-    t += al(nf * 8) + al(nb * 8) + al(sizeof(GkState)) + al((size_t)2 * iters * 8);
+    t += al(nf * 8 * TILE_PARTIALS) + al(nb * 8 * TILE_PARTIALS) + al(sizeof(GkState)) + al((size_t)2 * iters * 8);
     t += al(m * 4);                                         // re-layout of x when the result is read out
     return t;
 }
@@ -319,8 +320,8 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     if (e == cudaSuccess) e = A(&sl.w, (size_t)m);
     if (e == cudaSuccess) e = A(&sl.x, (size_t)m);
     if (e == cudaSuccess && r.method == M_LSMR) e = A(&sl.h2, (size_t)m);
-    if (e == cudaSuccess) e = A(&sl.pf, (size_t)std::max(sl.nf, VEC_BLOCKS));
-    if (e == cudaSuccess) e = A(&sl.pb, (size_t)sl.nb);
+    if (e == cudaSuccess) e = A(&sl.pf, (size_t)std::max(sl.nf * TILE_PARTIALS, VEC_BLOCKS));
+    if (e == cudaSuccess) e = A(&sl.pb, (size_t)sl.nb * TILE_PARTIALS);
     if (e == cudaSuccess) e = A(&sl.st, (size_t)1);
     if (e == cudaSuccess) e = A(&sl.hist, (size_t)2 * r.iters);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.b, r.b.data(), sizeof(float) * n, cudaMemcpyHostToDevice, sa);
@@ -348,7 +349,7 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     Epilogue eb{&sl.st->ba, &sl.st->bb, 0.0, 0.0, sl.pb, &sl.st->stop, nullptr};
     st = launch_backward(g, sl.Uw, sl.V, CBCT_F32, eb, sa, true, nullptr);
     if (st != CBCT_OK) return st;
-    gk_begin2<<<1, RED_THREADS, 0, sa>>>(sl.st, sl.pb, sl.nb, r.method);
+    gk_begin2<<<1, RED_THREADS, 0, sa>>>(sl.st, sl.pb, sl.nb * TILE_PARTIALS, r.method);
     k_start_dirs<float><<<VEC_BLOCKS, VEC_THREADS, 0, sa>>>(sl.V, sl.w, r.method == M_LSMR ? sl.h2 : nullptr, nullptr,
                                                             m, sl.st);
     CBCT_CUDA_TRY(cudaGetLastError());

@@ -82,7 +82,7 @@ struct ExplicitMonitor {
         if (!on) return CBCT_OK;
         tol = o->stop_tol;
         cap = o->iters;
-        nf = forward_num_blocks(g);
+        nf = forward_num_partials(g);
         CBCT_CUDA_TRY(ws.alloc(&r, (size_t)n));
         CBCT_CUDA_TRY(ws.alloc(&xprev, (size_t)m));
         CBCT_CUDA_TRY(ws.alloc(&part, (size_t)nf));
@@ -375,7 +375,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     // m: length of a volume-side vector (padded z-fastest layout); mvox: voxels
     const int64_t n = cbct_geometry_num_rays(geom), m = zf_len(geom->dev), mvox = cbct_geometry_num_voxels(geom);
     const int iters = o->iters;
-    const int nf = forward_num_blocks(g), nb = backward_num_blocks(g);
+    const int nf = forward_num_partials(g), nb = backward_num_partials(g);
     Workspace ws(s);
     SolveIO io{};
     cbct_status st = setup_io(geom, b, x, ws, io);
@@ -606,7 +606,7 @@ static cbct_status cgls_solve(const cbct_geometry *geom, const float *b, float *
     // m: length of a volume-side vector (padded z-fastest layout); mvox: voxels
     const int64_t n = cbct_geometry_num_rays(geom), m = zf_len(geom->dev), mvox = cbct_geometry_num_voxels(geom);
     const int iters = o->iters;
-    const int nf = forward_num_blocks(g);
+    const int nf = forward_num_partials(g);
     Workspace ws(s);
     SolveIO io{};
     cbct_status st = setup_io(geom, b, x, ws, io);

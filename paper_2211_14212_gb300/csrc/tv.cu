@@ -197,7 +197,7 @@ static cbct_status cgls_tv_solve(const cbct_geometry *geom, const float *b, floa
     const int iters = o->iters, outer = o->tv_outer;
     const double lam = o->lambda;
     const VolIndex vi{g.nx, g.ny, g.nz};
-    const int nf = forward_num_blocks(g);
+    const int nf = forward_num_partials(g);
     Workspace ws(s);
     SolveIO io{};
     cbct_status st = setup_io(geom, b, x, ws, io);
