@@ -19,7 +19,8 @@ Printed JSON line (rank 0):
              t_bound = max(compulsory HBM bytes / HBM peak, gather bytes /
              L2 peak, warp instructions / issue peak) term by term;
   serving    the serving stream (64 requests of 128^3..384^3 scans, Poisson
-             arrivals at 0.8 of the one-at-a-time throughput) through the
+             arrivals at 0.8 of the one-at-a-time throughput, from measured
+             service times) through the
              continuous-batching server and through the one-request-at-a-time
              solver, both fed in real time: recon/s, p50 / p99 / mean latency
              and the largest relative difference between their results;
@@ -107,12 +108,12 @@ def code_only(text):
 
 
 def projector_hash(sources=None):
-    """sha256 over the code of the projector kernel sources (projector.cu +
-    projector_device.cuh, comments and whitespace dropped), first 16 hex
+    """sha256 over the code of the projector kernel sources (projector.cu,
+    projector_device.cuh, transpose.cuh; comments and whitespace dropped), first 16 hex
     digits: the ncu counters stay attached to the kernels while only their
     comments change."""
     h = hashlib.sha256()
-    for name in ("projector.cu", "projector_device.cuh"):
+    for name in ("projector.cu", "projector_device.cuh", "transpose.cuh"):
         if sources is not None:
             text = sources[name]
         else:
@@ -373,7 +374,7 @@ def run_ours(args):
 
     serving = None
     if not args.no_serving and rank == 0:
-        serving = serving_compare(cbct, torch, dev, args.requests, args.serving_scale, value,
+        serving = serving_compare(cbct, torch, dev, args.requests, args.serving_scale,
                                   args.serving_slots, args.serving_budget_gb, args.serving_schedule)
 
     if rank != 0:
@@ -761,26 +762,55 @@ def latency_summary(lat, span, count):
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "max_s": float(lat.max())}
 
 
-def serving_compare(cbct, torch, dev, count, scale, gupd_per_s, slots, budget_gb, schedule, load=0.8):
+def calibrate_service(cbct, reqs, picks=4):
+    """One-at-a-time service time model of the stream, measured: the requests
+    at `picks` quantiles of nnz(A) are solved (through the same path as the
+    plain arm) at 3 and 6 iterations; the difference gives the time of one
+    iteration per nnz (updates/s) and the rest a fixed cost per request per
+    (rays + voxels) (scan set-up, b in, x out).  Returns the predicted service
+    time of every request and the fitted figures."""
+    import numpy as np
+    order = np.argsort([r["nnz"] for r in reqs])
+    idx = sorted({int(order[int(round(q * (len(order) - 1)))]) for q in np.linspace(0.0, 1.0, picks)})
+    rates, fixed = [], []
+    for i in idx:
+        r = reqs[i]
+        t = {}
+        for k in (3, 6):
+            t0 = time.perf_counter()
+            geom = cbct.Geometry(r["geom"])
+            getattr(cbct, r["solver"])(geom, r["b"], k)
+            geom.close()
+            t[k] = time.perf_counter() - t0
+        per_iter = max((t[6] - t[3]) / 3.0, 1e-6)
+        data = r["geom"].num_rays + r["geom"].num_voxels
+        rates.append(2.0 * r["nnz"] / per_iter)
+        fixed.append(max(t[3] - 3.0 * per_iter, 0.0) / data)
+    rate, fix = float(np.median(rates)), float(np.median(fixed))
+    svc = np.array([2.0 * r["nnz"] * r["iters"] / rate + fix * (r["geom"].num_rays + r["geom"].num_voxels)
+                    for r in reqs])
+    return svc, {"updates_per_s": rate, "fixed_s_per_element": fix, "calibration_requests": idx}
+
+
+def serving_compare(cbct, torch, dev, count, scale, slots, budget_gb, schedule, load=0.8):
     """The serving stream through the one-request-at-a-time solver and through
     the server, both fed in real time with the same Poisson arrivals.  The
-    arrival rate is `load` x the one-at-a-time throughput predicted from
-    each request's nnz(A) x (2 iters + 1) projector updates at the solver's
-    measured rate `gupd_per_s` (the 256^3 step's Gupdates/s)."""
+    arrival rate is `load` x the one-at-a-time throughput predicted by the
+    measured service model (calibrate_service)."""
     import numpy as np
     reqs = serving_requests(count, scale)
     serving_inputs(cbct, torch, dev, reqs)
-    work = sum(r["nnz"] * (2 * r["iters"] + 1) for r in reqs)
-    est_total_s = work / (gupd_per_s * 1e9)
-    rate = load * len(reqs) / est_total_s
-    rng = np.random.default_rng(4)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
-    arrivals -= arrivals[0]
     for r in reqs[:2]:                                  # warm-up of both paths (untimed)
         geom = cbct.Geometry(r["geom"])
         getattr(cbct, r["solver"])(geom, r["b"], 2)
         geom.close()
     server_arm(cbct, reqs[:2], [0.0, 0.0], slots, budget_gb, schedule)
+    svc, model = calibrate_service(cbct, reqs)
+    est_total_s = float(svc.sum())
+    rate = load * len(reqs) / est_total_s
+    rng = np.random.default_rng(4)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    arrivals -= arrivals[0]
     lat_p, xs, span_p = plain_arm(cbct, reqs, arrivals)
     lat_s, span_s, diff, stats = server_arm(cbct, reqs, arrivals, slots, budget_gb, schedule, xs)
     return {"workload": "%d requests: %d^3..%d^3 volumes, %d..%d px square detectors, %d..%d angles, "
@@ -790,7 +820,7 @@ def serving_compare(cbct, torch, dev, count, scale, gupd_per_s, slots, budget_gb
                             min(r["geom"].nangles for r in reqs), max(r["geom"].nangles for r in reqs),
                             min(r["iters"] for r in reqs), max(r["iters"] for r in reqs)),
             "scale": scale, "offered_load": load, "arrival_rate_per_s": rate,
-            "predicted_one_at_a_time_s": est_total_s,
+            "predicted_one_at_a_time_s": est_total_s, "service_model": model,
             "plain": latency_summary(lat_p, span_p, len(reqs)),
             "server": dict(latency_summary(lat_s, span_s, len(reqs)), schedule=schedule, max_slots=slots,
                            budget_gb=budget_gb, steps=stats["steps"], graph_replays=stats["graph_replays"]),
@@ -807,7 +837,7 @@ def run_serving(args):
     dev = torch.device("cuda", 0)
     out = {"mode": "serving"}
     for sched in args.serving_schedule.split(","):
-        out[sched] = serving_compare(cbct, torch, dev, args.requests, args.serving_scale, args.serving_rate,
+        out[sched] = serving_compare(cbct, torch, dev, args.requests, args.serving_scale,
                                      args.serving_slots, args.serving_budget_gb, sched)
     print(json.dumps(out), flush=True)
     return 0
@@ -831,8 +861,6 @@ def main():
     ap.add_argument("--serving-budget-gb", type=float, default=96.0)
     ap.add_argument("--serving-schedule", default="fifo",
                     help="server schedule (fifo, srpt, ratio, share; --mode serving takes a comma list)")
-    ap.add_argument("--serving-rate", type=float, default=700.0,
-                    help="--mode serving: the solver's Gupdates/s that sets the arrival rate")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream in the default run")
     ap.add_argument("--fwd-rows", type=int, default=4, help="--mode profile-solve: forward rays per lane")
     ap.add_argument("--bwd-config", type=int, default=5, help="--mode profile-solve: transpose tile")

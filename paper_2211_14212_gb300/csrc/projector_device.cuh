@@ -499,7 +499,7 @@ constexpr int BWD_SHORT_ROWS = 3;
 // ((j * nx + i) * nz + k) (unpadded); they may be the same buffer (each lane
 // reads and writes only its own voxels).  ZFAST output goes to the padded
 // z-fastest layout, else to the ABI layout x[k][j][i].
-template <typename T, bool ZFAST, int CX, int K, bool HOIST, typename PartialAt>
+template <typename T, bool ZFAST, int CX, int K, bool HOIST, int IU_UNROLL = 0, typename PartialAt>
 __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__restrict__ wproj, T *__restrict__ vol,
                                               const Epilogue &epi, int tx, int ty, int tz, int a_begin, int a_end,
                                               const float *acc_in, float *acc_out, PartialAt &&partial_at,
@@ -507,7 +507,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
     constexpr int CY = 8 / CX;
     // detector columns per unrolled step of the column loops: as many as fit
     // in registers next to the voxels' sums
-    constexpr int BWD_IU_UNROLL = !HOIST ? 1 : K == 1 ? 2 : K == 2 ? 4 : 2;
+    constexpr int BWD_IU_UNROLL = IU_UNROLL > 0 ? IU_UNROLL : !HOIST ? 1 : K == 1 ? 2 : K == 2 ? 4 : 2;
     // HOIST: the slab intervals of the candidate rows are loaded once per
     // angle and kept in registers (3 x 2 per voxel of the lane); otherwise
     // they are loaded for every detector column.

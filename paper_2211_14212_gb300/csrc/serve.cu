@@ -88,20 +88,29 @@ __device__ __forceinline__ int claim_tile(unsigned *counter, int *slot_sh) {
     return *slot_sh;
 }
 
+// The tile kernels copy the claimed tile's DevGeom into shared memory, one
+// int per thread (its fields then need no registers of their own).
+static_assert(sizeof(DevGeom) % sizeof(int) == 0 && sizeof(DevGeom) / sizeof(int) <= FWD_THREADS &&
+                  sizeof(DevGeom) / sizeof(int) <= BWD_THREADS,
+              "DevGeom is copied one int per thread");
+
 // U <- fa * A V + fb * U for every slot (forward tiles of all slots).
 __global__ void __launch_bounds__(FWD_THREADS, 3) srv_forward(const SlotTable *tab, unsigned *counter) {
     __shared__ double red[FWD_THREADS / 32];
     __shared__ int item_sh;
+    __shared__ DevGeom g_sh;               // the claimed tile's geometry
     const int n = tab->n;
     const int total = tab->fwd_start[n];
     for (int item = claim_tile(counter, &item_sh); item < total; item = claim_tile(counter, &item_sh)) {
         const int s = find_slot(tab->fwd_start, n, item);
         const SlotDev &sd = tab->s[s];
         if (sd.st->stop) continue;
+        if (threadIdx.x < sizeof(DevGeom) / sizeof(int)) ((int *)&g_sh)[threadIdx.x] = ((const int *)&sd.g)[threadIdx.x];
+        __syncthreads();
         const int local = item - tab->fwd_start[s];
         const int tx = local % sd.fgx, ty = (local / sd.fgx) % sd.fgy, a = local / (sd.fgx * sd.fgy);
         const Epilogue epi{&sd.st->fa, &sd.st->fb, 0.0, 0.0, nullptr, nullptr, nullptr, sd.Uw};
-        forward_tile<float, false, SRV_FWD_ROWS, true>(sd.g, sd.V, sd.U, epi, tx, ty, a,
+        forward_tile<float, false, SRV_FWD_ROWS, true>(g_sh, sd.V, sd.U, epi, tx, ty, a,
                                                        [&]() { return sd.pf + (size_t)local * TILE_PARTIALS; }, red);
     }
 }
@@ -110,17 +119,21 @@ __global__ void __launch_bounds__(FWD_THREADS, 3) srv_forward(const SlotTable *t
 __global__ void __launch_bounds__(BWD_THREADS, 4) srv_backward(const SlotTable *tab, unsigned *counter) {
     __shared__ double red[BWD_THREADS / 32];
     __shared__ int item_sh;
+    __shared__ DevGeom g_sh;               // the claimed tile's geometry
     const int n = tab->n;
     const int total = tab->bwd_start[n];
     for (int item = claim_tile(counter, &item_sh); item < total; item = claim_tile(counter, &item_sh)) {
         const int s = find_slot(tab->bwd_start, n, item);
         const SlotDev &sd = tab->s[s];
         if (sd.st->stop) continue;
+        if (threadIdx.x < sizeof(DevGeom) / sizeof(int)) ((int *)&g_sh)[threadIdx.x] = ((const int *)&sd.g)[threadIdx.x];
+        __syncthreads();
         const int local = item - tab->bwd_start[s];
         const int tbx = local % sd.bgx, tby = (local / sd.bgx) % sd.bgy, tbz = local / (sd.bgx * sd.bgy);
         const Epilogue epi{&sd.st->ba, &sd.st->bb, 0.0, 0.0, nullptr, nullptr, nullptr};
-        backward_tile<float, true, SRV_CX, SRV_BK, true>(sd.g, sd.Uw, sd.V, epi, tbx, tby, tbz, 0, sd.g.nangles, nullptr,
-                                                         nullptr, [&]() { return sd.pb + (size_t)local * TILE_PARTIALS; }, red);
+        backward_tile<float, true, SRV_CX, SRV_BK, true, 2>(g_sh, sd.Uw, sd.V, epi, tbx, tby, tbz, 0, g_sh.nangles,
+                                                         nullptr, nullptr,
+                                                         [&]() { return sd.pb + (size_t)local * TILE_PARTIALS; }, red);
     }
 }
 
@@ -208,6 +221,7 @@ struct Slot {
     bool aged = false;                // passed over SRV_SRPT_AGE_CAP steps in a row: first until it finishes
     double work_iter = 0.0;           // cost model of one iteration: rays x (nx + ny)
     cudaEvent_t ready = nullptr;      // recorded on the admission stream once the set-up is queued
+    cudaGraphExec_t solo_graph = nullptr;   // captured step of this slot alone (enqueue_step)
 };
 
 // Forward tiles and bricks of a scan under the server's launch shapes.
@@ -373,6 +387,10 @@ void ServerImpl::release_slot(Slot &sl, cudaStream_t st, bool keep_geometry) {
         cudaEventDestroy(sl.ready);
         sl.ready = nullptr;
     }
+    if (sl.solo_graph) {
+        cudaGraphExecDestroy(sl.solo_graph);
+        sl.solo_graph = nullptr;
+    }
     if (sl.geom) {
         cudaStreamSynchronize(st);
         if (keep_geometry) {
@@ -429,14 +447,31 @@ void ServerImpl::complete(const std::shared_ptr<Request> &r, cbct_status st, con
 }
 
 // One Krylov iteration of every slot, then the per-slot status to the host.
+// A step of one slot whose tiles fill the GPU alone runs the single-request
+// projector kernels instead of the multi-slot ones (the geometry in kernel
+// parameters, no tile claiming); both walk the same tiles in the same order
+// and leave the norm partials in the same places, so the results agree
+// bit for bit.  That step is captured once per slot.
 cbct_status ServerImpl::enqueue_step() {
+    Slot *solo = step_slots.size() == 1 && slots[step_slots[0]].nf >= SRV_SAT_TILES ? &slots[step_slots[0]] : nullptr;
     auto launch_all = [&]() -> cudaError_t {
-        cudaError_t e0 = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned), s);
-        if (e0 != cudaSuccess) return e0;
-        srv_forward<<<fwd_grid, FWD_THREADS, 0, s>>>(tab_dev, counters);
-        srv_after_forward<<<SRV_MAX_SLOTS, RED_THREADS, 0, s>>>(tab_dev);
-        srv_backward<<<bwd_grid, BWD_THREADS, 0, s>>>(tab_dev, counters + 1);
-        srv_after_backward<<<SRV_MAX_SLOTS, RED_THREADS, 0, s>>>(tab_dev);
+        if (solo) {
+            const DevGeom &g = solo->geom->dev;
+            const Epilogue ef{&solo->st->fa, &solo->st->fb, 0.0, 0.0, solo->pf, &solo->st->stop, nullptr, solo->Uw};
+            const Epilogue eb{&solo->st->ba, &solo->st->bb, 0.0, 0.0, solo->pb, &solo->st->stop, nullptr};
+            if (launch_forward(g, solo->V, solo->U, CBCT_F32, ef, s, true) != CBCT_OK) return cudaErrorLaunchFailure;
+            srv_after_forward<<<1, RED_THREADS, 0, s>>>(tab_dev);
+            if (launch_backward(g, solo->Uw, solo->V, CBCT_F32, eb, s, true, nullptr) != CBCT_OK)
+                return cudaErrorLaunchFailure;
+            srv_after_backward<<<1, RED_THREADS, 0, s>>>(tab_dev);
+        } else {
+            cudaError_t e0 = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned), s);
+            if (e0 != cudaSuccess) return e0;
+            srv_forward<<<fwd_grid, FWD_THREADS, 0, s>>>(tab_dev, counters);
+            srv_after_forward<<<SRV_MAX_SLOTS, RED_THREADS, 0, s>>>(tab_dev);
+            srv_backward<<<bwd_grid, BWD_THREADS, 0, s>>>(tab_dev, counters + 1);
+            srv_after_backward<<<SRV_MAX_SLOTS, RED_THREADS, 0, s>>>(tab_dev);
+        }
         srv_update<<<vec_grid, VEC_THREADS, 0, s>>>(tab_dev);
         srv_status<<<1, SRV_MAX_SLOTS, 0, s>>>(tab_dev, stat_dev);
         cudaError_t e = cudaGetLastError();
@@ -444,7 +479,8 @@ cbct_status ServerImpl::enqueue_step() {
             e = cudaMemcpyAsync(stat_host, stat_dev, sizeof(SlotStatus) * SRV_MAX_SLOTS, cudaMemcpyDeviceToHost, s);
         return e;
     };
-    if (use_graph && !step_graph) {
+    cudaGraphExec_t &exec = solo ? solo->solo_graph : step_graph;
+    if (use_graph && !exec) {
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
@@ -452,16 +488,16 @@ cbct_status ServerImpl::enqueue_step() {
             e = cudaStreamEndCapture(s, &graph);
             if (e1 != cudaSuccess) e = e1;
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&step_graph, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) {             // fall back to plain launches
             (void)cudaGetLastError();
-            step_graph = nullptr;
+            exec = nullptr;
             use_graph = 0;
         }
     }
-    if (use_graph && step_graph) {
-        CBCT_CUDA_TRY(cudaGraphLaunch(step_graph, s));
+    if (use_graph && exec) {
+        CBCT_CUDA_TRY(cudaGraphLaunch(exec, s));
         ++graph_replays;
         return CBCT_OK;
     }

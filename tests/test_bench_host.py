@@ -90,15 +90,17 @@ def test_projector_hash_ignores_comments_only():
     """The ncu counters stay attached to the kernels while only comments or
     whitespace change, and detach when the code changes."""
     base = {"projector.cu": 'int f(int a) { return a + 1; } // one\n/* two */ const char *s = "//x /*y*/";\n',
-            "projector_device.cuh": "#pragma once\nint g();\n"}
+            "projector_device.cuh": "#pragma once\nint g();\n", "transpose.cuh": "int h();\n"}
     h = bench.projector_hash(base)
     recommented = {"projector.cu": '/* header */\nint f(int a)\n{\n    return a + 1;  // changed note\n}\n'
                                    'const char *s = "//x /*y*/";\n',
-                   "projector_device.cuh": "#pragma once   // guard\nint g();\n"}
+                   "projector_device.cuh": "#pragma once   // guard\nint g();\n",
+                   "transpose.cuh": "int h();  /* tiles */\n"}
     assert bench.projector_hash(recommented) == h
     changed = dict(base, **{"projector.cu": base["projector.cu"].replace("a + 1", "a + 2")})
     assert bench.projector_hash(changed) != h
     in_string = dict(base, **{"projector.cu": base["projector.cu"].replace('"//x /*y*/"', '"//x /*z*/"')})
     assert bench.projector_hash(in_string) != h
+    assert bench.projector_hash(dict(base, **{"transpose.cuh": "int h2();\n"})) != h
     assert bench.code_only('a /* b */ c // d\n  e') == "a c e"
 
