@@ -633,7 +633,8 @@ def run_microct(args):
 
 def run_profile_solve(args):
     """A target for ncu: the 256^3 scan with the benchmark's launch shapes
-    (4 rays per lane, 2 x 4 columns x 128 transpose tile) and one LSQR solve
+    (by default 4 rays per lane, 2 x 4 columns x 64 transpose tile; the
+    autotuner's choice at this size) and one LSQR solve
     of 2 iterations on a random b, plain launches.  Its first forward_kernel
     and backward_kernel launches are the instantiations the benchmark's
     solvers run (v-fastest projections with the weighted copy, z-fastest
@@ -863,7 +864,7 @@ def main():
                     help="server schedule (fifo, srpt, ratio, share; --mode serving takes a comma list)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream in the default run")
     ap.add_argument("--fwd-rows", type=int, default=4, help="--mode profile-solve: forward rays per lane")
-    ap.add_argument("--bwd-config", type=int, default=5, help="--mode profile-solve: transpose tile")
+    ap.add_argument("--bwd-config", type=int, default=3, help="--mode profile-solve: transpose tile")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -650,12 +650,21 @@ void ServerImpl::run_steps() {
             cudaError_t e = cudaMemcpyAsync(tab_dev, tab_host, sizeof(SlotTable), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) table_dirty = false;
         }
+        // Steps queued before the host looks at the status again: under FIFO a
+        // slot that fills the GPU alone stays the only one picked until it
+        // finishes (nothing older waits and nothing fits beside it), so all
+        // its remaining iterations are queued at once (a slot that stops
+        // early turns the rest into no-ops); otherwise one.
+        int run = 1;
+        if (schedule == CBCT_SCHED_FIFO && step_slots.size() == 1 && slots[step_slots[0]].nf >= SRV_SAT_TILES)
+            run = std::max(1, slots[step_slots[0]].req->iters - slots[step_slots[0]].steps);
         const double t_step = now_s(t0);
-        cbct_status st = table_dirty ? cuda_fail(cudaGetLastError(), "server: slot table") : enqueue_step();
+        cbct_status st = table_dirty ? cuda_fail(cudaGetLastError(), "server: slot table") : CBCT_OK;
+        for (int q = 0; q < run && st == CBCT_OK; ++q) st = enqueue_step();
         cudaError_t e = cudaStreamSynchronize(s);
         {   // running estimate of the work rate (cost-model units per second)
             double w = 0.0;
-            for (int i : step_slots) w += slots[i].work_iter;
+            for (int i : step_slots) w += slots[i].work_iter * run;
             const double dt = now_s(t0) - t_step;
             if (dt > 0.0 && w > 0.0) work_rate = work_rate > 0.0 ? 0.8 * work_rate + 0.2 * (w / dt) : w / dt;
         }
@@ -677,14 +686,14 @@ void ServerImpl::run_steps() {
             }
             continue;
         }
-        ++steps_run;
+        steps_run += run;
         // table entries are in increasing slot index: walk them backwards so that
         // erasing a finished slot leaves the remaining indices valid
         std::vector<Slot> done_now;
         for (int ti = (int)step_slots.size() - 1; ti >= 0; --ti) {
             const int i = step_slots[ti];
             Slot &sl = slots[i];
-            ++sl.steps;
+            sl.steps += run;
             if (!stat_host[ti].stop && sl.steps < sl.req->iters) continue;
             done_now.push_back(sl);
             slots.erase(slots.begin() + i);
