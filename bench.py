@@ -54,8 +54,14 @@ REF_STEP_ANGLES = 8             # --impl reference: about 7 s per step, so K ste
 # 360 from ncu (dram__bytes_read.sum + dram__bytes_write.sum, and
 # smsp__inst_executed.sum = warp instructions), keyed by the code of the
 # projector sources they were measured on (projector_hash(), comments
-# ignored); the bench reports null once that code changed.
-NCU_COUNTERS = {}
+# ignored) and the launch shape (rays per lane, transpose configuration);
+# the bench reports null once either differs.
+NCU_COUNTERS = {
+    "forward": {"hash": "db16778c2d91c9f7", "shape": [4, 3], "kernel": "forward_kernel<float, 0, 4, 1>",
+                "dram_bytes": 3014525440, "warp_inst": 19929252800},
+    "backward": {"hash": "db16778c2d91c9f7", "shape": [4, 3], "kernel": "backward_kernel<float, 1, 2, 2, 1, 0>",
+                 "dram_bytes": 3160633600, "warp_inst": 35904504104},
+}
 
 # Instruction issue: one warp instruction per cycle per SM sub-partition.
 SMS, SUBPARTITIONS = 152, 4
@@ -241,7 +247,7 @@ def run_reference(args):
     return 0
 
 
-def roofline_block(g, nnz, fwd_ms, bwd_ms, clocks):
+def roofline_block(g, nnz, fwd_ms, bwd_ms, clocks, shape=None):
     """Roofline of the dominant projector kernel.  `achieved` is the gather-
     equivalent bandwidth (nnz x 4 B per launch / launch time) against the
     measured HBM copy peak, the scope table's projector target.  The kernels
@@ -249,13 +255,16 @@ def roofline_block(g, nnz, fwd_ms, bwd_ms, clocks):
     max(compulsory HBM bytes / HBM peak, gather bytes / L2 peak, warp
     instructions / issue peak): no L2 peak is measured on this machine (null),
     and the warp-instruction count comes from ncu (NCU_COUNTERS, null once the
-    kernel source changed)."""
+    kernel source changed or when the run's launch shape `shape` = (rays per
+    lane, transpose configuration) is not the one the counters were taken
+    on)."""
     dominant = "forward" if fwd_ms >= bwd_ms else "backward"
     avg_ms = fwd_ms if dominant == "forward" else bwd_ms
     peak, peak_kind = measured_peak()
     achieved = nnz * BYTES_PER_UPDATE / (avg_ms * 1e-3) / 1e9
     c = NCU_COUNTERS.get(dominant)
-    fresh = c is not None and c.get("hash") == projector_hash()
+    fresh = c is not None and c.get("hash") == projector_hash() and \
+        (shape is None or tuple(c.get("shape", ())) == tuple(shape))
     warp_inst = c["warp_inst"] if fresh else None
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     issue_peak = SMS * SUBPARTITIONS * mhz * 1e6            # warp instructions per second
@@ -395,7 +404,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
         "lsqr_iters_per_s": lsqr_ips,
         "nnz": nnz,
-        "roofline": roofline_block(g, nnz, fwd_ms / max(fwd_n, 1), bwd_ms / max(bwd_n, 1), clocks),
+        "roofline": roofline_block(g, nnz, fwd_ms / max(fwd_n, 1), bwd_ms / max(bwd_n, 1), clocks,
+                                   (tune["fwd_rows"], tune["bwd_config"])),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * geom.num_rays,
                 "d2h_bytes_per_step": 2 * 4 * geom.num_voxels},
@@ -613,7 +623,7 @@ def run_microct(args):
     products = rep.forward_launches + rep.backward_launches
     fwd = rep.forward_ms / max(rep.forward_launches, 1)
     bwd = rep.backward_ms / max(rep.backward_launches, 1)
-    rl = roofline_block(g, nnz, fwd, bwd, clocks)
+    rl = roofline_block(g, nnz, fwd, bwd, clocks, (tune["fwd_rows"], tune["bwd_config"]))
     rl["traffic"] = None
     rl["t_bound"]["issue_ms"] = None
     rl["issue_util"] = None

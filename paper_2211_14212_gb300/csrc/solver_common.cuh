@@ -15,12 +15,22 @@ constexpr int VEC_THREADS = 256;
 constexpr int VEC_BLOCKS = 152 * 4;     // fixed grid: fixed partial layout, deterministic sums
 constexpr int RED_THREADS = 256;
 
-// Sum of n partials in a fixed order (thread t takes t, t+256, ...; then the
-// block tree), result valid in thread 0.  Launch with RED_THREADS threads.
+// Sum of n partials in a fixed order, result valid in thread 0: thread t
+// keeps four running sums (of the partials t + (4 q + r) RED_THREADS,
+// r = 0..3, so that four loads are in flight), the rest goes to the first,
+// the four are added pairwise, then the block tree.  Launch with RED_THREADS
+// threads.
 __device__ __forceinline__ double reduce_partials(const double *p, int n, double *scratch) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += RED_THREADS) s += p[i];
-    return block_sum<RED_THREADS>(s, scratch);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = threadIdx.x;
+    for (; i + 3 * RED_THREADS < n; i += 4 * RED_THREADS) {
+        s0 += p[i];
+        s1 += p[i + RED_THREADS];
+        s2 += p[i + 2 * RED_THREADS];
+        s3 += p[i + 3 * RED_THREADS];
+    }
+    for (; i < n; i += RED_THREADS) s0 += p[i];
+    return block_sum<RED_THREADS>((s0 + s1) + (s2 + s3), scratch);
 }
 
 // Givens rotation (c, s, r): [c s; -s c] [a; b] = [r; 0], r = hypot(a, b) >= 0.

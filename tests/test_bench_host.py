@@ -104,3 +104,25 @@ def test_projector_hash_ignores_comments_only():
     assert bench.projector_hash(dict(base, **{"transpose.cuh": "int h2();\n"})) != h
     assert bench.code_only('a /* b */ c // d\n  e') == "a c e"
 
+
+
+def test_roofline_counters_follow_code_and_launch_shape(monkeypatch):
+    """ncu counters enter the roofline line only for the kernel code and the
+    launch shape they were taken on; otherwise traffic and the issue floor
+    are null."""
+    import synth
+    g = synth.config("c2")
+    h = bench.projector_hash()
+    monkeypatch.setattr(bench, "NCU_COUNTERS", {
+        "backward": {"hash": h, "shape": [4, 3], "dram_bytes": 3.0e9, "warp_inst": 3.75e10}})
+    rl = bench.roofline_block(g, 2.8e10, 24.0, 38.0, {"sm_mhz": 2070.0}, (4, 3))
+    assert rl["kernel"] == "backward" and rl["bound"] == "issue"
+    assert rl["traffic"] == 3.0e9
+    assert abs(rl["t_bound"]["issue_ms"] - 3.75e10 / (152 * 4 * 2070e6) * 1e3) < 1e-9
+    assert abs(rl["frac"] - 2.8e10 * 4 / 38e-3 / 1e9 / rl["peak"]) < 1e-12
+    other = bench.roofline_block(g, 2.8e10, 24.0, 38.0, {"sm_mhz": 2070.0}, (4, 1))
+    assert other["traffic"] is None and other["t_bound"]["issue_ms"] is None
+    monkeypatch.setattr(bench, "NCU_COUNTERS", {
+        "backward": {"hash": "0" * 16, "shape": [4, 3], "dram_bytes": 3.0e9, "warp_inst": 3.75e10}})
+    stale = bench.roofline_block(g, 2.8e10, 24.0, 38.0, {"sm_mhz": 2070.0}, (4, 3))
+    assert stale["traffic"] is None and stale["issue_util"] is None
