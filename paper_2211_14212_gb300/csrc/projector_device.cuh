@@ -23,6 +23,7 @@
 #pragma once
 
 #include <cfloat>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -543,7 +544,6 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
         const float x0 = g.bx0 + i * g.dx, x1 = x0 + g.dx;
         const float y0 = g.by0 + j * g.dy, y1 = y0 + g.dy;
         const size_t nuv = (size_t)g.nu * g.nv;
-        const int rmax = g.nv - BWD_SHORT_ROWS;
         for (int a = a_begin; a < a_end; ++a) {
             const float2 cs = __ldg(&g.trig[a]);
             float umin = FLT_MAX, umax = -FLT_MAX, magmin = FLT_MAX, magmax = 0.0f;
@@ -560,8 +560,9 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
             }
             const int iu0 = max(0, (int)ceilf(__fmaf_rn(umin, inv_du, cu - 0.05f)));
             const int iu1 = min(g.nu - 1, (int)floorf(__fmaf_rn(umax, inv_du, cu + 0.05f)));
-            int r0[K];
-            bool short_rows = true;
+            // rows 2 / 3: every lane's window has at most 2 / 3 rows
+            int wlo[K];
+            bool rows2 = true, rows3 = true;
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) {
                 const int k = k0 + kk * 32 + lane;
@@ -569,17 +570,26 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                 const float vmax = fmaxf(zhi[kk] * magmin, zhi[kk] * magmax);
                 const int lo = max(0, (int)ceilf(vmin + (cv - 0.05f)));
                 const int hi = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
-                short_rows = short_rows && hi - lo < BWD_SHORT_ROWS;
-                r0[kk] = min(lo, rmax);
+                rows2 = rows2 && hi - lo < 2;
+                rows3 = rows3 && hi - lo < 3;
+                wlo[kk] = lo;
             }
-            short_rows = __all_sync(0xffffffffu, short_rows) && rmax >= 0;
+            rows2 = __all_sync(0xffffffffu, rows2) && g.nv >= 2;
+            rows3 = __all_sync(0xffffffffu, rows3) && g.nv >= 3;
             const float *pa = wproj + (size_t)a * nuv;
-            if (short_rows) {
-                float2 zb[K][BWD_SHORT_ROWS];
+            // A fixed sequence of ROWS rows per voxel, starting at the window's
+            // first row moved down to fit the detector; their slab intervals
+            // are loaded once per angle.
+            auto short_pass = [&](auto rows_c) {
+                constexpr int ROWS = decltype(rows_c)::value;
+                int r0[K];
+                float2 zb[K][ROWS];
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk)
+                for (int kk = 0; kk < K; ++kk) {
+                    r0[kk] = min(wlo[kk], g.nv - ROWS);
 #pragma unroll
-                    for (int t = 0; t < BWD_SHORT_ROWS; ++t) zb[kk][t] = __ldg(&g.zbox[zboff[kk] + r0[kk] + t]);
+                    for (int t = 0; t < ROWS; ++t) zb[kk][t] = __ldg(&g.zbox[zboff[kk] + r0[kk] + t]);
+                }
                 // unrolled: the next columns' table and projection loads are
                 // issued before this column's sums (measured 7 % faster than
                 // the compiler's choice, which kept the loop rolled)
@@ -597,13 +607,18 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                     for (int kk = 0; kk < K; ++kk) {
                         const float *wr = wcol + r0[kk];
 #pragma unroll
-                        for (int t = 0; t < BWD_SHORT_ROWS; ++t) {
+                        for (int t = 0; t < ROWS; ++t) {
                             const float2 e = zb[kk][t];
                             const float lo = fmaxf(ain, e.x), hi = fminf(aout, e.y);
                             acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wr + t), acc[kk]);
                         }
                     }
                 }
+            };
+            if (rows2) {
+                short_pass(std::integral_constant<int, 2>());
+            } else if (rows3) {
+                short_pass(std::integral_constant<int, 3>());
             } else {
                 int rlo[K], rhi[K];
 #pragma unroll
