@@ -310,7 +310,10 @@ cbct_status cbct_hybrid_lsmr_solve(const cbct_geometry *geom, const float *b, fl
  * schedule.  CBCT_SCHED_FIFO takes them in submission order while the
  * step's forward tiles (8 detector columns x 128 rows of one angle each) stay
  * within 2048, so small requests share a step and large ones run one at a
- * time, oldest first (the order that minimises the longest wait);
+ * time, oldest first (the order that minimises the longest wait).  A step
+ * of one request that fills the GPU alone runs the single-request projector
+ * kernels, and under FIFO all of that request's remaining iterations are
+ * queued before the worker looks at the device again;
  * CBCT_SCHED_SRPT takes them in order of least remaining work (iterations
  * left x rays x (nx + ny)) under the same limit, which shortens the median
  * latency but makes long requests wait behind short ones (a request left out
