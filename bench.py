@@ -57,10 +57,10 @@ REF_STEP_ANGLES = 8             # --impl reference: about 7 s per step, so K ste
 # ignored) and the launch shape (rays per lane, transpose configuration);
 # the bench reports null once either differs.
 NCU_COUNTERS = {
-    "forward": {"hash": "db16778c2d91c9f7", "shape": [4, 3], "kernel": "forward_kernel<float, 0, 4, 1>",
-                "dram_bytes": 3014525440, "warp_inst": 19929252800},
-    "backward": {"hash": "db16778c2d91c9f7", "shape": [4, 3], "kernel": "backward_kernel<float, 1, 2, 2, 1, 0>",
-                 "dram_bytes": 3160633600, "warp_inst": 35904504104},
+    "forward": {"hash": "1a21aa326c147b5e", "shape": [4, 3], "kernel": "forward_kernel<float, 0, 4, 1>",
+                "dram_bytes": 3025939456, "warp_inst": 19929252800},
+    "backward": {"hash": "1a21aa326c147b5e", "shape": [4, 3], "kernel": "backward_kernel<float, 1, 2, 2, 1, 0>",
+                 "dram_bytes": 3025801472, "warp_inst": 35444234412},
 }
 
 # Instruction issue: one warp instruction per cycle per SM sub-partition.
