@@ -264,9 +264,9 @@ size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
 //               (one captured graph replayed) and hands finished slots on;
 //   read-out    copies each finished result to the host on its own stream,
 //               frees the slot's memory and wakes the waiters.
-// Geometries of finished slots are destroyed only while no slot is active
-// (their tables are a few MB), because freeing device memory waits for the
-// whole device.
+// Geometries of read-out slots are destroyed by the step thread right after
+// it has queued a step (freeing device memory waits for the whole device,
+// and the step thread waits for the step next anyway).
 struct ServerImpl {
     size_t budget = 0, in_use = 0;
     int max_slots = 1, use_graph = 1, device = 0, schedule = CBCT_SCHED_FIFO;
@@ -375,7 +375,7 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
 }
 
 // Frees the slot's buffers on stream `st`; the geometry is destroyed at once
-// or (keep_geometry) left in the graveyard for a quiet moment.
+// or (keep_geometry) left in the graveyard for the step thread.
 void ServerImpl::release_slot(Slot &sl, cudaStream_t st, bool keep_geometry) {
     for (void *p : {(void *)sl.U, (void *)sl.Uw, (void *)sl.b, (void *)sl.V, (void *)sl.w, (void *)sl.x, (void *)sl.h2,
                     (void *)sl.pf, (void *)sl.pb, (void *)sl.st, (void *)sl.hist})
@@ -605,9 +605,12 @@ void ServerImpl::run_steps() {
             if (stopping) break;
             incoming.swap(ready);
             active_slots = (int)(slots.size() + incoming.size());
-            if (slots.empty() && finishing.empty()) dead.swap(graveyard);     // a quiet moment
+            dead.swap(graveyard);
         }
-        for (cbct_geometry *g : dead) cbct_geometry_destroy(g);
+        if (slots.empty() && incoming.empty()) {        // nothing to step: free them now
+            for (cbct_geometry *g : dead) cbct_geometry_destroy(g);
+            continue;
+        }
         for (Slot &sl : incoming) {
             cudaStreamWaitEvent(s, sl.ready, 0);          // the step stream follows the slot's set-up
             slots.push_back(sl);
@@ -661,6 +664,10 @@ void ServerImpl::run_steps() {
         const double t_step = now_s(t0);
         cbct_status st = table_dirty ? cuda_fail(cudaGetLastError(), "server: slot table") : CBCT_OK;
         for (int q = 0; q < run && st == CBCT_OK; ++q) st = enqueue_step();
+        // read-out slots' geometries: freeing device memory waits for the
+        // device, which this thread does next anyway
+        for (cbct_geometry *g : dead) cbct_geometry_destroy(g);
+        dead.clear();
         cudaError_t e = cudaStreamSynchronize(s);
         {   // running estimate of the work rate (cost-model units per second)
             double w = 0.0;

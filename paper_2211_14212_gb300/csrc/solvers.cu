@@ -368,6 +368,19 @@ k_cg_p(float *__restrict__ p, const float *__restrict__ s, int64_t n, double *pa
 // ====================================================================== drivers
 
 
+// Fixed-order fold of many norm partials into FOLD_BLOCKS block sums (block b
+// takes a contiguous range), so that the single-block scalar step that
+// follows reads few values; used when a projector leaves more than
+// FOLD_MIN partials.
+constexpr int FOLD_BLOCKS = 152, FOLD_MIN = 16384;
+__global__ void __launch_bounds__(RED_THREADS) k_fold_partials(const double *p, int n, double *out) {
+    __shared__ double red[RED_THREADS / 32];
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int b0 = min(n, (int)blockIdx.x * chunk), b1 = min(n, b0 + chunk);
+    const double sum = reduce_partials(p + b0, b1 - b0, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = sum;
+}
+
 template <typename T>
 static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
                             cbct_solve_report *rep, cudaStream_t s, Method method, bool lsmr_proj) {
@@ -404,6 +417,8 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     CBCT_CUDA_TRY(ws.alloc(&pf, (size_t)nf));
     CBCT_CUDA_TRY(ws.alloc(&pb, (size_t)nb));
     CBCT_CUDA_TRY(ws.alloc(&pv, (size_t)VEC_BLOCKS));
+    double *pfold = nullptr;        // folded partials (k_fold_partials)
+    CBCT_CUDA_TRY(ws.alloc(&pfold, (size_t)2 * FOLD_BLOCKS));
     CBCT_CUDA_TRY(ws.alloc(&hist, (size_t)3 * iters));
     CBCT_CUDA_TRY(ws.alloc(&dst, 1));
     float *accum = nullptr;         // running sums of a transpose summed in passes
@@ -414,6 +429,18 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     Tracker tr;
     tr.profile = o->profile != 0;
     tr.s = s;
+    // the scalar steps read the tiles' partials directly or folded first
+    auto partials = [&](const double *p, int np, double *fold, const double **q, int *nq) {
+        if (np > FOLD_MIN) {
+            k_fold_partials<<<FOLD_BLOCKS, RED_THREADS, 0, s>>>(p, np, fold);
+            ++tr.launches;
+            *q = fold;
+            *nq = FOLD_BLOCKS;
+        } else {
+            *q = p;
+            *nq = np;
+        }
+    };
     GkState init;
     std::memset(&init, 0, sizeof init);
     init.damp = method == M_HYBRID ? 0.0 : o->lambda;
@@ -524,7 +551,12 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
                 done_fwd = true;
             }
         }
-        if (!done_fwd) gk_after_forward<<<1, RED_THREADS, 0, s>>>(dst, pf, nf, beta_arr);
+        if (!done_fwd) {
+            const double *q;
+            int nq;
+            partials(pf, nf, pfold, &q, &nq);
+            gk_after_forward<<<1, RED_THREADS, 0, s>>>(dst, q, nq, beta_arr);
+        }
         Epilogue eb{&dst->ba, &dst->bb, 0, 0, pb, stop, method == M_HYBRID ? (const void *)Vin : nullptr};
         r = bwd(W, Vout, eb);
         if (r != CBCT_OK) return r;
@@ -539,9 +571,13 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
                 done_bwd = true;
             }
         }
-        if (!done_bwd)
-            gk_after_backward<<<1, RED_THREADS, 0, s>>>(dst, pb, nb, (int)method, hist_r, hist_n, alpha_arr,
+        if (!done_bwd) {
+            const double *q;
+            int nq;
+            partials(pb, nb, pfold + FOLD_BLOCKS, &q, &nq);
+            gk_after_backward<<<1, RED_THREADS, 0, s>>>(dst, q, nq, (int)method, hist_r, hist_n, alpha_arr,
                                                          scale_arr, iters);
+        }
         tr.launches += 3;            // two finalize kernels + the update / projected solve
         em.keep(io.xz, m, stop, s, tr);
         if (method == M_LSQR) {
