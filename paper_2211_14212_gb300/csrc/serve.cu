@@ -49,6 +49,8 @@ struct SlotDev {
     float *U, *Uw, *V, *w, *x, *h2;     // Uw = |d'| U, the transpose's input
     GkState *st;
     double *pf, *pb, *hist_r, *hist_n;
+    const double *qf, *qb;  // the partials the scalar steps read: pf / pb, or their folds
+    int nqf, nqb;
     int method, cap;
     int fgx, fgy;          // forward tile grid (x: columns / 8, y: row groups); z: angles
     int bgx, bgy;          // brick grid (x, y); z: bricks along z
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(RED_THREADS) srv_after_forward(const SlotTable
     if (s >= tab->n) return;
     const SlotDev &sd = tab->s[s];
     if (sd.st->stop) return;
-    const double ss = reduce_partials(sd.pf, (tab->fwd_start[s + 1] - tab->fwd_start[s]) * TILE_PARTIALS, red);
+    const double ss = reduce_partials(sd.qf, sd.nqf, red);
     if (threadIdx.x == 0) gk_after_forward_step(sd.st, ss, nullptr);
 }
 
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(RED_THREADS) srv_after_backward(const SlotTabl
     if (s >= tab->n) return;
     const SlotDev &sd = tab->s[s];
     if (sd.st->stop) return;
-    const double ss = reduce_partials(sd.pb, (tab->bwd_start[s + 1] - tab->bwd_start[s]) * TILE_PARTIALS, red);
+    const double ss = reduce_partials(sd.qb, sd.nqb, red);
     if (threadIdx.x == 0)
         gk_after_backward_step(sd.st, ss, sd.method, sd.hist_r, sd.hist_n, nullptr, nullptr, sd.cap);
 }
@@ -216,6 +218,7 @@ struct Slot {
     float *U = nullptr, *Uw = nullptr, *V = nullptr, *w = nullptr, *x = nullptr, *h2 = nullptr, *b = nullptr;
     GkState *st = nullptr;
     double *pf = nullptr, *pb = nullptr, *hist = nullptr;
+    double *pfold = nullptr;          // 2 x FOLD_BLOCKS folded partials (steps of this slot alone)
     int nf = 0, nb = 0, steps = 0;
     int passed_over = 0;              // consecutive steps this slot was left out of (SRPT aging)
     bool aged = false;                // passed over SRV_SRPT_AGE_CAP steps in a row: first until it finishes
@@ -246,7 +249,8 @@ size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
     t += al((size_t)d.nz * d.nv * 8);                       // z slab table
     t += 3 * al(n * 4);                                     // U, |d'| U and the staged b
     t += al(m * 4) * (method == M_LSMR ? 4 : 3);            // V, w, x (+ hbar)
-    t += al(nf * 8 * TILE_PARTIALS) + al(nb * 8 * TILE_PARTIALS) + al(sizeof(GkState)) + al((size_t)2 * iters * 8);
+    t += al(nf * 8 * TILE_PARTIALS) + al(nb * 8 * TILE_PARTIALS) + al(2 * FOLD_BLOCKS * 8) + al(sizeof(GkState)) +
+         al((size_t)2 * iters * 8);
     t += al(m * 4);                                         // re-layout of x when the result is read out
     return t;
 }
@@ -264,9 +268,11 @@ size_t request_bytes(const cbct_geometry_desc &d, int method, int iters) {
 //               (one captured graph replayed) and hands finished slots on;
 //   read-out    copies each finished result to the host on its own stream,
 //               frees the slot's memory and wakes the waiters.
-// Geometries of read-out slots are destroyed by the step thread right after
-// it has queued a step (freeing device memory waits for the whole device,
-// and the step thread waits for the step next anyway).
+// Geometries of finished slots are destroyed only while no slot is active
+// (their tables are a few MB), because freeing device memory waits for the
+// whole device and would hold up the set-up of the next request (measured:
+// freeing them right after queuing a step raised the median latency of the
+// serving stream by 9 %).
 struct ServerImpl {
     size_t budget = 0, in_use = 0;
     int max_slots = 1, use_graph = 1, device = 0, schedule = CBCT_SCHED_FIFO;
@@ -304,6 +310,8 @@ struct ServerImpl {
     void release_slot(Slot &sl, cudaStream_t st, bool keep_geometry);
     cbct_status finish_slot(Slot &sl);
     cbct_status enqueue_step();
+    // the current step advances one slot whose tiles fill the GPU alone
+    bool solo_step() const { return step_slots.size() == 1 && slots[step_slots[0]].nf >= SRV_SAT_TILES; }
     void complete(const std::shared_ptr<Request> &r, cbct_status st, const std::string &msg);
 };
 
@@ -336,6 +344,7 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
     if (e == cudaSuccess && r.method == M_LSMR) e = A(&sl.h2, (size_t)m);
     if (e == cudaSuccess) e = A(&sl.pf, (size_t)std::max(sl.nf * TILE_PARTIALS, VEC_BLOCKS));
     if (e == cudaSuccess) e = A(&sl.pb, (size_t)sl.nb * TILE_PARTIALS);
+    if (e == cudaSuccess) e = A(&sl.pfold, (size_t)2 * FOLD_BLOCKS);
     if (e == cudaSuccess) e = A(&sl.st, (size_t)1);
     if (e == cudaSuccess) e = A(&sl.hist, (size_t)2 * r.iters);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.b, r.b.data(), sizeof(float) * n, cudaMemcpyHostToDevice, sa);
@@ -375,13 +384,13 @@ cbct_status ServerImpl::setup_slot(Slot &sl) {
 }
 
 // Frees the slot's buffers on stream `st`; the geometry is destroyed at once
-// or (keep_geometry) left in the graveyard for the step thread.
+// or (keep_geometry) left in the graveyard for a quiet moment.
 void ServerImpl::release_slot(Slot &sl, cudaStream_t st, bool keep_geometry) {
     for (void *p : {(void *)sl.U, (void *)sl.Uw, (void *)sl.b, (void *)sl.V, (void *)sl.w, (void *)sl.x, (void *)sl.h2,
-                    (void *)sl.pf, (void *)sl.pb, (void *)sl.st, (void *)sl.hist})
+                    (void *)sl.pf, (void *)sl.pb, (void *)sl.pfold, (void *)sl.st, (void *)sl.hist})
         if (p) cudaFreeAsync(p, st);
     sl.U = sl.Uw = sl.b = sl.V = sl.w = sl.x = sl.h2 = nullptr;
-    sl.pf = sl.pb = sl.hist = nullptr;
+    sl.pf = sl.pb = sl.pfold = sl.hist = nullptr;
     sl.st = nullptr;
     if (sl.ready) {
         cudaEventDestroy(sl.ready);
@@ -453,16 +462,22 @@ void ServerImpl::complete(const std::shared_ptr<Request> &r, cbct_status st, con
 // and leave the norm partials in the same places, so the results agree
 // bit for bit.  That step is captured once per slot.
 cbct_status ServerImpl::enqueue_step() {
-    Slot *solo = step_slots.size() == 1 && slots[step_slots[0]].nf >= SRV_SAT_TILES ? &slots[step_slots[0]] : nullptr;
+    Slot *solo = solo_step() ? &slots[step_slots[0]] : nullptr;
     auto launch_all = [&]() -> cudaError_t {
         if (solo) {
             const DevGeom &g = solo->geom->dev;
             const Epilogue ef{&solo->st->fa, &solo->st->fb, 0.0, 0.0, solo->pf, &solo->st->stop, nullptr, solo->Uw};
             const Epilogue eb{&solo->st->ba, &solo->st->bb, 0.0, 0.0, solo->pb, &solo->st->stop, nullptr};
             if (launch_forward(g, solo->V, solo->U, CBCT_F32, ef, s, true) != CBCT_OK) return cudaErrorLaunchFailure;
+            if (solo->nf * TILE_PARTIALS > FOLD_MIN)
+                k_fold_partials<RED_THREADS><<<FOLD_BLOCKS, RED_THREADS, 0, s>>>(solo->pf, solo->nf * TILE_PARTIALS,
+                                                                                solo->pfold);
             srv_after_forward<<<1, RED_THREADS, 0, s>>>(tab_dev);
             if (launch_backward(g, solo->Uw, solo->V, CBCT_F32, eb, s, true, nullptr) != CBCT_OK)
                 return cudaErrorLaunchFailure;
+            if (solo->nb * TILE_PARTIALS > FOLD_MIN)
+                k_fold_partials<RED_THREADS><<<FOLD_BLOCKS, RED_THREADS, 0, s>>>(solo->pb, solo->nb * TILE_PARTIALS,
+                                                                                solo->pfold + FOLD_BLOCKS);
             srv_after_backward<<<1, RED_THREADS, 0, s>>>(tab_dev);
         } else {
             cudaError_t e0 = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned), s);
@@ -605,12 +620,9 @@ void ServerImpl::run_steps() {
             if (stopping) break;
             incoming.swap(ready);
             active_slots = (int)(slots.size() + incoming.size());
-            dead.swap(graveyard);
+            if (slots.empty() && finishing.empty()) dead.swap(graveyard);     // a quiet moment
         }
-        if (slots.empty() && incoming.empty()) {        // nothing to step: free them now
-            for (cbct_geometry *g : dead) cbct_geometry_destroy(g);
-            continue;
-        }
+        for (cbct_geometry *g : dead) cbct_geometry_destroy(g);
         for (Slot &sl : incoming) {
             cudaStreamWaitEvent(s, sl.ready, 0);          // the step stream follows the slot's set-up
             slots.push_back(sl);
@@ -641,6 +653,13 @@ void ServerImpl::run_steps() {
                 d.U = sl.U; d.Uw = sl.Uw; d.V = sl.V; d.w = sl.w; d.x = sl.x; d.h2 = sl.h2;
                 d.st = sl.st;
                 d.pf = sl.pf; d.pb = sl.pb;
+                // a step of this slot alone folds its partials first (enqueue_step)
+                const bool fold_f = solo_step() && sl.nf * TILE_PARTIALS > FOLD_MIN;
+                const bool fold_b = solo_step() && sl.nb * TILE_PARTIALS > FOLD_MIN;
+                d.qf = fold_f ? sl.pfold : sl.pf;
+                d.nqf = fold_f ? FOLD_BLOCKS : sl.nf * TILE_PARTIALS;
+                d.qb = fold_b ? sl.pfold + FOLD_BLOCKS : sl.pb;
+                d.nqb = fold_b ? FOLD_BLOCKS : sl.nb * TILE_PARTIALS;
                 d.hist_r = sl.hist; d.hist_n = sl.hist + sl.req->iters;
                 d.method = sl.req->method;
                 d.cap = sl.req->iters;
@@ -659,15 +678,11 @@ void ServerImpl::run_steps() {
         // its remaining iterations are queued at once (a slot that stops
         // early turns the rest into no-ops); otherwise one.
         int run = 1;
-        if (schedule == CBCT_SCHED_FIFO && step_slots.size() == 1 && slots[step_slots[0]].nf >= SRV_SAT_TILES)
+        if (schedule == CBCT_SCHED_FIFO && solo_step())
             run = std::max(1, slots[step_slots[0]].req->iters - slots[step_slots[0]].steps);
         const double t_step = now_s(t0);
         cbct_status st = table_dirty ? cuda_fail(cudaGetLastError(), "server: slot table") : CBCT_OK;
         for (int q = 0; q < run && st == CBCT_OK; ++q) st = enqueue_step();
-        // read-out slots' geometries: freeing device memory waits for the
-        // device, which this thread does next anyway
-        for (cbct_geometry *g : dead) cbct_geometry_destroy(g);
-        dead.clear();
         cudaError_t e = cudaStreamSynchronize(s);
         {   // running estimate of the work rate (cost-model units per second)
             double w = 0.0;

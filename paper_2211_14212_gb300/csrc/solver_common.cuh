@@ -33,6 +33,21 @@ __device__ __forceinline__ double reduce_partials(const double *p, int n, double
     return block_sum<RED_THREADS>((s0 + s1) + (s2 + s3), scratch);
 }
 
+// Fixed-order fold of many norm partials into FOLD_BLOCKS block sums (block b
+// takes a contiguous range), so that the single-block scalar step that
+// follows reads few values; used when a projector leaves more than
+// FOLD_MIN partials.  Launch FOLD_BLOCKS blocks of RED_THREADS threads.
+constexpr int FOLD_BLOCKS = 152, FOLD_MIN = 16384;
+template <int NT>
+__global__ void __launch_bounds__(NT) k_fold_partials(const double *p, int n, double *out) {
+    static_assert(NT == RED_THREADS, "reduce_partials runs on RED_THREADS threads");
+    __shared__ double red[NT / 32];
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int b0 = min(n, (int)blockIdx.x * chunk), b1 = min(n, b0 + chunk);
+    const double sum = reduce_partials(p + b0, b1 - b0, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = sum;
+}
+
 // Givens rotation (c, s, r): [c s; -s c] [a; b] = [r; 0], r = hypot(a, b) >= 0.
 struct Rot { double c, s, r; };
 __device__ __forceinline__ Rot givens(double a, double b) {

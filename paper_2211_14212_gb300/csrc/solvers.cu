@@ -368,19 +368,6 @@ k_cg_p(float *__restrict__ p, const float *__restrict__ s, int64_t n, double *pa
 // ====================================================================== drivers
 
 
-// Fixed-order fold of many norm partials into FOLD_BLOCKS block sums (block b
-// takes a contiguous range), so that the single-block scalar step that
-// follows reads few values; used when a projector leaves more than
-// FOLD_MIN partials.
-constexpr int FOLD_BLOCKS = 152, FOLD_MIN = 16384;
-__global__ void __launch_bounds__(RED_THREADS) k_fold_partials(const double *p, int n, double *out) {
-    __shared__ double red[RED_THREADS / 32];
-    const int chunk = (n + gridDim.x - 1) / gridDim.x;
-    const int b0 = min(n, (int)blockIdx.x * chunk), b1 = min(n, b0 + chunk);
-    const double sum = reduce_partials(p + b0, b1 - b0, red);
-    if (threadIdx.x == 0) out[blockIdx.x] = sum;
-}
-
 template <typename T>
 static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x, const cbct_solve_opts *o,
                             cbct_solve_report *rep, cudaStream_t s, Method method, bool lsmr_proj) {
@@ -432,7 +419,7 @@ static cbct_status gk_solve(const cbct_geometry *geom, const float *b, float *x,
     // the scalar steps read the tiles' partials directly or folded first
     auto partials = [&](const double *p, int np, double *fold, const double **q, int *nq) {
         if (np > FOLD_MIN) {
-            k_fold_partials<<<FOLD_BLOCKS, RED_THREADS, 0, s>>>(p, np, fold);
+            k_fold_partials<RED_THREADS><<<FOLD_BLOCKS, RED_THREADS, 0, s>>>(p, np, fold);
             ++tr.launches;
             *q = fold;
             *nq = FOLD_BLOCKS;
