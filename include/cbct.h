@@ -366,7 +366,10 @@ cbct_status cbct_server_poll(cbct_server *srv, uint64_t id, int *done);
  * forgets the request and returns its status. */
 cbct_status cbct_server_wait(cbct_server *srv, uint64_t id, double timeout_s, float *x_host,
                              cbct_solve_report *report, cbct_request_times *times);
-/* Counters: steps run, CUDA-graph replays, bytes currently held, requests in slots and waiting. */
+/* Counters: steps run, CUDA-graph replays, bytes currently held, requests in slots and waiting.
+ * A request is done (and cbct_server_wait returns) as soon as its result is on
+ * the host; its device memory is freed right after, so bytes_in_use can lag
+ * the last wait by the time of those frees. */
 typedef struct {
     int64_t steps, graph_replays;
     size_t bytes_in_use;

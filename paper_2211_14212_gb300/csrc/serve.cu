@@ -313,6 +313,8 @@ struct ServerImpl {
     // the current step advances one slot whose tiles fill the GPU alone
     bool solo_step() const { return step_slots.size() == 1 && slots[step_slots[0]].nf >= SRV_SAT_TILES; }
     void complete(const std::shared_ptr<Request> &r, cbct_status st, const std::string &msg);
+    void publish(const std::shared_ptr<Request> &r, cbct_status st, const std::string &msg);
+    void return_budget(const std::shared_ptr<Request> &r);
 };
 
 // -------------------------------------------------------------- slot life
@@ -443,15 +445,28 @@ cbct_status ServerImpl::finish_slot(Slot &sl) {
 
 // Marks a request done (its memory already released) and wakes waiters and admission.
 void ServerImpl::complete(const std::shared_ptr<Request> &r, cbct_status st, const std::string &msg) {
+    publish(r, st, msg);
+    return_budget(r);
+}
+
+// Marks a request done and wakes its waiters (its memory may still be held).
+void ServerImpl::publish(const std::shared_ptr<Request> &r, cbct_status st, const std::string &msg) {
     {
         std::lock_guard<std::mutex> lk(mu);
         if (st != CBCT_OK) r->status = st;
         if (!msg.empty()) r->error = msg;
         r->done = true;
         r->t_finish = now_s(t0);
-        in_use -= r->bytes;
     }
     cv_done.notify_all();
+}
+
+// Gives a request's memory back to the budget (its buffers already freed) and wakes admission.
+void ServerImpl::return_budget(const std::shared_ptr<Request> &r) {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        in_use -= r->bytes;
+    }
     cv_admit.notify_one();
 }
 
@@ -756,8 +771,9 @@ void ServerImpl::run_readout() {
         cbct_status fs = finish_slot(sl);
         const std::string msg = fs == CBCT_OK ? std::string() : std::string(cbct_last_error());
         std::shared_ptr<Request> r = sl.req;
+        publish(r, fs, msg);                     // the result is on the host: the waiter may go on
         release_slot(sl, s_read, true);
-        complete(r, fs, msg);
+        return_budget(r);
     }
 }
 
