@@ -488,6 +488,50 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, const T *__restri
 // w[a][iu][iv] = |d'| * y.
 
 constexpr int BWD_THREADS = 256;
+
+// Calls body(iu, ain, aout) for every detector column iu in [iu0, iu1], in
+// increasing order, whose ray column crosses voxel column (i, j) of angle a:
+// [ain, aout] is the alpha interval of the x/y cell (warp-uniform), from the
+// same plane_alpha values either way.  LANES: the lanes clip up to 32 columns
+// at once (lane l: column c0 + l), then the warp walks them, taking each
+// column's interval from its lane; otherwise the warp clips column by column
+// (fewer registers).  All lanes must call it.
+template <bool LANES, int UNROLL, typename Body>
+__device__ __forceinline__ void for_crossing_columns(const DevGeom &g, int a, int i, int j, int iu0, int iu1,
+                                                     int lane, Body &&body) {
+    auto clip = [&](int iu, float &ain, float &aout) {
+        const float4 xy = __ldg(&g.ray_xy[(size_t)a * g.nu + iu]);
+        const float2 q = __ldg(&g.ray_xyq[(size_t)a * g.nu + iu]);
+        ain = -FLT_MAX;
+        aout = FLT_MAX;
+        bool miss = false;
+        clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
+        clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
+        if (miss) {
+            ain = FLT_MAX;                             // empty: no crossing
+            aout = -FLT_MAX;
+        }
+    };
+    if (LANES) {
+        for (int c0 = iu0; c0 <= iu1; c0 += 32) {
+            const int cn = min(32, iu1 - c0 + 1);
+            float cin = FLT_MAX, cout = -FLT_MAX;
+            if (lane < cn) clip(c0 + lane, cin, cout);
+#pragma unroll UNROLL
+            for (int c = 0; c < cn; ++c) {
+                const float ain = __shfl_sync(0xffffffffu, cin, c), aout = __shfl_sync(0xffffffffu, cout, c);
+                if (ain < aout) body(c0 + c, ain, aout);
+            }
+        }
+    } else {
+#pragma unroll UNROLL
+        for (int iu = iu0; iu <= iu1; ++iu) {
+            float ain, aout;
+            clip(iu, ain, aout);
+            if (ain < aout) body(iu, ain, aout);
+        }
+    }
+}
 constexpr int BWD_SHORT_ROWS = 3;
 
 // Angles [a_begin, a_end) are summed in one call.  A scan whose projections
@@ -506,9 +550,11 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                                               const float *acc_in, float *acc_out, PartialAt &&partial_at,
                                               double *red) {
     constexpr int CY = 8 / CX;
-    // detector columns per unrolled step of the column loops: as many as fit
-    // in registers next to the voxels' sums
-    constexpr int BWD_IU_UNROLL = IU_UNROLL > 0 ? IU_UNROLL : !HOIST ? 1 : K == 1 ? 2 : K == 2 ? 4 : 2;
+    // detector columns clipped by the lanes at once (tiles of up to 2 voxels
+    // per lane; the 4-voxel tiles keep the per-column clip, which needs fewer
+    // registers) and columns per unrolled step of the column loops
+    constexpr bool BWD_LANE_CLIP = K <= 2;
+    constexpr int BWD_IU_UNROLL = IU_UNROLL > 0 ? IU_UNROLL : !HOIST ? 1 : K == 1 ? 2 : K == 2 ? 1 : 2;
     // HOIST: the slab intervals of the candidate rows are loaded once per
     // angle and kept in registers (3 x 2 per voxel of the lane); otherwise
     // they are loaded for every detector column.
@@ -593,15 +639,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                 // unrolled: the next columns' table and projection loads are
                 // issued before this column's sums (measured 7 % faster than
                 // the compiler's choice, which kept the loop rolled)
-#pragma unroll BWD_IU_UNROLL
-                for (int iu = iu0; iu <= iu1; ++iu) {
-                    const float4 xy = __ldg(&g.ray_xy[(size_t)a * g.nu + iu]);
-                    const float2 q = __ldg(&g.ray_xyq[(size_t)a * g.nu + iu]);
-                    float ain = -FLT_MAX, aout = FLT_MAX;
-                    bool miss = false;
-                    clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
-                    clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
-                    if (miss || !(ain < aout)) continue;
+                for_crossing_columns<BWD_LANE_CLIP, BWD_IU_UNROLL>(g, a, i, j, iu0, iu1, lane, [&](int iu, float ain, float aout) {
                     const float *wcol = pa + (size_t)iu * g.nv;
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) {
@@ -613,7 +651,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                             acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wr + t), acc[kk]);
                         }
                     }
-                }
+                });
             };
             if (rows2) {
                 short_pass(std::integral_constant<int, 2>());
@@ -629,14 +667,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                     rlo[kk] = max(0, (int)ceilf(vmin + (cv - 0.05f)));
                     rhi[kk] = k < g.nz ? min(g.nv - 1, (int)floorf(vmax + (cv + 0.05f))) : -1;
                 }
-                for (int iu = iu0; iu <= iu1; ++iu) {
-                    const float4 xy = __ldg(&g.ray_xy[(size_t)a * g.nu + iu]);
-                    const float2 q = __ldg(&g.ray_xyq[(size_t)a * g.nu + iu]);
-                    float ain = -FLT_MAX, aout = FLT_MAX;
-                    bool miss = false;
-                    clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
-                    clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
-                    if (miss || !(ain < aout)) continue;
+                for_crossing_columns<BWD_LANE_CLIP, 1>(g, a, i, j, iu0, iu1, lane, [&](int iu, float ain, float aout) {
                     const float *wcol = pa + (size_t)iu * g.nv;
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) {
@@ -646,7 +677,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                             acc[kk] = __fmaf_rn(fmaxf(hi - lo, 0.0f), __ldg(wcol + iv), acc[kk]);
                         }
                     }
-                }
+                });
             }
         }
     }
@@ -702,15 +733,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
             short_rows = __all_sync(0xffffffffu, short_rows);
             const float *pa = wproj + (size_t)a * nuv;
             // unrolled for the same reason as the hoisted loop above
-#pragma unroll BWD_IU_UNROLL
-            for (int iu = iu0; iu <= iu1; ++iu) {
-                const float4 xy = __ldg(&g.ray_xy[(size_t)a * g.nu + iu]);
-                const float2 q = __ldg(&g.ray_xyq[(size_t)a * g.nu + iu]);
-                float ain = -FLT_MAX, aout = FLT_MAX;
-                bool miss = false;
-                clip_slab(RayAxis{xy.x, xy.y, q.x}, g.dx, i, i + 1, ain, aout, miss);
-                clip_slab(RayAxis{xy.z, xy.w, q.y}, g.dy, j, j + 1, ain, aout, miss);
-                if (miss || !(ain < aout)) continue;
+            for_crossing_columns<BWD_LANE_CLIP, BWD_IU_UNROLL>(g, a, i, j, iu0, iu1, lane, [&](int iu, float ain, float aout) {
                 const float *wcol = pa + (size_t)iu * g.nv;
                 if (short_rows) {
 #pragma unroll
@@ -738,7 +761,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
                         }
                     }
                 }
-            }
+            });
         }
     }
     if (acc_out) {                      // an earlier pass: keep the running sums
