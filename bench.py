@@ -57,10 +57,10 @@ REF_STEP_ANGLES = 8             # --impl reference: about 7 s per step, so K ste
 # ignored) and the launch shape (rays per lane, transpose configuration);
 # the bench reports null once either differs.
 NCU_COUNTERS = {
-    "forward": {"hash": "1a21aa326c147b5e", "shape": [4, 3], "kernel": "forward_kernel<float, 0, 4, 1>",
-                "dram_bytes": 3025939456, "warp_inst": 19929252800},
-    "backward": {"hash": "1a21aa326c147b5e", "shape": [4, 3], "kernel": "backward_kernel<float, 1, 2, 2, 1, 0>",
-                 "dram_bytes": 3025801472, "warp_inst": 35444234412},
+    "forward": {"hash": "bf0c463e413182ae", "shape": [4, 3], "kernel": "forward_kernel<float, 0, 4, 1>",
+                "dram_bytes": 3018182400, "warp_inst": 19929252800},
+    "backward": {"hash": "bf0c463e413182ae", "shape": [4, 3], "kernel": "backward_kernel<float, 1, 2, 2, 1, 0>",
+                 "dram_bytes": 2791051008, "warp_inst": 31975031028},
 }
 
 # Instruction issue: one warp instruction per cycle per SM sub-partition.
