@@ -126,3 +126,44 @@ def test_roofline_counters_follow_code_and_launch_shape(monkeypatch):
         "backward": {"hash": "0" * 16, "shape": [4, 3], "dram_bytes": 3.0e9, "warp_inst": 3.75e10}})
     stale = bench.roofline_block(g, 2.8e10, 24.0, 38.0, {"sm_mhz": 2070.0}, (4, 3))
     assert stale["traffic"] is None and stale["issue_util"] is None
+
+
+def test_calibrate_service_recovers_rate_and_fixed_cost(monkeypatch):
+    """calibrate_service fits the one-at-a-time service time as
+    fixed x (rays + voxels) + iters x 2 nnz / rate: on a fake library whose
+    solves advance a fake clock by exactly that, the fit returns both
+    constants and the predicted service of every request."""
+    import types
+
+    import numpy as np
+
+    import synth
+    rate, fixed = 1.0e9, 6.0e-10          # per-iteration times well above the fit's 1 us floor
+    clock = [0.0]
+    monkeypatch.setattr(bench.time, "perf_counter", lambda: clock[0])
+
+    class Geometry:
+        def __init__(self, g):
+            self.g = g
+
+        def close(self):
+            pass
+
+    def solve(geom, b, iters):
+        r = by_id[id(geom.g)]
+        clock[0] += fixed * (r["geom"].num_rays + r["geom"].num_voxels) + iters * 2.0 * r["nnz"] / rate
+        return None, None
+
+    fake = types.SimpleNamespace(Geometry=Geometry, lsqr=solve, lsmr=solve)
+    reqs = []
+    for i, n in enumerate((16, 24, 32, 40, 48)):
+        g = synth.Geometry(n, n, n, 1.0, 1.0, 1.0, 2 * n, n, 1.0, 1.0, 400.0, 640.0, synth.circular_angles(10 + i))
+        reqs.append({"geom": g, "solver": ["lsqr", "lsmr"][i % 2], "iters": 20 + i, "b": None,
+                     "nnz": g.num_rays * n})
+    by_id = {id(r["geom"]): r for r in reqs}
+    svc, model = bench.calibrate_service(fake, reqs)
+    assert abs(model["updates_per_s"] / rate - 1) < 1e-9
+    assert abs(model["fixed_s_per_element"] / fixed - 1) < 1e-9
+    want = [fixed * (r["geom"].num_rays + r["geom"].num_voxels) + r["iters"] * 2.0 * r["nnz"] / rate for r in reqs]
+    assert np.allclose(svc, want, rtol=1e-9)
+    assert model["calibration_requests"] == [0, 1, 3, 4]
