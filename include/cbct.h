@@ -357,6 +357,12 @@ cbct_status cbct_server_create(const cbct_server_opts *opts, cbct_server **out);
  * needs more than the budget.  *id identifies the request. */
 cbct_status cbct_server_submit(cbct_server *srv, const cbct_geometry_desc *desc, const float *b_host,
                                cbct_solver solver, const cbct_solve_opts *opts, uint64_t *id);
+/* Device memory a request of this scan, solver and iteration count holds at
+ * its peak: what cbct_server_submit charges against the budget (ray tables,
+ * Krylov vectors, staging of b, norm partials, state and histories).  Host
+ * arithmetic only (no device needed); CBCT_EINVAL on a null pointer, an
+ * invalid geometry, a solver other than LSQR / LSMR or iters < 1. */
+cbct_status cbct_server_request_bytes(const cbct_geometry_desc *desc, cbct_solver solver, int iters, size_t *bytes);
 /* *done = 1 once the request's result is ready (CBCT_ENOTFOUND for unknown ids). */
 cbct_status cbct_server_poll(cbct_server *srv, uint64_t id, int *done);
 /* Waits up to timeout_s seconds (< 0: forever) for the request.  On time-out

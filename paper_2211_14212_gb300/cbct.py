@@ -123,6 +123,8 @@ def load(path: str = LIB_PATH):
     lib.cbct_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(ctypes.c_void_p)]
     lib.cbct_server_submit.argtypes = [vp, ctypes.POINTER(_Desc), vp, ctypes.c_int, ctypes.POINTER(_Opts),
                                        ctypes.POINTER(ctypes.c_uint64)]
+    lib.cbct_server_request_bytes.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_size_t)]
     lib.cbct_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
     lib.cbct_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, vp, ctypes.POINTER(_Report),
                                      ctypes.POINTER(_Times)]
@@ -541,6 +543,17 @@ class ServedResult:
     submit_s: float
     admit_s: float
     finish_s: float
+
+
+def server_request_bytes(spec, solver="lsqr", iters=30) -> int:
+    """Device memory a server request of this scan holds at its peak, the
+    amount cbct_server_submit charges against the budget
+    (cbct_server_request_bytes; host arithmetic, no device needed)."""
+    d, _angles = _desc_of(spec)
+    out = ctypes.c_size_t()
+    _check("cbct_server_request_bytes", load().cbct_server_request_bytes(ctypes.byref(d), Server.SOLVERS[solver],
+                                                                         int(iters), ctypes.byref(out)))
+    return int(out.value)
 
 
 class Server:

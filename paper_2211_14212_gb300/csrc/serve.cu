@@ -861,6 +861,20 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *o, cbct_server
     return CBCT_OK;
 }
 
+extern "C" cbct_status cbct_server_request_bytes(const cbct_geometry_desc *desc, cbct_solver solver, int iters,
+                                                 size_t *bytes) {
+    if (!desc || !bytes) { set_error("cbct_server_request_bytes: null argument"); return CBCT_EINVAL; }
+    if (solver != CBCT_SOLVER_LSQR && solver != CBCT_SOLVER_LSMR) {
+        set_error("cbct_server_request_bytes: solver must be LSQR or LSMR");
+        return CBCT_EINVAL;
+    }
+    if (iters < 1) { set_error("cbct_server_request_bytes: need iters >= 1"); return CBCT_EINVAL; }
+    const cbct_status st = validate_geometry_desc(desc);
+    if (st != CBCT_OK) return st;
+    *bytes = request_bytes(*desc, solver == CBCT_SOLVER_LSQR ? M_LSQR : M_LSMR, iters);
+    return CBCT_OK;
+}
+
 extern "C" cbct_status cbct_server_submit(cbct_server *srv, const cbct_geometry_desc *desc, const float *b_host,
                                           cbct_solver solver, const cbct_solve_opts *o, uint64_t *id) {
     if (!srv || !desc || !b_host || !o || !id) { set_error("cbct_server_submit: null argument"); return CBCT_EINVAL; }

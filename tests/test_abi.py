@@ -99,6 +99,32 @@ def test_server_argument_checks(lib):
     lib.cbct_server_destroy(None)
 
 
+def test_server_request_bytes(lib):
+    """The budget charge of a server request, computed on the host: it
+    counts the Krylov vectors (LSMR keeps one more volume than LSQR, each
+    iteration adds two FP64 history entries) and grows with the scan."""
+    from paper_2211_14212_gb300 import cbct
+    g = synth.config("c1")
+    lsqr = cbct.server_request_bytes(g, "lsqr", 10)
+    lsmr = cbct.server_request_bytes(g, "lsmr", 10)
+    padded_volume = g.nx * g.ny * (g.nz + 2) + 4
+    assert lsqr >= 4 * (3 * g.num_rays + 3 * padded_volume)
+    assert lsmr - lsqr >= 4 * padded_volume
+    # buffers are rounded up to 1 KiB each
+    assert cbct.server_request_bytes(g, "lsqr", 1000) - lsqr >= 2 * 990 * 8 - 1024
+    more_angles = g.with_angles(synth.circular_angles(2 * g.nangles))
+    assert cbct.server_request_bytes(more_angles, "lsqr", 10) - lsqr >= 4 * 3 * g.num_rays
+    d, _angles = cbct._desc_of(g)
+    out = ctypes.c_size_t()
+    assert lib.cbct_server_request_bytes(None, 0, 10, ctypes.byref(out)) == cbct.CBCT_EINVAL
+    assert lib.cbct_server_request_bytes(ctypes.byref(d), 0, 10, None) == cbct.CBCT_EINVAL
+    assert lib.cbct_server_request_bytes(ctypes.byref(d), 2, 10, ctypes.byref(out)) == cbct.CBCT_EINVAL
+    assert lib.cbct_server_request_bytes(ctypes.byref(d), 0, 0, ctypes.byref(out)) == cbct.CBCT_EINVAL
+    bad = cbct._desc_of(g)[0]
+    bad.nx = 0
+    assert lib.cbct_server_request_bytes(ctypes.byref(bad), 0, 10, ctypes.byref(out)) == cbct.CBCT_EINVAL
+
+
 def test_geometry_device_of_null(lib):
     assert lib.cbct_geometry_device(None) == -1
 

@@ -79,13 +79,15 @@ def test_alone_equals_mix_equals_solver(cbct, scans):
 
 
 def test_budget_admission_one_at_a_time(cbct, scans):
-    """A budget that fits one request: the others wait and are admitted as it finishes."""
+    """A budget that fits one request and not two (slots to spare): the others
+    wait and are admitted once its memory is back, after its result."""
     g, b, solver, _ = scans[2]
-    with cbct.Server(1 << 30, max_slots=1) as srv:
+    need = cbct.server_request_bytes(g, solver, 6)
+    with cbct.Server(need + need // 2, max_slots=4) as srv:
         ids = [srv.submit(g, b, solver, 6) for _ in range(3)]
         res = [srv.wait(i, timeout=300) for i in ids]
     for r0, r1 in zip(res, res[1:]):
-        assert r1.admit_s >= r0.finish_s - 1e-3
+        assert r1.admit_s >= r0.finish_s
     for r in res[1:]:
         assert rel(r.x, res[0].x) <= MIX_TOL
 
