@@ -23,7 +23,8 @@ Printed JSON line (rank 0):
              service times) through the
              continuous-batching server and through the one-request-at-a-time
              solver, both fed in real time: recon/s, p50 / p99 / mean latency
-             and the largest relative difference between their results;
+             and the largest relative difference between their results (at
+             N = 1 only);
   cpu_baseline  the FP64 oracle on the host cores, on a 24-angle sample.
 `--impl reference` times that oracle alone (the CPU reference arm).
 Multi-GPU (torchrun): independent replicas, one per rank, weak scaling.
@@ -382,7 +383,9 @@ def run_ours(args):
     del x1, x2, b
 
     serving = None
-    if not args.no_serving and rank == 0:
+    # the serving stream runs on one GPU for about ten minutes: at N = 1 only,
+    # so that a multi-GPU run does not hold the other GPUs idle meanwhile
+    if not args.no_serving and world == 1:
         serving = serving_compare(cbct, torch, dev, args.requests, args.serving_scale,
                                   args.serving_slots, args.serving_budget_gb, args.serving_schedule)
 
@@ -412,7 +415,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "launch_shapes": {"fwd_rows": tune["fwd_rows"], "bwd_brick": tune["bwd_shape"]},
-        "serving": serving,
+        "serving": serving if world == 1 else {"measured": "at N = 1 only (one GPU, about ten minutes)"},
     }
     print(json.dumps(out), flush=True)
     if world > 1:
