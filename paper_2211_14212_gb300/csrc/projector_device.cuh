@@ -636,9 +636,11 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
 #pragma unroll
                     for (int t = 0; t < ROWS; ++t) zb[kk][t] = __ldg(&g.zbox[zboff[kk] + r0[kk] + t]);
                 }
-                // unrolled: the next columns' table and projection loads are
-                // issued before this column's sums (measured 7 % faster than
-                // the compiler's choice, which kept the loop rolled)
+                // the column walk is unrolled by BWD_IU_UNROLL, so that the
+                // next columns' loads are issued before this column's sums
+                // (the per-column clip measured 7 % faster that way than the
+                // compiler's choice, which kept the loop rolled; the lane
+                // clip runs best rolled, at 3 CTAs per SM)
                 for_crossing_columns<BWD_LANE_CLIP, BWD_IU_UNROLL>(g, a, i, j, iu0, iu1, lane, [&](int iu, float ain, float aout) {
                     const float *wcol = pa + (size_t)iu * g.nv;
 #pragma unroll
@@ -732,7 +734,7 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
             for (int kk = 0; kk < K; ++kk) short_rows = short_rows && r1[kk] - r0[kk] < BWD_SHORT_ROWS;
             short_rows = __all_sync(0xffffffffu, short_rows);
             const float *pa = wproj + (size_t)a * nuv;
-            // unrolled for the same reason as the hoisted loop above
+            // unrolled by BWD_IU_UNROLL, as the hoisted walk above
             for_crossing_columns<BWD_LANE_CLIP, BWD_IU_UNROLL>(g, a, i, j, iu0, iu1, lane, [&](int iu, float ain, float aout) {
                 const float *wcol = pa + (size_t)iu * g.nv;
                 if (short_rows) {
