@@ -556,8 +556,8 @@ __device__ __forceinline__ void backward_tile(const DevGeom &g, const float *__r
     constexpr bool BWD_LANE_CLIP = K <= 2;
     constexpr int BWD_IU_UNROLL = IU_UNROLL > 0 ? IU_UNROLL : !HOIST ? 1 : K == 1 ? 2 : K == 2 ? 1 : 2;
     // HOIST: the slab intervals of the candidate rows are loaded once per
-    // angle and kept in registers (3 x 2 per voxel of the lane); otherwise
-    // they are loaded for every detector column.
+    // angle and kept in registers (2 or 3 rows x 2 floats per voxel of the
+    // lane); otherwise they are loaded for every detector column.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = tx * CX + (warp % CX), j = ty * CY + (warp / CX);
     const int k0 = tz * 32 * K;
